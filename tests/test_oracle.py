@@ -1,0 +1,282 @@
+"""Pins for the CPU oracle against facts fixed outside the oracle itself.
+
+* Table 1 of the paper: 17 printed (L, E, F, hex) rows -> Eq. 1 + Eq. 2 + encoding.
+* Closed forms: Barker sequences (|C_k| <= 1), constant and alternating sequences.
+* Exhaustive cross-check against numpy.correlate (a library routine) for small L.
+* Invariants of skew-symmetric sequences: C_k = 0 for odd k; E(-S) = E(S), etc.
+* Random123 known-answer vectors for Philox4x32-10.
+* The walk (Eq. 3, Algorithm 2): replayed against a brute-force table of all
+  2^D skew energies, computed here with numpy, for every step of several walks.
+"""
+import os
+
+import numpy as np
+import pytest
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_rows(name):
+    rows = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def decode_table1_hex(hexstr, L):
+    """Table 1 encoding: low D bits of the hex number, most significant first, 0->+1, 1->-1."""
+    D = (L + 1) // 2
+    v = int(hexstr, 16)
+    assert v < (1 << D), "hex string longer than D bits"
+    return np.array([-1 if (v >> (D - 1 - i)) & 1 else 1 for i in range(D)], dtype=np.int8)
+
+
+def np_energy(s):
+    """Eq. 1 through numpy's full cross-correlation (lags 1..L-1 on one side)."""
+    s = np.asarray(s, dtype=np.int64)
+    L = s.size
+    c = np.correlate(s, s, mode="full")[L:]  # lags 1..L-1
+    return int(np.sum(c * c))
+
+
+def np_skew(free, L):
+    """Eq. 2 written directly from its statement: s_{D+i} = (-1)^i s_{D-i}, 1-based."""
+    D = (L + 1) // 2
+    s = np.zeros(L + 1, dtype=np.int64)  # 1-based
+    s[1:D + 1] = free
+    for i in range(1, D):
+        s[D + i] = (-1) ** i * s[D - i]
+    return s[1:].astype(np.int8)
+
+
+# ----------------------------------------------------------------- Table 1
+@pytest.mark.parametrize("row", read_rows("table1_skew_sequences.txt"), ids=lambda r: "L%s" % r[0])
+def test_table1_energy_and_merit(oracle_mod, row):
+    L, E, F = int(row[0]), int(row[1]), row[2]
+    free = decode_table1_hex(row[4], L)
+    s = oracle_mod.skew_expand(free, L)
+    assert np.array_equal(s, np_skew(free, L))
+    assert oracle_mod.energy(s) == E
+    # F = L^2 / (2E), printed to 4 decimals; the table truncates some rows
+    # (L=193: 9.12966.. -> 9.1296) and rounds others (L=219: 9.20556.. -> 9.2056)
+    f = L * L / (2.0 * E)
+    assert abs(f - float(F)) < 1e-4
+    # negating the sequence or using the other sign convention leaves E unchanged
+    assert oracle_mod.energy(-s) == E
+
+
+def test_table1_bit_order_matters(oracle_mod):
+    # the least-significant-first reading does not reproduce the printed energies
+    misses = 0
+    for row in read_rows("table1_skew_sequences.txt"):
+        L, E = int(row[0]), int(row[1])
+        free = decode_table1_hex(row[4], L)[::-1].copy()
+        misses += oracle_mod.energy(oracle_mod.skew_expand(free, L)) != E
+    assert misses >= 15
+
+
+# ------------------------------------------------------------ closed forms
+BARKER = {
+    5: "+++-+",
+    7: "+++--+-",
+    11: "+++---+--+-",
+    13: "+++++--++-+-+",
+}
+
+
+@pytest.mark.parametrize("L", sorted(BARKER))
+def test_barker_sequences(oracle_mod, L):
+    s = np.array([1 if c == "+" else -1 for c in BARKER[L]], dtype=np.int8)
+    # odd-length Barker sequences are skew-symmetric, |C_k| <= 1, so E = (L-1)/2
+    D = (L + 1) // 2
+    assert np.array_equal(oracle_mod.skew_expand(s[:D], L), s)
+    C = oracle_mod.autocorrelations(s)
+    assert C[0] == L and np.all(np.abs(C[1:]) <= 1)
+    assert oracle_mod.energy(s) == (L - 1) // 2
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 10, 27, 64, 121])
+def test_constant_and_alternating(oracle_mod, L):
+    closed = (L - 1) * L * (2 * L - 1) // 6  # sum_{k=1}^{L-1} (L-k)^2
+    ones = np.ones(L, dtype=np.int8)
+    alt = np.array([(-1) ** i for i in range(L)], dtype=np.int8)
+    assert oracle_mod.energy(ones) == closed
+    assert oracle_mod.energy(alt) == closed
+    C = oracle_mod.autocorrelations(alt)
+    assert all(C[k] == (-1) ** k * (L - k) for k in range(L))
+
+
+def test_energy_rejects_non_pm1(oracle_mod):
+    with pytest.raises(ValueError):
+        oracle_mod.energy(np.array([1, 0, -1], dtype=np.int8))
+    with pytest.raises(ValueError):
+        oracle_mod.skew_expand(np.ones(3, dtype=np.int8), 6)
+
+
+# ------------------------------------------------- exhaustive, small L
+@pytest.mark.parametrize("L", [5, 7, 9, 11, 13, 15, 17])
+def test_exhaustive_vs_numpy_and_invariants(oracle_mod, L):
+    D = (L + 1) // 2
+    best = None
+    for code in range(1 << D):
+        free = np.array([-1 if (code >> j) & 1 else 1 for j in range(D)], dtype=np.int8)
+        s = oracle_mod.skew_expand(free, L)
+        e = oracle_mod.energy(s)
+        assert e == np_energy(s)
+        C = oracle_mod.autocorrelations(s)
+        assert np.all(C[1::2] == 0), "odd lags vanish on skew-symmetric sequences"
+        assert np.all(C[2::2] % 2 == 1), "even lags are sums of an odd number of +-1"
+        if code % 7 == 0:
+            alt = (s * np.array([(-1) ** i for i in range(L)], dtype=np.int8)).astype(np.int8)
+            assert oracle_mod.energy(s[::-1].copy()) == e
+            assert oracle_mod.energy(alt) == e
+        best = e if best is None else min(best, e)
+    if L in BARKER:
+        assert best == (L - 1) // 2  # Barker sequences are optimal where they exist
+
+
+# --------------------------------------------------------------- Philox
+@pytest.mark.parametrize("row", read_rows("philox4x32_10_kat.txt"))
+def test_philox_known_answers(oracle_mod, row):
+    v = [int(x, 16) for x in row]
+    out = oracle_mod.philox4x32_10(v[0:4], v[4:6])
+    assert [int(x) for x in out] == v[6:10]
+
+
+def test_start_stream_layout(oracle_mod):
+    # bit j of the start = bit (j%32) of word (j/32)%4 of Philox(ctr=(walk, round, j/128, 0), key=seed)
+    seed, walk, rnd, D = 0x0123456789ABCDEF, 77, 5, 225
+    got = oracle_mod.start_free_values(seed, walk, rnd, D)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(D):
+        blk = oracle_mod.philox4x32_10([walk, rnd, j // 128, 0], key)
+        bit = (int(blk[(j // 32) % 4]) >> (j % 32)) & 1
+        assert got[j] == (-1 if bit else 1)
+    # streams of different walks / rounds / seeds differ and are balanced
+    a = np.concatenate([oracle_mod.start_free_values(1, w, 0, 61) for w in range(400)])
+    assert abs(float(np.mean(a == -1)) - 0.5) < 0.02
+    assert not np.array_equal(oracle_mod.start_free_values(1, 0, 0, 61), oracle_mod.start_free_values(1, 0, 1, 61))
+    assert not np.array_equal(oracle_mod.start_free_values(1, 0, 0, 61), oracle_mod.start_free_values(2, 0, 0, 61))
+
+
+# ------------------------------------------------------ walk vs brute force
+def brute_table(L):
+    """Energy of every skew pivot, indexed by the free-bit code (bit j <-> s_{j+1} = -1)."""
+    D = (L + 1) // 2
+    codes = np.arange(1 << D, dtype=np.int64)
+    bits = ((codes[:, None] >> np.arange(D)[None, :]) & 1).astype(np.int64)
+    free = 1 - 2 * bits
+    full = np.zeros((codes.size, L), dtype=np.int64)
+    c = D - 1
+    full[:, :D] = free
+    for i in range(1, D):
+        full[:, c + i] = (-1) ** i * full[:, c - i]
+    E = np.zeros(codes.size, dtype=np.int64)
+    for k in range(1, L):
+        Ck = np.sum(full[:, :L - k] * full[:, k:], axis=1)
+        E += Ck * Ck
+    return E
+
+
+def code_of(free):
+    return int(sum((1 << j) for j, v in enumerate(free) if v == -1))
+
+
+def replay(oracle_mod, L, seed, walk, rnd, walk_len, table):
+    """Re-derive the whole trajectory of Eq. 3 from the brute-force table."""
+    D = (L + 1) // 2
+    tr = oracle_mod.walk_trace(L, seed, walk, rnd, walk_len, check=True)
+    assert not tr["check_failed"]
+    cur = code_of(oracle_mod.start_free_values(seed, walk, rnd, D))
+    visited = {cur}
+    energies = [int(table[cur])]
+    flips = []
+    stuck = 0
+    for _ in range(walk_len):
+        cands = [(int(table[cur ^ (1 << j)]), j) for j in range(D) if (cur ^ (1 << j)) not in visited]
+        if not cands:
+            stuck = 1
+            break
+        e, j = min(cands)  # lowest energy, then lowest flip index
+        cur ^= 1 << j
+        visited.add(cur)
+        flips.append(j)
+        energies.append(e)
+    assert tr["moves"] == len(flips)
+    assert tr["stuck"] == stuck
+    assert list(tr["flips"]) == flips
+    assert list(tr["energies"]) == energies
+    assert len(visited) == len(flips) + 1  # never revisits a pivot
+    best = min(energies)
+    assert tr["best_E"] == best and tr["best_step"] == energies.index(best)
+    assert code_of(tr["best_seq"][:D]) == code_of(oracle_mod.skew_expand(tr["best_seq"][:D], L)[:D])
+    assert np.array_equal(oracle_mod.skew_expand(tr["best_seq"][:D], L), tr["best_seq"])
+    assert int(table[code_of(tr["best_seq"][:D])]) == best
+    return tr, stuck
+
+
+def test_walks_vs_bruteforce_L27():
+    import oracle
+    table = brute_table(27)
+    assert int(table.min()) == 37  # optimum of the skew-symmetric L=27 space
+    reached = 0
+    for w in range(6):
+        tr, _ = replay(oracle, 27, 1, w, 0, 1500, table)
+        reached += tr["best_E"] == 37
+    assert reached >= 1
+
+
+@pytest.mark.parametrize("L,walk_len", [(5, 12), (7, 40), (9, 300), (11, 64), (13, 200)])
+def test_walks_vs_bruteforce_small_with_stuck(oracle_mod, L, walk_len):
+    table = brute_table(L)
+    D = (L + 1) // 2
+    stuck_seen = 0
+    for w in range(8):
+        tr, stuck = replay(oracle_mod, L, 3, w, 1, walk_len, table)
+        stuck_seen += stuck
+        if stuck:
+            assert tr["moves"] < (1 << D)
+    if walk_len >= (1 << D):
+        assert stuck_seen == 8  # a walk cannot outlast the space
+
+
+@pytest.mark.parametrize("L", [61, 121])
+def test_incremental_matches_eq1_every_step(oracle_mod, L):
+    tr = oracle_mod.walk_trace(L, 9, 3, 2, 40 if L == 121 else 150, check=True)
+    assert not tr["check_failed"]
+    # every recorded pivot energy equals Eq. 1 on the pivot rebuilt from the flips
+    D = (L + 1) // 2
+    free = oracle_mod.start_free_values(9, 3, 2, D).copy()
+    assert oracle_mod.energy(oracle_mod.skew_expand(free, L)) == tr["energies"][0]
+    for i, j in enumerate(tr["flips"]):
+        free[j] = -free[j]
+        assert np_energy(oracle_mod.skew_expand(free, L)) == tr["energies"][i + 1]
+
+
+def test_batch_and_solve_round_logic(oracle_mod):
+    L, walks, wl = 21, 5, 30
+    D = (L + 1) // 2
+    b0 = oracle_mod.walk_batch(L, 4, 0, 0, walks, wl, threads=2)
+    b1 = oracle_mod.walk_batch(L, 4, 1, 0, walks, wl, threads=3)
+    for w in range(walks):
+        tr = oracle_mod.walk_trace(L, 4, w, 0, wl)
+        assert tr["best_E"] == b0["best_E"][w]
+        assert np.array_equal(tr["best_seq"], b0["best_seq"][w])
+        assert b0["evals"][w] == D * (tr["moves"] + tr["stuck"])
+    per_round = int(b0["evals"].sum())
+    # a budget of one round plus one evaluation needs exactly two rounds
+    r = oracle_mod.solve(L, [4], walks, wl, per_round + 1)
+    assert int(r["rounds"][0]) == 2
+    assert int(r["evals"][0]) == per_round + int(b1["evals"].sum())
+    allE = list(b0["best_E"]) + list(b1["best_E"])
+    best = min(allE)
+    assert int(r["best_E"][0]) == best
+    first = allE.index(best)  # earliest (round, walk) wins ties
+    src = (b0 if first < walks else b1)["best_seq"][first % walks]
+    assert np.array_equal(r["best_seq"][0], src)
+    # target energy stops at the first round boundary where it is reached
+    r2 = oracle_mod.solve(L, [4], walks, wl, 10 ** 9, target_E=int(max(allE)) + 1000)
+    assert int(r2["rounds"][0]) == 1
