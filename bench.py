@@ -1,0 +1,292 @@
+"""Benchmark: neighbour evaluations per second of the plain solver at
+L=121 (D=61), 131072 concurrent walks of 8192 steps, a budget of 1e11
+neighbour evaluations (two whole rounds), Philox seed 1 (rank r uses seed 1+r).
+
+One "step" = one whole solve (every round until the budget) through the C ABI.
+  value  : evaluations/s with inputs resident in HBM (device buffers, workspace
+           preallocated), CUDA events on the launching stream, max over ranks;
+  e2e    : the same metric through labs_walks with HOST buffers (seed upload,
+           workspace allocation and result download inside the timed region);
+  roofline: the walk kernel's bit-sliced core against the int32 ALU-pipe peak;
+  cpu_baseline: the CPU oracle on a bounded sample of the same walks.
+
+`--impl reference` times the CPU oracle (the reference arm of this project)
+on the same workload and prints the same JSON line with "impl": "reference".
+
+Multi-GPU (torchrun): each rank solves its own independent problem (weak
+scaling, no data-path collective); the host barrier and a max-reduction of the
+time are the only communication.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L = 121
+WALKS = 131072
+WALK_LEN = 8192
+BUDGET = 10 ** 11
+SEED = 1
+INT_LANES_PER_SM = 64          # int32 ALU-pipe lanes per SM per clock (LOP3/SHF/IADD3 class)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def digits_for(L):
+    T = 1
+    while (1 << T) < L - 1:
+        T += 1
+    return T
+
+
+def core_alu_ops_per_eval(L):
+    """ALU-pipe lane-ops of the bit-sliced Delta core per neighbour evaluation:
+    per 32 lags and digit plane, two masked XORs and a full adder (4 LOP3)."""
+    m = (L - 1) // 2
+    return 4.0 * digits_for(L) * m / 32.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED):
+    """The oracle on a bounded sample of the benchmark's walks, all host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n = n_walks or 8 * cores
+    t0 = time.perf_counter()
+    r = oracle.walk_batch(L, seed, 0, 0, n, walk_len, threads=cores)
+    dt = time.perf_counter() - t0
+    ev = int(r["evals"].sum())
+    return {"value": ev / dt, "unit": "neighbour_evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the %d walks of round 0 (L=%d, %d steps each), %d evaluations in %.1f s"
+                      % (n, WALKS, L, walk_len, ev, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(n_walks=args.ref_walks)
+        if i >= args.warmup:
+            steps.append(cb)
+    val = statistics.mean(s["value"] for s in steps)
+    line = {
+        "metric": "neighbour_evals_per_s", "value": val, "unit": "neighbour_evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (Philox starts, seed 1)",
+        "impl": "reference",
+        "config": {"workload": "plain_L121_131072x8192_budget1e11", "L": L, "walks": WALKS, "walk_len": WALK_LEN,
+                   "budget": BUDGET, "note": "each step: the CPU oracle on a bounded sample of the walks"},
+        "cpu_baseline": {"value": val, "unit": "neighbour_evals/s", "cores": steps[0]["cores"], "kind": "oracle",
+                         "sample": steps[0]["sample"]},
+        "e2e": {"value": val, "unit": "neighbour_evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    line["ms_per_step"] = None
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--walks", type=int, default=WALKS)
+    ap.add_argument("--walk-len", type=int, default=WALK_LEN)
+    ap.add_argument("--budget", type=int, default=BUDGET)
+    ap.add_argument("--ref-walks", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2210_15962_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.load()
+    stream = torch.cuda.Stream()
+    seed = SEED + rank
+    walks, wl, budget = args.walks, args.walk_len, args.budget
+    ws_bytes = pkg.labs_walks_workspace_size(L, 1, walks, wl)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    seeds_d = torch.tensor([seed], dtype=torch.int64, device="cuda")
+    best_seq_d = torch.zeros((1, L), dtype=torch.int8, device="cuda")
+    best_E_d = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def device_step():
+        return pkg.labs_walks_device(L, seeds_d, walks, wl, budget, best_seq_d, best_E_d, stream=stream,
+                                     workspace=ws)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        device_step()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    total_evals = 0
+    launches = 0
+    walk_ms = 0.0
+    walk_launches = 0
+    for _ in range(args.steps):
+        st = device_step()
+        total_evals += st["evals"]
+        launches += st["launches"]
+        walk_ms += st["walk_kernel_ms"]
+        walk_launches += st["walk_launches"]
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    barrier()
+
+    # ---- end to end through the public call with host buffers
+    del ws
+    torch.cuda.synchronize()
+    e2e_evals = 0
+    h2d = d2h = 0
+    pkg.labs_walks(L, [seed], walks, wl, budget)  # first call maps the allocator pool
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = pkg.labs_walks(L, [seed], walks, wl, budget)
+        e2e_evals += int(r["evals"].sum())
+    t1 = time.perf_counter()
+    barrier()
+    h2d = 8 + 8 + 8          # seed, budget, target per problem
+    d2h = L + 8 + 8 + 4 + 4  # best sequence, best E, evaluations, rounds, stop flag
+    e2e_s = t1 - t0
+
+    # ---- max over ranks, totals over ranks
+    vals = torch.tensor([dev_s, e2e_s, float(total_evals), float(e2e_evals)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = vals.clone()
+        dist.all_reduce(mx[0:2], op=dist.ReduceOp.MAX)
+        sm = vals.clone()
+        dist.all_reduce(sm[2:4], op=dist.ReduceOp.SUM)
+        vals = torch.cat([mx[0:2], sm[2:4]])
+    dev_s, e2e_s, tot_evals, tot_e2e = [float(x) for x in vals.cpu()]
+
+    if rank == 0:
+        value = tot_evals / dev_s
+        per_launch_ms = walk_ms / max(walk_launches, 1)
+        evals_per_launch = total_evals / max(walk_launches, 1)
+        achieved = evals_per_launch * core_alu_ops_per_eval(L) / (per_launch_ms / 1e3) / 1e12
+        peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        line = {
+            "metric": "neighbour_evals_per_s", "value": value, "unit": "neighbour_evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (Philox-drawn uniform +-1 starts, seed %d per rank)" % SEED,
+            "config": {"workload": "plain_L121_131072x8192_budget1e11", "L": L, "walks": walks, "walk_len": wl,
+                       "budget": budget, "rounds_per_step": int(round(total_evals / args.steps /
+                                                                     (walks * wl * ((L + 1) // 2)))),
+                       "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: %.1f GiB of visited tables per round" % (ws_bytes / 2 ** 30)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "walk_kernel<W=2,T=7,K=4>", "kernel_ms_per_launch": per_launch_ms,
+                         "ops_per_eval": core_alu_ops_per_eval(L),
+                         "peak_basis": "152 SMs x 64 lanes/clk (measured LOP3 rate) x 2070 MHz max clock"},
+            "e2e": {"value": tot_e2e / e2e_s, "unit": "neighbour_evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

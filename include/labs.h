@@ -1,0 +1,160 @@
+/*
+ * labs.h -- C ABI of a GB300 (sm_103a) solver for the skew-symmetric
+ * Low-Autocorrelation Binary Sequences problem by parallel contiguous
+ * self-avoiding walks, after Bošković, Herzog and Brest, "Parallel
+ * Self-Avoiding Walks for a Low-Autocorrelation Binary Sequences Problem"
+ * (arXiv 2210.15962).
+ *
+ * Problem (Eq. 1): for S = (s_1..s_L), s_i in {+1,-1},
+ *     C_k = sum_{i=1}^{L-k} s_i s_{i+k},  E = sum_{k=1}^{L-1} C_k^2,  F = L^2 / (2E).
+ * Search space (Eq. 2): odd L, D = (L+1)/2 free values s_1..s_D, and
+ *     s_{D+i} = (-1)^i s_{D-i}, i = 1..D-1.
+ * Walk (Eq. 3, Algorithm 2): from a random pivot P_1, each step evaluates all
+ * D neighbours (flip s_j and its mirror s_{L+1-j}) with an incremental update
+ * of the C_k, moves to the lowest-energy neighbour that is not an earlier
+ * pivot of the same walk (lowest j on ties), and records the walk's best.
+ * Rounds (Eq. 4, Algorithm 1): every round runs many independent walks; the
+ * problem's best is kept across rounds until a neighbour-evaluation budget
+ * (or a target energy) is reached.
+ *
+ * Conventions shared by every entry point:
+ *   - L is odd with LABS_L_MIN <= L <= LABS_L_MAX, otherwise LABS_EINVAL;
+ *   - sequences are int8 arrays of +1/-1 of length L (s_1 first);
+ *   - the random first pivot of walk w in round r of the problem seeded by
+ *     `seed` uses Philox4x32-10 with key (seed & 0xffffffff, seed >> 32) and
+ *     counter (w, r, b, 0); free value j takes bit j%32 of word (j/32)%4 of
+ *     block b = j/128, bit 1 meaning -1;
+ *   - one "neighbour evaluation" is one of the D flips examined at a step;
+ *     a walk that finds all neighbours visited stops ("stuck") and its last
+ *     scan counts as D evaluations;
+ *   - a round always completes; rounds continue while the evaluations done
+ *     are below step_budget and the best energy is above the target;
+ *   - all buffers are caller-owned unless stated; no call keeps a pointer to
+ *     a caller buffer after it returns, except a server (labs_serve_*),
+ *     which owns its own memory;
+ *   - no C++ exception crosses this interface; every call returns a status.
+ *
+ * Everything a call computes runs in this library's CUDA kernels on the
+ * current CUDA device.  There is no CPU fallback: without a usable GPU the
+ * calls return LABS_ECUDA.
+ */
+#ifndef LABS_H_
+#define LABS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t labs_status;
+
+#define LABS_OK 0
+#define LABS_PENDING 1      /* labs_serve_poll: request not finished yet */
+#define LABS_EINVAL (-1)    /* bad argument (L, sizes, null pointers, non +-1 values) */
+#define LABS_ENOMEM (-2)    /* device memory could not be obtained or is too small */
+#define LABS_ECUDA (-3)     /* a CUDA call failed (no device, launch error, ...) */
+#define LABS_ETIMEOUT (-4)  /* a bounded wait expired */
+#define LABS_EOVERFLOW (-5) /* a visited table ran out of slots (cannot happen with the sizes used) */
+#define LABS_ENOTFOUND (-6) /* unknown server ticket */
+#define LABS_ECHECK (-7)    /* the debug recheck found incremental and full energies different */
+#define LABS_ESHUTDOWN (-8) /* server is shutting down */
+
+#define LABS_L_MIN 5
+#define LABS_L_MAX 511
+
+/* Options of labs_walks.  Zero-initialise (or call labs_opts_init), then set
+ * what you need. */
+typedef struct labs_opts {
+  void *stream;           /* cudaStream_t to run on; NULL = legacy default stream */
+  int32_t device_buffers; /* 0: seeds, best_seq, best_E are host pointers;
+                             1: they are device pointers (stream-ordered, no
+                                host copies of inputs or outputs) */
+  int32_t recheck_every;  /* 0 = off; n > 0: every n steps each walk recomputes all
+                             C_k and E with XOR+popc (Eq. 1) and compares them with its
+                             incremental state; a mismatch makes the call return LABS_ECHECK */
+  int64_t target_E;       /* stop a problem after the first round whose best E <= target_E;
+                             < 0 = no target.  Set to -1 by labs_opts_init. */
+  int32_t max_rounds;     /* 0 = no limit; else stop every problem after this many rounds */
+  int32_t reserved0;
+  void *workspace;        /* optional device scratch of workspace_bytes bytes (e.g. from
+                             PyTorch); NULL = the library allocates and frees it itself */
+  size_t workspace_bytes;
+  uint64_t *evals_per_seed;  /* optional host (or device, if device_buffers) [n_seeds] out */
+  int32_t *rounds_per_seed;  /* optional host (or device, if device_buffers) [n_seeds] out */
+} labs_opts;
+
+/* Aggregate statistics of one call (host struct, optional). */
+typedef struct labs_stats {
+  uint64_t evals;            /* neighbour evaluations over all seeds */
+  int32_t rounds;            /* largest number of rounds any seed ran */
+  int32_t launches;          /* kernels this call launched */
+  int32_t walk_launches;     /* of which walk kernels */
+  int32_t reserved0;
+  double walk_kernel_ms;     /* sum of the walk kernels' durations (CUDA events) */
+  double device_ms;          /* first to last kernel of the call (CUDA events) */
+} labs_stats;
+
+void labs_opts_init(labs_opts *o);
+
+/* Eq. 1 energy E of one +-1 sequence of length L (1 <= L <= 65536, any L,
+ * not only skew-symmetric).  seq is a host pointer.  Returns E >= 0, or a
+ * negative labs_status (LABS_EINVAL for a bad pointer, L, or a value other
+ * than +1/-1; LABS_ECUDA on a device error). */
+int64_t labs_energy(const int8_t *seq, int32_t L);
+
+/* Eq. 1 energies of n sequences stored back to back (seqs[n*L], device
+ * pointer) into E_out[n] (device pointer), stream-ordered on `stream`.
+ * Returns LABS_EINVAL for bad sizes; a value other than +-1 is reported by
+ * a LABS_EINVAL return after the stream is synchronised when check != 0. */
+labs_status labs_energy_batch(const int8_t *seqs, int32_t n, int32_t L, int64_t *E_out, void *stream,
+                              int32_t check);
+
+/* The whole solver (Algorithm 1 around Algorithm 2) for n_seeds independent
+ * problems of the same L: rounds of walks_per_seed walks of walk_len steps,
+ * until step_budget neighbour evaluations (per seed) or opts->target_E.
+ *   seeds[n_seeds]       problem seeds;
+ *   best_seq[n_seeds*L]  out: best sequence found for each seed (+-1);
+ *   best_E[n_seeds]      out: its energy (Eq. 1);
+ *   opts                 NULL = defaults; see labs_opts;
+ *   stats                NULL or out.
+ * Limits: 1 <= n_seeds, 1 <= walks_per_seed, n_seeds*walks_per_seed <= 2^31,
+ * 1 <= walk_len <= 2^26, step_budget >= 1.  Ties between equal energies go to
+ * the earliest round, then the lowest walk index.  Returns LABS_OK,
+ * LABS_EINVAL, LABS_ENOMEM, LABS_ECUDA, LABS_ECHECK or LABS_EOVERFLOW. */
+labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
+                       int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
+                       const labs_opts *opts, labs_stats *stats);
+
+/* Device bytes labs_walks needs to run all walks of a round at once (a
+ * smaller opts->workspace makes it run each round in several launches; the
+ * minimum is what one warp of walks needs). */
+size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len);
+
+/* One round (Eq. 4) of walks 0..n_walks-1 of the problem `seed`, with
+ * per-walk results: the building block of labs_walks, exposed for checking
+ * and tracing.  Host pointers; any output may be NULL.
+ *   walk_best_E[n_walks], walk_best_seq[n_walks*L], walk_moves[n_walks],
+ *   walk_stuck[n_walks], walk_best_step[n_walks];
+ *   trace_flips[trace_count*walk_len]: the flip index chosen at every step
+ *     of walks trace_begin..trace_begin+trace_count-1 (unused tail = -1);
+ *   visited_keys[visited_cap*((D+63)/64)]: if not NULL, the free-bit keys of
+ *     every pivot of walk `visited_walk` (bit j = 1 <-> s_{j+1} = -1), one
+ *     per entry in table order, and *visited_count = how many.
+ * Returns like labs_walks. */
+labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
+                           int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
+                           int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
+                           int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
+                           int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
+                           int32_t *visited_count);
+
+/* Human-readable name of a status code (static string). */
+const char *labs_status_str(labs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABS_H_ */

@@ -1,0 +1,258 @@
+"""GB300 (sm_103a) parallel self-avoiding walks for skew-symmetric LABS.
+
+Thin Python binding of the C ABI in ``include/labs.h`` (same names).  This
+module only marshals arguments: every step of the solver runs in the CUDA
+kernels of ``liblabs_gb300.so``.  There is no CPU fallback; if the library
+has not been built (``python -m paper_2210_15962_gb300.build``) or no CUDA
+device is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+LABS_OK = 0
+LABS_PENDING = 1
+LABS_EINVAL = -1
+LABS_ENOMEM = -2
+LABS_ECUDA = -3
+LABS_ETIMEOUT = -4
+LABS_EOVERFLOW = -5
+LABS_ENOTFOUND = -6
+LABS_ECHECK = -7
+LABS_ESHUTDOWN = -8
+LABS_L_MIN = 5
+LABS_L_MAX = 511
+
+
+class LabsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, status_str(status) if _lib else "?", status))
+
+
+class labs_opts(ctypes.Structure):
+    _fields_ = [
+        ("stream", ctypes.c_void_p),
+        ("device_buffers", ctypes.c_int32),
+        ("recheck_every", ctypes.c_int32),
+        ("target_E", ctypes.c_int64),
+        ("max_rounds", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("evals_per_seed", ctypes.c_void_p),
+        ("rounds_per_seed", ctypes.c_void_p),
+    ]
+
+
+class labs_stats(ctypes.Structure):
+    _fields_ = [
+        ("evals", ctypes.c_uint64),
+        ("rounds", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("walk_launches", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("walk_kernel_ms", ctypes.c_double),
+        ("device_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if not f[0].startswith("reserved")}
+
+
+_lib = None
+
+_EXPORTS = {
+    # name: (restype, argtypes)
+    "labs_opts_init": (None, [ctypes.POINTER(labs_opts)]),
+    "labs_status_str": (ctypes.c_char_p, [ctypes.c_int32]),
+    "labs_energy": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int32]),
+    "labs_energy_batch": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int32]),
+    "labs_walks": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(labs_opts),
+                                    ctypes.POINTER(labs_stats)]),
+    "labs_walks_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "labs_saw_round": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_void_p]),
+}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load():
+    """Load liblabs_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblabs_gb300.so is not built; run `python -m paper_2210_15962_gb300.build` "
+                               "(needs nvcc with sm_103a support)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return load().labs_status_str(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != LABS_OK:
+        raise LabsError(status, what)
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def labs_energy(seq) -> int:
+    """Eq. 1 energy of one +-1 sequence (host array), computed on the GPU."""
+    s = np.ascontiguousarray(seq, dtype=np.int8)
+    e = load().labs_energy(_ptr(s), s.size)
+    if e < 0:
+        raise LabsError(int(e), "labs_energy")
+    return int(e)
+
+
+def labs_energy_batch(seqs, stream=None, check: bool = True):
+    """Eq. 1 energies of a (n, L) int8 CUDA tensor, returned as an int64 CUDA tensor."""
+    import torch
+    if not (isinstance(seqs, torch.Tensor) and seqs.is_cuda and seqs.dtype == torch.int8 and seqs.dim() == 2):
+        raise ValueError("seqs must be a 2-D int8 CUDA tensor")
+    seqs = seqs.contiguous()
+    out = torch.empty(seqs.shape[0], dtype=torch.int64, device=seqs.device)
+    st = stream if stream is not None else torch.cuda.current_stream(seqs.device)
+    _check(load().labs_energy_batch(ctypes.c_void_p(seqs.data_ptr()), seqs.shape[0], seqs.shape[1],
+                                    ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream), int(check)),
+           "labs_energy_batch")
+    return out
+
+
+def make_opts(stream=None, device_buffers=False, recheck_every=0, target_E=-1, max_rounds=0, workspace=None,
+              evals_per_seed=None, rounds_per_seed=None) -> labs_opts:
+    o = labs_opts()
+    load().labs_opts_init(ctypes.byref(o))
+    if stream is not None:
+        o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    o.device_buffers = int(bool(device_buffers))
+    o.recheck_every = int(recheck_every)
+    o.target_E = int(target_E)
+    o.max_rounds = int(max_rounds)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    if evals_per_seed is not None:
+        o.evals_per_seed = ctypes.c_void_p(evals_per_seed.data_ptr() if hasattr(evals_per_seed, "data_ptr")
+                                           else evals_per_seed.ctypes.data)
+    if rounds_per_seed is not None:
+        o.rounds_per_seed = ctypes.c_void_p(rounds_per_seed.data_ptr() if hasattr(rounds_per_seed, "data_ptr")
+                                            else rounds_per_seed.ctypes.data)
+    return o
+
+
+def labs_walks_workspace_size(L: int, n_seeds: int, walks_per_seed: int, walk_len: int) -> int:
+    return int(load().labs_walks_workspace_size(L, n_seeds, walks_per_seed, walk_len))
+
+
+def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, *, target_E: int = -1,
+               max_rounds: int = 0, recheck_every: int = 0, stream=None, workspace=None) -> dict:
+    """Algorithm 1 around Algorithm 2 for every seed; host buffers in and out.
+
+    Returns dict(best_seq=(n, L) int8, best_E=(n,) int64, evals=(n,) uint64,
+    rounds=(n,) int32, stats=dict).
+    """
+    sd = np.ascontiguousarray(np.atleast_1d(np.asarray(seeds, dtype=np.uint64)))
+    n = sd.size
+    best_seq = np.zeros((n, L), dtype=np.int8)
+    best_E = np.zeros(n, dtype=np.int64)
+    evals = np.zeros(n, dtype=np.uint64)
+    rounds = np.zeros(n, dtype=np.int32)
+    o = make_opts(stream=stream, recheck_every=recheck_every, target_E=target_E, max_rounds=max_rounds,
+                  workspace=workspace, evals_per_seed=evals, rounds_per_seed=rounds)
+    stats = labs_stats()
+    _check(load().labs_walks(L, _ptr(sd), n, walks_per_seed, walk_len, step_budget, _ptr(best_seq), _ptr(best_E),
+                             ctypes.byref(o), ctypes.byref(stats)), "labs_walks")
+    return {"best_seq": best_seq, "best_E": best_E, "evals": evals, "rounds": rounds, "stats": stats.as_dict()}
+
+
+def labs_walks_device(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, best_seq, best_E, *,
+                      target_E: int = -1, max_rounds: int = 0, recheck_every: int = 0, stream=None,
+                      workspace=None, evals_per_seed=None, rounds_per_seed=None) -> dict:
+    """labs_walks on device-resident buffers (torch CUDA tensors): seeds int64/uint64 (n,),
+    best_seq int8 (n, L), best_E int64 (n,).  Stream-ordered; returns the call's stats."""
+    o = make_opts(stream=stream, device_buffers=True, recheck_every=recheck_every, target_E=target_E,
+                  max_rounds=max_rounds, workspace=workspace, evals_per_seed=evals_per_seed,
+                  rounds_per_seed=rounds_per_seed)
+    stats = labs_stats()
+    _check(load().labs_walks(L, ctypes.c_void_p(seeds.data_ptr()), seeds.numel(), walks_per_seed, walk_len,
+                             step_budget, ctypes.c_void_p(best_seq.data_ptr()), ctypes.c_void_p(best_E.data_ptr()),
+                             ctypes.byref(o), ctypes.byref(stats)), "labs_walks")
+    return stats.as_dict()
+
+
+def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, *, recheck_every: int = 0,
+                   trace_begin: int = 0, trace_count: int = 0, visited_walk: int = -1) -> dict:
+    """One round of walks 0..n_walks-1 with per-walk results (and optional traces / visited keys)."""
+    D = (L + 1) // 2
+    best_E = np.zeros(n_walks, dtype=np.int64)
+    best_seq = np.zeros((n_walks, L), dtype=np.int8)
+    moves = np.zeros(n_walks, dtype=np.int32)
+    stuck = np.zeros(n_walks, dtype=np.int32)
+    best_step = np.zeros(n_walks, dtype=np.int32)
+    trace = np.full((trace_count, walk_len), -1, dtype=np.int32) if trace_count > 0 else None
+    kout = (D + 63) // 64
+    vcap = walk_len + 1
+    visited = np.zeros((vcap, kout), dtype=np.uint64) if visited_walk >= 0 else None
+    vcount = np.zeros(1, dtype=np.int32)
+    _check(load().labs_saw_round(L, seed, round_, n_walks, walk_len, recheck_every, _ptr(best_E), _ptr(best_seq),
+                                 _ptr(moves), _ptr(stuck), _ptr(best_step), _ptr(trace) if trace is not None else None,
+                                 trace_begin, trace_count, visited_walk,
+                                 _ptr(visited) if visited is not None else None, vcap,
+                                 _ptr(vcount) if visited is not None else None), "labs_saw_round")
+    out = {"best_E": best_E, "best_seq": best_seq, "moves": moves, "stuck": stuck, "best_step": best_step}
+    if trace is not None:
+        out["trace"] = trace
+    if visited is not None:
+        out["visited"] = visited[:min(int(vcount[0]), vcap)]
+        out["visited_count"] = int(vcount[0])
+    return out
+
+
+def to_hex(seq) -> str:
+    """Table 1 encoding of a skew-symmetric sequence: its first D values, s_1 as the most
+    significant bit, +1 -> 0 and -1 -> 1, in hexadecimal."""
+    s = np.asarray(seq)
+    D = (s.size + 1) // 2
+    v = 0
+    for x in s[:D]:
+        v = (v << 1) | (1 if x < 0 else 0)
+    return "0x%X" % v
+
+
+def from_hex(hexstr: str, L: int) -> np.ndarray:
+    """Inverse of to_hex: the length-L skew-symmetric sequence (Eq. 2) of a Table 1 code."""
+    D = (L + 1) // 2
+    v = int(hexstr, 16)
+    if v >> D:
+        raise ValueError("code has more than D = %d bits" % D)
+    s = np.zeros(L, dtype=np.int8)
+    for i in range(D):
+        s[i] = -1 if (v >> (D - 1 - i)) & 1 else 1
+    c = D - 1
+    for i in range(1, D):
+        s[c + i] = -s[c - i] if i & 1 else s[c - i]
+    return s

@@ -1,0 +1,515 @@
+// Host side of the C ABI declared in include/labs.h: argument checks,
+// workspace layout, the round loop of Algorithm 1 and result copies.  All
+// arithmetic of the method runs in the kernels of walk_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/labs.h"
+#include "walk_kernels.cuh"
+
+namespace psaw {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kRoundBatch = 16;  // rounds enqueued between host checks of the stop flags
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_L(int32_t L) { return L >= LABS_L_MIN && L <= LABS_L_MAX && (L & 1); }
+
+// visited-table slots: a power of two >= 1.5 x the pivots of a walk
+uint32_t table_cap(int32_t walk_len) {
+  const uint64_t need = ((uint64_t)walk_len + 1) * 3 / 2 + 1;
+  uint64_t cap = 64;
+  while (cap < need) cap <<= 1;
+  return (uint32_t)cap;
+}
+
+// A bump allocator over one device block.
+struct Carver {
+  char *base;
+  size_t off = 0;
+  explicit Carver(void *b) : base((char *)b) {}
+  template <typename T>
+  T *take(size_t n) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off = align_up(off + n * sizeof(T));
+    return p;
+  }
+};
+
+struct Buffers {
+  int32_t *w_bestE, *w_moves, *w_stuck, *w_best_step;
+  uint32_t *w_key;
+  unsigned long long *p_evals, *p_round_best;
+  int64_t *p_bestE;
+  uint32_t *p_key;
+  int32_t *p_rounds, *p_best_round, *p_best_walk, *done;
+  uint64_t *seeds, *budget;
+  int64_t *target;
+  int8_t *best_seq;
+  int32_t *err;
+  uint64_t *tables;
+};
+
+// Lay out everything except the tables, then g_chunk tables.
+size_t carve(Buffers &b, void *base, int L, int n_seeds, size_t n_walks, size_t g_chunk, size_t table_bytes) {
+  Carver c(base);
+  b.w_bestE = c.take<int32_t>(n_walks);
+  b.w_moves = c.take<int32_t>(n_walks);
+  b.w_stuck = c.take<int32_t>(n_walks);
+  b.w_best_step = c.take<int32_t>(n_walks);
+  b.w_key = c.take<uint32_t>(n_walks * kKeyWords);
+  b.p_evals = c.take<unsigned long long>(n_seeds);
+  b.p_round_best = c.take<unsigned long long>(n_seeds);
+  b.p_bestE = c.take<int64_t>(n_seeds);
+  b.p_key = c.take<uint32_t>((size_t)n_seeds * kKeyWords);
+  b.p_rounds = c.take<int32_t>(n_seeds);
+  b.p_best_round = c.take<int32_t>(n_seeds);
+  b.p_best_walk = c.take<int32_t>(n_seeds);
+  b.done = c.take<int32_t>(n_seeds);
+  b.seeds = c.take<uint64_t>(n_seeds);
+  b.budget = c.take<uint64_t>(n_seeds);
+  b.target = c.take<int64_t>(n_seeds);
+  b.best_seq = c.take<int8_t>((size_t)n_seeds * L);
+  b.err = c.take<int32_t>(1);
+  b.tables = c.take<uint64_t>(g_chunk * (table_bytes / 8));
+  return c.off;
+}
+
+labs_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LABS_OK;
+  if (e == cudaErrorMemoryAllocation) return LABS_ENOMEM;
+  return LABS_ECUDA;
+}
+
+#define LABS_CU(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      st = cuda_status(e_);                             \
+      goto done;                                        \
+    }                                                   \
+  } while (0)
+
+// Event pairs around walk launches, summed at the end.
+struct Timer {
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t rec(cudaStream_t s) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, s);
+    ev.push_back(e);
+    return e;
+  }
+  ~Timer() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+double elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (a && b && cudaEventElapsedTime(&ms, a, b) == cudaSuccess) return ms;
+  return 0.0;
+}
+
+// Keep memory freed with cudaFreeAsync in this process's default pool of the
+// current device instead of returning it to the driver at every
+// synchronisation (a process-local allocator setting).
+void retain_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+struct RunConfig {
+  int32_t L, n_seeds, walks, walk_len, recheck_every;
+  uint64_t budget;
+  int64_t target;
+  int32_t max_rounds;
+};
+
+}  // namespace
+}  // namespace psaw
+
+using namespace psaw;
+
+extern "C" void labs_opts_init(labs_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->target_E = -1;
+}
+
+extern "C" const char *labs_status_str(labs_status s) {
+  switch (s) {
+    case LABS_OK: return "ok";
+    case LABS_PENDING: return "pending";
+    case LABS_EINVAL: return "invalid argument";
+    case LABS_ENOMEM: return "out of device memory";
+    case LABS_ECUDA: return "CUDA error";
+    case LABS_ETIMEOUT: return "timeout";
+    case LABS_EOVERFLOW: return "visited table overflow";
+    case LABS_ENOTFOUND: return "unknown ticket";
+    case LABS_ECHECK: return "recheck mismatch";
+    case LABS_ESHUTDOWN: return "server shutting down";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int64_t labs_energy(const int8_t *seq, int32_t L) {
+  if (!seq || L < 1 || L > 65536) return LABS_EINVAL;
+  int8_t *d_seq = nullptr;
+  int64_t *d_E = nullptr;
+  int32_t *d_err = nullptr;
+  int64_t E = 0;
+  int32_t err = 0;
+  labs_status st = LABS_OK;
+  LABS_CU(cudaMalloc(&d_seq, (size_t)L));
+  LABS_CU(cudaMalloc(&d_E, sizeof(int64_t)));
+  LABS_CU(cudaMalloc(&d_err, sizeof(int32_t)));
+  LABS_CU(cudaMemcpy(d_seq, seq, (size_t)L, cudaMemcpyHostToDevice));
+  LABS_CU(cudaMemset(d_err, 0, sizeof(int32_t)));
+  LABS_CU(launch_energy(d_seq, 1, L, d_E, d_err, 0));
+  LABS_CU(cudaMemcpy(&E, d_E, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  LABS_CU(cudaMemcpy(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (err) st = LABS_EINVAL;
+done:
+  cudaFree(d_seq);
+  cudaFree(d_E);
+  cudaFree(d_err);
+  return st == LABS_OK ? E : (int64_t)st;
+}
+
+extern "C" labs_status labs_energy_batch(const int8_t *seqs, int32_t n, int32_t L, int64_t *E_out, void *stream,
+                                         int32_t check) {
+  if (!seqs || !E_out || n < 0 || L < 1 || L > 65536) return LABS_EINVAL;
+  if (n == 0) return LABS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  labs_status st = LABS_OK;
+  int32_t *d_err = nullptr;
+  int32_t err = 0;
+  LABS_CU(cudaMallocAsync(&d_err, sizeof(int32_t), s));
+  LABS_CU(cudaMemsetAsync(d_err, 0, sizeof(int32_t), s));
+  LABS_CU(launch_energy(seqs, n, L, E_out, d_err, s));
+  if (check) {
+    LABS_CU(cudaMemcpyAsync(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LABS_CU(cudaStreamSynchronize(s));
+    if (err) st = LABS_EINVAL;
+  }
+done:
+  if (d_err) cudaFreeAsync(d_err, s);
+  return st;
+}
+
+extern "C" size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {
+  if (!valid_L(L) || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1) return 0;
+  const size_t n_walks = (size_t)n_seeds * (size_t)walks_per_seed;
+  const size_t tb = (size_t)table_cap(walk_len) * key_words64((L + 1) / 2) * 8;
+  Buffers b;
+  return carve(b, nullptr, L, n_seeds, n_walks, n_walks, tb);
+}
+
+namespace psaw {
+namespace {
+
+// Shared driver of labs_walks and labs_saw_round.
+struct Run {
+  RunConfig cfg;
+  cudaStream_t s = 0;
+  void *ws = nullptr;
+  bool own_ws = false;
+  Buffers b{};
+  size_t n_walks = 0, g_chunk = 0, table_bytes = 0;
+  uint32_t cap = 0;
+  int kw64 = 0, W = 0;
+  int launches = 0, walk_launches = 0;
+  double walk_ms = 0.0;
+  Timer timer;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> walk_ev;
+
+  labs_status setup(void *user_ws, size_t user_bytes) {
+    const int D = (cfg.L + 1) / 2;
+    W = lag_words(cfg.L);
+    cap = table_cap(cfg.walk_len);
+    kw64 = key_words64(D);
+    table_bytes = (size_t)cap * kw64 * 8;
+    n_walks = (size_t)cfg.n_seeds * (size_t)cfg.walks;
+    const size_t fixed = carve(b, nullptr, cfg.L, cfg.n_seeds, n_walks, 0, table_bytes);
+    if (user_ws) {
+      if (user_bytes < fixed + table_bytes) return LABS_ENOMEM;
+      g_chunk = std::min(n_walks, (user_bytes - fixed) / table_bytes);
+      if (g_chunk < n_walks && g_chunk > 32) g_chunk = g_chunk / 32 * 32;
+      ws = user_ws;
+    } else {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return LABS_ECUDA;
+      const size_t budget = free_b / 10 * 9;
+      if (budget < fixed + table_bytes) return LABS_ENOMEM;
+      g_chunk = std::min(n_walks, (budget - fixed) / table_bytes);
+      if (g_chunk < n_walks && g_chunk > 32) g_chunk = g_chunk / 32 * 32;
+      const size_t bytes = carve(b, nullptr, cfg.L, cfg.n_seeds, n_walks, g_chunk, table_bytes);
+      retain_pool_memory();
+      if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) return LABS_ENOMEM;
+      own_ws = true;
+    }
+    carve(b, ws, cfg.L, cfg.n_seeds, n_walks, g_chunk, table_bytes);
+    return LABS_OK;
+  }
+
+  WalkParams params(uint32_t round, uint32_t g_begin, uint32_t g_count) const {
+    WalkParams p{};
+    p.L = cfg.L;
+    p.walk_len = cfg.walk_len;
+    p.walks_per_problem = cfg.walks;
+    p.n_problems = cfg.n_seeds;
+    p.round = round;
+    p.g_begin = g_begin;
+    p.g_count = g_count;
+    p.cap = cap;
+    p.kw64 = kw64;
+    p.recheck_every = cfg.recheck_every;
+    p.seeds = b.seeds;
+    p.done = b.done;
+    p.tables = b.tables;
+    p.w_bestE = b.w_bestE;
+    p.w_moves = b.w_moves;
+    p.w_stuck = b.w_stuck;
+    p.w_best_step = b.w_best_step;
+    p.w_key = b.w_key;
+    p.p_evals = b.p_evals;
+    p.p_round_best = b.p_round_best;
+    p.err = b.err;
+    return p;
+  }
+
+  cudaError_t launch_round(uint32_t round, int32_t *trace, uint32_t trace_begin, uint32_t trace_count) {
+    for (size_t g0 = 0; g0 < n_walks; g0 += g_chunk) {
+      WalkParams p = params(round, (uint32_t)g0, (uint32_t)std::min(g_chunk, n_walks - g0));
+      p.trace_flips = trace;
+      p.trace_begin = trace_begin;
+      p.trace_count = trace ? trace_count : 0;
+      cudaEvent_t e0 = timer.rec(s);
+      cudaError_t e = launch_walk_round(W, p, s);
+      cudaEvent_t e1 = timer.rec(s);
+      if (e != cudaSuccess) return e;
+      walk_ev.push_back({e0, e1});
+      ++launches;
+      ++walk_launches;
+    }
+    FinalizeParams f{};
+    f.n_problems = cfg.n_seeds;
+    f.walks_per_problem = cfg.walks;
+    f.round = round;
+    f.done = b.done;
+    f.budget = b.budget;
+    f.target = b.target;
+    f.w_key = b.w_key;
+    f.p_evals = b.p_evals;
+    f.p_round_best = b.p_round_best;
+    f.p_bestE = b.p_bestE;
+    f.p_key = b.p_key;
+    f.p_rounds = b.p_rounds;
+    f.p_best_round = b.p_best_round;
+    f.p_best_walk = b.p_best_walk;
+    ++launches;
+    return launch_finalize(f, s);
+  }
+
+  cudaError_t init_problems(const uint64_t *seeds_src, cudaMemcpyKind kind) {
+    std::vector<uint64_t> bud(cfg.n_seeds, cfg.budget);
+    std::vector<int64_t> tgt(cfg.n_seeds, cfg.target);
+    cudaError_t e = cudaMemcpyAsync(b.seeds, seeds_src, sizeof(uint64_t) * cfg.n_seeds, kind, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.budget, bud.data(), sizeof(uint64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.target, tgt.data(), sizeof(int64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) {
+      ++launches;
+      e = launch_init_problems(cfg.n_seeds, b.p_bestE, b.p_evals, b.p_round_best, b.done, b.p_rounds,
+                               b.p_best_round, b.p_best_walk, b.p_key, s);
+    }
+    // pageable copies above complete before returning; keep host vectors alive until then
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  }
+
+  labs_status error_status() {
+    int32_t err = 0;
+    if (cudaMemcpyAsync(&err, b.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LABS_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LABS_ECUDA;
+    if (err & kErrOverflow) return LABS_EOVERFLOW;
+    if (err & kErrRecheck) return LABS_ECHECK;
+    return LABS_OK;
+  }
+
+  void finish_timing() {
+    for (auto &pr : walk_ev) walk_ms += elapsed(pr.first, pr.second);
+  }
+
+  ~Run() {
+    if (own_ws && ws) cudaFreeAsync(ws, s);
+  }
+};
+
+}  // namespace
+}  // namespace psaw
+
+extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
+                                  int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
+                                  const labs_opts *opts_in, labs_stats *stats) {
+  labs_opts opts;
+  if (opts_in) opts = *opts_in;
+  else labs_opts_init(&opts);
+  if (!valid_L(L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1 ||
+      walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0)
+    return LABS_EINVAL;
+  if ((uint64_t)n_seeds * (uint64_t)walks_per_seed > (1ull << 31)) return LABS_EINVAL;
+  labs_status st = LABS_OK;
+  Run run;
+  run.cfg = RunConfig{L, n_seeds, walks_per_seed, walk_len, opts.recheck_every, step_budget, opts.target_E,
+                      opts.max_rounds};
+  run.s = (cudaStream_t)opts.stream;
+  const cudaMemcpyKind in_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind out_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const uint64_t full_round = (uint64_t)walks_per_seed * (uint64_t)walk_len * (uint64_t)((L + 1) / 2);
+  uint64_t est = (step_budget + full_round - 1) / full_round;
+  if (opts.max_rounds > 0) est = std::min<uint64_t>(est, (uint64_t)opts.max_rounds);
+  uint32_t round = 0;
+  std::vector<int32_t> done_h(n_seeds);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+
+  st = run.setup(opts.workspace, opts.workspace_bytes);
+  if (st != LABS_OK) return st;
+  LABS_CU(run.init_problems(seeds, in_kind));
+  t0 = run.timer.rec(run.s);
+  for (;;) {
+    // rounds are enqueued speculatively (a finished problem's later rounds are
+    // no-ops on the device), at most kRoundBatch before the host looks again
+    const uint32_t stop = (uint32_t)std::min<uint64_t>(est, (uint64_t)round + kRoundBatch);
+    for (; round < stop; ++round) LABS_CU(run.launch_round(round, nullptr, 0, 0));
+    LABS_CU(cudaMemcpyAsync(done_h.data(), run.b.done, sizeof(int32_t) * n_seeds, cudaMemcpyDeviceToHost, run.s));
+    LABS_CU(cudaStreamSynchronize(run.s));
+    bool all = true;
+    for (int i = 0; i < n_seeds; ++i) all = all && done_h[i];
+    if (all || (opts.max_rounds > 0 && round >= (uint32_t)opts.max_rounds)) break;
+    if (round >= est) est = round + 1;
+  }
+  ++run.launches;
+  LABS_CU(launch_expand(n_seeds, L, run.b.p_key, kKeyWords, run.b.best_seq, run.s));
+  t1 = run.timer.rec(run.s);
+  LABS_CU(cudaMemcpyAsync(best_seq, run.b.best_seq, (size_t)n_seeds * L, out_kind, run.s));
+  LABS_CU(cudaMemcpyAsync(best_E, run.b.p_bestE, sizeof(int64_t) * n_seeds, out_kind, run.s));
+  if (opts.evals_per_seed)
+    LABS_CU(cudaMemcpyAsync(opts.evals_per_seed, run.b.p_evals, sizeof(uint64_t) * n_seeds, out_kind, run.s));
+  if (opts.rounds_per_seed)
+    LABS_CU(cudaMemcpyAsync(opts.rounds_per_seed, run.b.p_rounds, sizeof(int32_t) * n_seeds, out_kind, run.s));
+  st = run.error_status();
+  if (st != LABS_OK) goto done;
+  if (stats) {
+    std::vector<unsigned long long> ev(n_seeds);
+    std::vector<int32_t> rounds(n_seeds);
+    LABS_CU(cudaMemcpyAsync(ev.data(), run.b.p_evals, sizeof(uint64_t) * n_seeds, cudaMemcpyDeviceToHost, run.s));
+    LABS_CU(cudaMemcpyAsync(rounds.data(), run.b.p_rounds, sizeof(int32_t) * n_seeds, cudaMemcpyDeviceToHost, run.s));
+    LABS_CU(cudaStreamSynchronize(run.s));
+    run.finish_timing();
+    std::memset(stats, 0, sizeof(*stats));
+    for (int i = 0; i < n_seeds; ++i) {
+      stats->evals += ev[i];
+      stats->rounds = std::max(stats->rounds, rounds[i]);
+    }
+    stats->launches = run.launches;
+    stats->walk_launches = run.walk_launches;
+    stats->walk_kernel_ms = run.walk_ms;
+    stats->device_ms = elapsed(t0, t1);
+  }
+done:
+  if (st == LABS_OK) {
+    cudaError_t e = cudaStreamSynchronize(run.s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  return st;
+}
+
+extern "C" labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
+                                      int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
+                                      int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
+                                      int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
+                                      int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
+                                      int32_t *visited_count) {
+  if (!valid_L(L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0) return LABS_EINVAL;
+  if (trace_flips && (trace_begin < 0 || trace_count < 0 || trace_begin + trace_count > n_walks)) return LABS_EINVAL;
+  if (visited_keys && (visited_walk < 0 || visited_walk >= n_walks || visited_cap < 0 || !visited_count))
+    return LABS_EINVAL;
+  const int D = (L + 1) / 2;
+  labs_status st = LABS_OK;
+  Run run;
+  run.cfg = RunConfig{L, 1, n_walks, walk_len, recheck_every, ~0ull, -1, 1};
+  run.s = 0;
+  int32_t *d_trace = nullptr;
+  int8_t *d_seqs = nullptr;
+  std::vector<int32_t> i32(n_walks);
+  const size_t trace_n = trace_flips ? (size_t)trace_count * (size_t)walk_len : 0;
+
+  st = run.setup(nullptr, 0);
+  if (st != LABS_OK) return st;
+  if (run.g_chunk < (size_t)n_walks) return LABS_ENOMEM;  // the tables of the round must stay resident
+  LABS_CU(run.init_problems(&seed, cudaMemcpyHostToDevice));
+  if (trace_n) {
+    LABS_CU(cudaMalloc(&d_trace, trace_n * sizeof(int32_t)));
+    LABS_CU(cudaMemset(d_trace, 0xFF, trace_n * sizeof(int32_t)));
+  }
+  LABS_CU(run.launch_round(round, d_trace, (uint32_t)trace_begin, (uint32_t)trace_count));
+  st = run.error_status();
+  if (st != LABS_OK) goto done;
+  if (walk_best_E) {
+    LABS_CU(cudaMemcpy(i32.data(), run.b.w_bestE, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n_walks; ++i) walk_best_E[i] = i32[i];
+  }
+  if (walk_moves) LABS_CU(cudaMemcpy(walk_moves, run.b.w_moves, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost));
+  if (walk_stuck) LABS_CU(cudaMemcpy(walk_stuck, run.b.w_stuck, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost));
+  if (walk_best_step)
+    LABS_CU(cudaMemcpy(walk_best_step, run.b.w_best_step, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost));
+  if (walk_best_seq) {
+    LABS_CU(cudaMalloc(&d_seqs, (size_t)n_walks * L));
+    LABS_CU(launch_expand(n_walks, L, run.b.w_key, kKeyWords, d_seqs, 0));
+    LABS_CU(cudaMemcpy(walk_best_seq, d_seqs, (size_t)n_walks * L, cudaMemcpyDeviceToHost));
+  }
+  if (trace_n) LABS_CU(cudaMemcpy(trace_flips, d_trace, trace_n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (visited_keys) {
+    const size_t words = run.table_bytes / 8;
+    std::vector<uint64_t> tbl(words);
+    LABS_CU(cudaMemcpy(tbl.data(), run.b.tables + (size_t)visited_walk * words, run.table_bytes,
+                       cudaMemcpyDeviceToHost));
+    const int kout = (D + 63) / 64;
+    int32_t cnt = 0;
+    for (uint32_t sl = 0; sl < run.cap; ++sl) {
+      const uint64_t *e = tbl.data() + (size_t)sl * run.kw64;
+      bool empty = true;
+      for (int i = 0; i < run.kw64; ++i) empty = empty && e[i] == 0;
+      if (empty) continue;
+      if (cnt < visited_cap) {
+        for (int i = 0; i < kout; ++i) {
+          uint64_t v = e[i];
+          if ((D >> 6) == i) v &= ~(1ull << (D & 63));  // drop the occupancy flag
+          visited_keys[(size_t)cnt * kout + i] = v;
+        }
+      }
+      ++cnt;
+    }
+    *visited_count = cnt;
+  }
+done:
+  if (d_trace) cudaFree(d_trace);
+  if (d_seqs) cudaFree(d_seqs);
+  if (st == LABS_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  return st;
+}

@@ -1,0 +1,507 @@
+// Bit-sliced core of one contiguous self-avoiding walk over skew-symmetric
+// binary sequences (Bošković, Herzog, Brest, arXiv 2210.15962, Eq. 1-3 and
+// Algorithm 2).  One CUDA thread owns one walk; every array below lives in
+// that thread's registers (all indices are compile-time after unrolling).
+//
+// Notation (0-based positions a = 0..L-1; the paper's s_{a+1}):
+//   D = (L+1)/2 free positions 0..D-1, centre c = D-1, m = (L-1)/2 even lags
+//   k = 2i (i = 1..m).  Bit b(a) = 1 <-> s_a = -1.  Flip j negates position
+//   a = j and its mirror a' = L-1-j (Eq. 2), which is a itself when j = c.
+//
+// Facts used (each follows from Eq. 1 and Eq. 2):
+//   * C_k = 0 for odd k, and for even k the flip changes
+//       C_{2i} by -4 u_i,  u_i = s_a (s_{a-2i} [a-2i >= 0] + s_{a+2i} [a+2i <= L-1, a+2i != a'])
+//     (only the s_{a-2i} term for the centre), so the neighbour's energy change is
+//       Delta_j = sum_i (-4u_i)(2 C_{2i} - 4u_i) = 16 sum_i u_i^2 - 8 sum_i u_i C_{2i};
+//   * positions a and a +- 2i have the same parity, so each parity class of
+//     positions is kept as its own bit array ("cls"); the windows of bits at
+//     a-2i and a+2i over all lags i are plain shifts of that array;
+//   * every C_{2i} is odd (a sum of L-2i terms +-1), so it has a unique
+//     T-digit signed-binary form C = sum_t 2^t d_t with d_t in {-1,+1};
+//     the digit bits e_t = (d_t+1)/2 are the bits of e = (C + 2^T - 1)/2, held
+//     as T bit planes over the lags ("ep").  With x'_i = s_a s_{a-2i} = 1-2X_i,
+//       sum_{i in V} x'_i C_{2i} = 2 sum_t 2^t popc(V & (X ^ e_t)) - (2^T-1)|V|,
+//     so a neighbour costs, per 32 lags and digit plane, two masked XORs, one
+//     carry-save full adder over the two sides and one population count.
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define LABS_HD __host__ __device__ __forceinline__
+#else
+#define LABS_HD inline
+#endif
+
+namespace psaw {
+
+// ---------------------------------------------------------------- limits
+constexpr int kLMin = 5;
+constexpr int kLMax = 511;        // D <= 256 free bits, m <= 255 lags
+constexpr int kMaxWords = 8;      // 32-bit words of lags (m <= 32 * kMaxWords)
+constexpr int kKeyWords = 9;      // 32-bit words of a key (D bits + occupancy flag)
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kDeltaBias = 1 << 22;  // |Delta| < 2^21 for L <= 511
+
+LABS_HD uint32_t popc32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return (uint32_t)__popc(x);
+#else
+  return (uint32_t)__builtin_popcount(x);
+#endif
+}
+
+// low 32 bits of (hi:lo) >> s, 0 <= s <= 31
+LABS_HD uint32_t fshr(uint32_t lo, uint32_t hi, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, s);
+#else
+  s &= 31u;
+  return s ? ((lo >> s) | (hi << (32u - s))) : lo;
+#endif
+}
+
+LABS_HD uint32_t brev32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return __brev(x);
+#else
+  x = ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+  x = ((x >> 2) & 0x33333333u) | ((x & 0x33333333u) << 2);
+  x = ((x >> 4) & 0x0F0F0F0Fu) | ((x & 0x0F0F0F0Fu) << 4);
+  x = ((x >> 8) & 0x00FF00FFu) | ((x & 0x00FF00FFu) << 8);
+  return (x >> 16) | (x << 16);
+#endif
+}
+
+LABS_HD uint32_t mulhi32(uint32_t a, uint32_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// word w of the mask whose low n bits are set (n may be <= 0)
+LABS_HD uint32_t low_mask_word(int n, int w) {
+  const int s = n - 32 * w;
+  return s <= 0 ? 0u : (s >= 32 ? 0xFFFFFFFFu : ((1u << s) - 1u));
+}
+
+// Dynamic-position access to small register arrays.  Each word is selected
+// with an AND mask rather than an index so that the array stays in registers.
+LABS_HD uint32_t sel_mask(bool b) { return 0u - (uint32_t)b; }
+
+// bit `pos` of a register array
+template <int N>
+LABS_HD uint32_t get_bit(const uint32_t (&a)[N], int pos) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i) w |= a[i] & sel_mask((pos >> 5) == i);
+  return (w >> (pos & 31)) & 1u;
+}
+
+template <int N>
+LABS_HD void xor_bit(uint32_t (&a)[N], int pos, uint32_t v) {
+  const uint32_t b = v << (pos & 31);
+#pragma unroll
+  for (int i = 0; i < N; ++i) a[i] ^= b & sel_mask((pos >> 5) == i);
+}
+
+// out = bits [s, s + 32*NO) of a (zero past the end), s >= 0 dynamic
+template <int NO, int NI>
+LABS_HD void shr_dyn(uint32_t (&out)[NO], const uint32_t (&a)[NI], int s) {
+  const int ws = s >> 5;
+  const uint32_t bs = (uint32_t)(s & 31);
+#pragma unroll
+  for (int w = 0; w < NO; ++w) {
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      lo |= a[i] & sel_mask(i == w + ws);
+      hi |= a[i] & sel_mask(i == w + ws + 1);
+    }
+    out[w] = fshr(lo, hi, bs);
+  }
+}
+
+// ------------------------------------------------- Philox4x32-10 generator
+// Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of
+//   (x0,x1,x2,x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1, lo(M0 x0))
+// with the key advanced by the Weyl increments after each round.
+LABS_HD void philox4x32_10(uint32_t (&x)[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * x[0], hi0 = mulhi32(0xD2511F53u, x[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * x[2], hi1 = mulhi32(0xCD9E8D57u, x[2]);
+    const uint32_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+    x[0] = y0;
+    x[1] = lo1;
+    x[2] = y2;
+    x[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+// ----------------------------------------------------------- problem shape
+struct Geometry {
+  int L, D, c, m;
+  int N[2];      // sizes of the two parity classes (D and D-1)
+  int nfree[2];  // free positions (a < D) in each class
+  int T;         // digit planes
+};
+
+LABS_HD Geometry make_geometry(int L, int T) {
+  Geometry g;
+  g.L = L;
+  g.D = (L + 1) / 2;
+  g.c = g.D - 1;
+  g.m = (L - 1) / 2;
+  g.N[0] = g.D;
+  g.N[1] = g.D - 1;
+  g.nfree[0] = (g.D + 1) / 2;
+  g.nfree[1] = g.D / 2;
+  g.T = T;
+  return g;
+}
+
+// smallest T with 2^T - 1 >= L - 2 (the largest |C_{2i}|)
+LABS_HD int digits_for(int L) {
+  int T = 1;
+  while ((1 << T) < L - 1) ++T;
+  return T;
+}
+
+// ------------------------------------------------------------- walk state
+// W: 32-bit words of lags; T: digit planes; NS = W + 1 words per class.
+template <int W, int T>
+struct WalkState {
+  static constexpr int NS = W + 1;
+  uint32_t cls[2][NS];  // cls[q] bit t = b(2t + q)
+  uint32_t ep[T][W];    // ep[t] bit (i-1) = bit t of e_i = (C_{2i} + 2^T - 1) / 2
+  uint32_t key[NS];     // key bit j = b(j), j < D (the free half identifies a skew pivot)
+  int32_t E;            // energy of the current pivot, Eq. 1
+};
+
+// C_{2i} from the class arrays with XOR + popc on packed words: the pairs
+// (a, a+2i) inside class q are (t, t+i), t = 0..N_q-1-i, and
+// C = (#pairs) - 2 (#disagreeing pairs).  Called for i = 1, 2, ... in order;
+// sh[q] holds cls[q] >> (i-1) on entry and cls[q] >> i on return.
+template <int W, int T>
+LABS_HD int next_even_correlation(const WalkState<W, T> &st, const Geometry &g, uint32_t (&sh)[2][W + 1], int i) {
+  constexpr int NS = W + 1;
+  int C = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+#pragma unroll
+    for (int w = 0; w < NS; ++w) sh[q][w] = fshr(sh[q][w], (w + 1 < NS) ? sh[q][w + 1] : 0u, 1u);
+    const int pairs = g.N[q] - i;
+    if (pairs > 0) {
+      int dis = 0;
+#pragma unroll
+      for (int w = 0; w < NS; ++w) dis += (int)popc32((st.cls[q][w] ^ sh[q][w]) & low_mask_word(pairs, w));
+      C += pairs - 2 * dis;
+    }
+  }
+  return C;
+}
+
+// P_1 of Eq. 3: free bit j = bit (j%32) of word (j/32)%4 of
+// Philox(counter = (walk, round, j/128, 0), key = seed), 1 <-> -1; then
+// Eq. 2 fills the second half, and Eq. 1 gives C and E.
+template <int W, int T>
+LABS_HD void init_walk(WalkState<W, T> &st, const Geometry &g, uint64_t seed, uint32_t walk, uint32_t round) {
+  constexpr int NS = W + 1;
+  uint32_t blk[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int w = 0; w < NS; ++w) {
+    if ((w & 3) == 0) {
+      blk[0] = walk;
+      blk[1] = round;
+      blk[2] = (uint32_t)(w >> 2);
+      blk[3] = 0;
+      philox4x32_10(blk, (uint32_t)seed, (uint32_t)(seed >> 32));
+    }
+    st.key[w] = blk[w & 3] & low_mask_word(g.D, w);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int w = 0; w < NS; ++w) st.cls[q][w] = 0;
+  for (int a = 0; a < g.L; ++a) {
+    uint32_t b;
+    if (a < g.D) {
+      b = get_bit(st.key, a);
+    } else {
+      const int i = a - g.c;                       // s_{c+i} = (-1)^i s_{c-i}
+      b = get_bit(st.key, g.c - i) ^ (uint32_t)(i & 1);
+    }
+    if (a & 1) xor_bit(st.cls[1], a >> 1, b);
+    else xor_bit(st.cls[0], a >> 1, b);
+  }
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int w = 0; w < W; ++w) st.ep[t][w] = 0;
+  int32_t E = 0;
+  uint32_t sh[2][NS];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int w = 0; w < NS; ++w) sh[q][w] = st.cls[q][w];
+  for (int i = 1; i <= g.m; ++i) {
+    const int C = next_even_correlation(st, g, sh, i);
+    E += C * C;
+    const uint32_t e = (uint32_t)((C + (1 << T) - 1) >> 1);
+#pragma unroll
+    for (int t = 0; t < T; ++t) xor_bit(st.ep[t], i - 1, (e >> t) & 1u);
+  }
+  st.E = E;
+}
+
+// Full recheck (debug): recompute every C_{2i} with XOR + popc and E from
+// Eq. 1 and compare with the digit planes and the running E.
+template <int W, int T>
+LABS_HD bool recheck_walk(const WalkState<W, T> &st, const Geometry &g) {
+  constexpr int NS = W + 1;
+  bool ok = true;
+  int32_t E = 0;
+  uint32_t sh[2][NS];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int w = 0; w < NS; ++w) sh[q][w] = st.cls[q][w];
+  for (int i = 1; i <= g.m; ++i) {
+    const int C = next_even_correlation(st, g, sh, i);
+    E += C * C;
+    uint32_t e = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) e |= get_bit(st.ep[t], i - 1) << t;
+    ok = ok && ((int)(2 * e) - ((1 << T) - 1) == C);
+  }
+  return ok && (E == st.E);
+}
+
+// insert x into the ascending list top[0..K-1] (the largest drops off)
+template <int K>
+LABS_HD void top_insert(uint32_t (&top)[K], uint32_t x) {
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    const uint32_t lo = top[r] < x ? top[r] : x;
+    x = top[r] < x ? x : top[r];
+    top[r] = lo;
+  }
+}
+
+// Delta_j of every flip j of the pivot (Algorithm 2, CalculateNeighborhoodDelta)
+// and the K smallest packed keys ((Delta_j + bias) << 8 | j) that are >= floor,
+// skipping j == jprev (the previous pivot, always visited).
+template <int W, int T, int K>
+LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, int jprev, uint32_t floor,
+                             uint32_t (&top)[K]) {
+  constexpr int NS = W + 1;
+#pragma unroll
+  for (int r = 0; r < K; ++r) top[r] = kNone;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int Nq = g.N[q];
+    uint32_t F[W], B[W], Vx[W], Vy[W], Pm[W];
+    // F bit (i-1) = b at class index t+i; B bit (i-1) = b at class index t-i
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      F[w] = fshr(st.cls[q][w], st.cls[q][w + 1], 1u);
+      B[w] = 0;
+      Vx[w] = 0;
+      Vy[w] = low_mask_word(Nq - 1, w);
+      // pair lag i0 = c - a of the flip's own mirror: bit (c - q - 1) at t = 0
+      Pm[w] = ((g.c - q - 1) >> 5) == w ? (1u << ((g.c - q - 1) & 31)) : 0u;
+    }
+    uint32_t ba = st.cls[q][0] & 1u;
+    (void)NS;
+    for (int t = 0; t < g.nfree[q]; ++t) {
+      const int a = 2 * t + q;
+      const bool centre = (a == g.c);
+      const uint32_t bm = 0u - ba;
+      int accq = 0, accr = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        const uint32_t X = B[w] ^ bm;
+        const uint32_t Y = F[w] ^ bm;
+        const uint32_t vx = Vx[w];
+        const uint32_t vy = centre ? 0u : (Vy[w] & ~Pm[w]);
+        uint32_t carry = 0;
+#pragma unroll
+        for (int tt = 0; tt < T; ++tt) {
+          const uint32_t A = vx & (X ^ st.ep[tt][w]);
+          const uint32_t Bv = vy & (Y ^ st.ep[tt][w]);
+          const uint32_t s = A ^ Bv ^ carry;
+          carry = (A & Bv) | (carry & (A ^ Bv));
+          accq += (int)popc32(s) << tt;
+        }
+        accq += (int)popc32(carry) << T;
+        accr += (int)popc32(vx & vy & (X ^ Y));
+      }
+      const int nx = t;
+      const int ny = centre ? 0 : (Nq - 2 - t);
+      int nxy = 0;
+      if (!centre) {
+        const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
+        nxy = lim - ((g.c - a) <= lim ? 1 : 0);
+      }
+      const int Q = 2 * accq - ((1 << T) - 1) * (nx + ny);  // sum u_i C_{2i}
+      const int R = nx + ny + 2 * (nxy - 2 * accr);          // sum u_i^2
+      const int delta = 16 * R - 8 * Q;
+      uint32_t x = ((uint32_t)(delta + kDeltaBias) << 8) | (uint32_t)a;
+      x = (a == jprev || x < floor) ? kNone : x;
+      top_insert(top, x);
+      // advance to t + 1
+#pragma unroll
+      for (int w = W - 1; w >= 0; --w) {
+        B[w] = (B[w] << 1) | (w ? (B[w - 1] >> 31) : ba);
+        Vx[w] = (Vx[w] << 1) | (w ? (Vx[w - 1] >> 31) : 1u);
+      }
+      ba = F[0] & 1u;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        F[w] = fshr(F[w], (w + 1 < W) ? F[w + 1] : 0u, 1u);
+        Vy[w] = fshr(Vy[w], (w + 1 < W) ? Vy[w + 1] : 0u, 1u);
+        Pm[w] = fshr(Pm[w], (w + 1 < W) ? Pm[w + 1] : 0u, 2u);
+      }
+    }
+  }
+}
+
+LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }
+LABS_HD int key_delta(uint32_t k) { return (int)(k >> 8) - kDeltaBias; }
+
+// Move to the neighbour of flip a (Algorithm 2, UpdateData): C_{2i} -= 4 u_i
+// on the digit planes by a bit-sliced add, E += delta, and flip the bits.
+template <int W, int T>
+LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta) {
+  constexpr int NS = W + 1;
+  const int q = a & 1, t = a >> 1;
+  const int Nq = g.D - q;  // class size N_q without indexing g.N
+  const bool centre = (a == g.c);
+  uint32_t cq[NS];  // the flip's parity class, selected without dynamic indexing
+  const uint32_t mq = sel_mask(q != 0);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) cq[w] = (st.cls[1][w] & mq) | (st.cls[0][w] & ~mq);
+  const uint32_t ba = get_bit(cq, t);
+  const uint32_t bm = 0u - ba;
+  // Y window: class bits t+1 .. ; X window: class bits t-1, t-2, .. via a full bit reversal
+  uint32_t F[W], R[NS], X[W];
+  shr_dyn(F, cq, t + 1);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) R[w] = brev32(cq[NS - 1 - w]);
+  shr_dyn(X, R, 32 * NS - t);
+  const int i0 = g.c - a;  // pair lag excluded from the y side
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t vx = low_mask_word(t, w);
+    uint32_t vy = centre ? 0u : low_mask_word(Nq - 1 - t, w);
+    if (!centre && ((i0 - 1) >> 5) == w) vy &= ~(1u << ((i0 - 1) & 31));
+    const uint32_t Xw = X[w] ^ bm, Yw = F[w] ^ bm;
+    // g_x = -x' in {-1,0,1}: bit0 = vx, sign bits = vx & ~X (X=1 -> +1, X=0 -> -1)
+    const uint32_t x0 = vx, xs = vx & ~Xw;
+    const uint32_t y0 = vy, ys = vy & ~Yw;
+    // d = g_x + g_y in [-2, 2], three-bit two's complement
+    const uint32_t d0 = x0 ^ y0;
+    const uint32_t c1 = x0 & y0;
+    const uint32_t d1 = xs ^ ys ^ c1;
+    const uint32_t c2 = (xs & ys) | (c1 & (xs ^ ys));
+    const uint32_t d2 = xs ^ ys ^ c2;
+    // e += 2 d over T planes (addend planes: 0, d0, d1, d2, d2, ...)
+    uint32_t carry = 0;
+#pragma unroll
+    for (int tt = 1; tt < T; ++tt) {
+      const uint32_t add = tt == 1 ? d0 : (tt == 2 ? d1 : d2);
+      const uint32_t e = st.ep[tt][w];
+      st.ep[tt][w] = e ^ add ^ carry;
+      carry = (e & add) | (carry & (e ^ add));
+    }
+  }
+  st.E += delta;
+  xor_bit(cq, t, 1u);
+  if (!centre) xor_bit(cq, (g.L - 1 - a - q) >> 1, 1u);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) {
+    st.cls[0][w] = (st.cls[0][w] & mq) | (cq[w] & ~mq);
+    st.cls[1][w] = (cq[w] & mq) | (st.cls[1][w] & ~mq);
+  }
+  xor_bit(st.key, a, 1u);
+}
+
+// ------------------------------------------------------ visited hash table
+// Open addressing with linear probing over `cap` (power of two) slots of
+// KW64 64-bit words; a slot stores the D key bits plus an occupancy flag at
+// bit D, and an all-zero slot is empty.  The hash is the MurmurHash3 32-bit
+// finaliser (Appleby) applied to a multiplicative fold of the key words.
+template <int NS>
+LABS_HD uint32_t hash_key(const uint32_t (&k)[NS]) {
+  uint32_t h = 0x2545F491u;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) h = (h ^ k[w]) * 0x9E3779B1u + (uint32_t)w;
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Look key up in the table; returns true if present, else false with *slot =
+// the empty slot where it would be inserted.  *probes counts slots read;
+// returns false with *slot = kNone if the table is full (cannot happen when
+// cap exceeds the walk's pivot count, but is reported as an overflow).
+template <int NS>
+LABS_HD bool table_find(const uint64_t *table, uint32_t cap, int KW64, const uint32_t (&k)[NS], int D,
+                        uint32_t *slot) {
+  uint64_t want[(NS + 1) / 2 + 1];
+#pragma unroll
+  for (int i = 0; i < (NS + 1) / 2 + 1; ++i) {
+    const uint32_t lo = 2 * i < NS ? k[2 * i] : 0u;
+    const uint32_t hi = 2 * i + 1 < NS ? k[2 * i + 1] : 0u;
+    want[i] = ((uint64_t)hi << 32) | lo;
+  }
+  // occupancy flag at bit D
+#pragma unroll
+  for (int i = 0; i < (NS + 1) / 2 + 1; ++i) want[i] |= ((D >> 6) == i) ? (1ull << (D & 63)) : 0ull;
+  uint32_t idx = hash_key(k) & (cap - 1u);
+  for (uint32_t n = 0; n < cap; ++n) {
+    const uint64_t *s = table + (size_t)idx * KW64;
+    bool empty = true, equal = true;
+#pragma unroll
+    for (int i = 0; i < (NS + 1) / 2 + 1; ++i) {
+      if (i < KW64) {
+        const uint64_t v = s[i];
+        empty = empty && (v == 0);
+        equal = equal && (v == want[i]);
+      }
+    }
+    if (equal) return true;
+    if (empty) {
+      *slot = idx;
+      return false;
+    }
+    idx = (idx + 1u) & (cap - 1u);
+  }
+  *slot = kNone;
+  return false;
+}
+
+template <int NS>
+LABS_HD void table_store(uint64_t *table, uint32_t slot, int KW64, const uint32_t (&k)[NS], int D) {
+  uint64_t *s = table + (size_t)slot * KW64;
+#pragma unroll
+  for (int i = 0; i < (NS + 1) / 2 + 1; ++i) {
+    if (i < KW64) {
+      const uint32_t lo = 2 * i < NS ? k[2 * i] : 0u;
+      const uint32_t hi = 2 * i + 1 < NS ? k[2 * i + 1] : 0u;
+      s[i] = (((uint64_t)hi << 32) | lo) | (((D >> 6) == i) ? (1ull << (D & 63)) : 0ull);
+    }
+  }
+}
+
+LABS_HD int key_words64(int D) { return (D + 1 + 63) / 64; }
+
+}  // namespace psaw

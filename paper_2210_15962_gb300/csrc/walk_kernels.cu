@@ -1,0 +1,286 @@
+// Kernels of one round of parallel contiguous self-avoiding walks (Eq. 4 and
+// Algorithm 2 of arXiv 2210.15962), the per-round best reduction of
+// Algorithm 1, the key -> sequence expansion (Eq. 2) and the Eq. 1 energy.
+#include <climits>
+
+#include "walk_kernels.cuh"
+
+namespace psaw {
+
+// One thread = one walk.  The warp first zeroes the visited tables of its 32
+// walks with coalesced 16-byte stores, then every lane runs its walk:
+// random P_1, then walk_len steps of "evaluate all D flips -> best unvisited
+// neighbour (ties to the lowest flip) -> insert -> update C, E -> keep the
+// strict best".  The candidate scan keeps the kTopK smallest (Delta, flip)
+// keys; if all of them are visited it rescans above the last one, so the
+// choice is exactly the minimum over unvisited neighbours.
+template <int W, int T, int K>
+__global__ void __launch_bounds__(kWalkBlock) walk_kernel(const WalkParams p) {
+  constexpr int NS = W + 1;
+  const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
+  const uint32_t gw = p.g_begin + lid;
+  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
+  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
+  const bool live = lid < p.g_count && !(p.done && p.done[prob]);
+  {
+    const uint32_t first = lid - (uint32_t)lane;
+    const uint32_t live_lanes = __ballot_sync(0xFFFFFFFFu, live);
+    const size_t n16 = table_words / 2;
+    for (int l = 0; l < 32; ++l) {
+      const uint32_t s = first + (uint32_t)l;
+      if ((live_lanes >> l) & 1u) {
+        uint4 *base = reinterpret_cast<uint4 *>(p.tables + (size_t)s * table_words);
+        for (size_t i = (size_t)lane; i < n16; i += 32) base[i] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    __syncwarp();
+  }
+  if (!live) return;
+
+  const Geometry g = make_geometry(p.L, T);
+  WalkState<W, T> st;
+  init_walk(st, g, p.seeds[prob], walk, p.round);
+  uint64_t *table = p.tables + (size_t)lid * table_words;
+  {
+    uint32_t slot;
+    table_find(table, p.cap, p.kw64, st.key, g.D, &slot);
+    table_store(table, slot, p.kw64, st.key, g.D);
+  }
+  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
+  uint32_t best_key[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+  int32_t *trace = nullptr;
+  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
+    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
+
+  int jprev = -1;
+  for (int step = 1; step <= p.walk_len; ++step) {
+    uint32_t floor = 0;
+    int chosen = -1, cdelta = 0;
+    uint32_t cslot = 0;
+    bool need = true;
+    while (need) {
+      uint32_t top[K];
+      eval_neighbours<W, T, K>(st, g, jprev, floor, top);
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        if (need) {
+          if (top[r] == kNone) {
+            need = false;  // every neighbour not below `floor` is visited: stuck
+          } else {
+            const int a = key_flip(top[r]);
+            uint32_t nk[NS];
+#pragma unroll
+            for (int w = 0; w < NS; ++w) nk[w] = st.key[w];
+            xor_bit(nk, a, 1u);
+            uint32_t s;
+            if (!table_find(table, p.cap, p.kw64, nk, g.D, &s)) {
+              need = false;
+              if (s == kNone) {
+                atomicOr(p.err, kErrOverflow);
+              } else {
+                chosen = a;
+                cdelta = key_delta(top[r]);
+                cslot = s;
+              }
+            }
+          }
+        }
+      }
+      if (need) floor = top[K - 1] + 1u;
+    }
+    if (chosen < 0) {
+      stuck = 1;
+      break;
+    }
+    apply_move(st, g, chosen, cdelta);
+    table_store(table, cslot, p.kw64, st.key, g.D);
+    jprev = chosen;
+    moves = step;
+    if (trace) trace[step - 1] = chosen;
+    if (st.E < bestE) {
+      bestE = st.E;
+      best_step = step;
+#pragma unroll
+      for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+    }
+    if (p.recheck_every > 0 && (step % p.recheck_every) == 0 && !recheck_walk(st, g)) atomicOr(p.err, kErrRecheck);
+  }
+  p.w_bestE[gw] = bestE;
+  p.w_moves[gw] = moves;
+  p.w_stuck[gw] = stuck;
+  p.w_best_step[gw] = best_step;
+#pragma unroll
+  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? best_key[w] : 0u;
+  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(moves + stuck));
+  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)bestE << 32) | walk);
+}
+
+// digit planes used for lag-word class W (covers every L with m <= 32W)
+template <int W>
+struct PlanesFor {
+  static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
+};
+
+template <int W>
+static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
+  constexpr int T = PlanesFor<W>::value;
+  const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
+  walk_kernel<W, T, kTopK><<<blocks, kWalkBlock, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_round(int W, const WalkParams &p, cudaStream_t s) {
+  if (p.g_count == 0) return cudaSuccess;
+  switch (W) {
+    case 1: return launch_w<1>(p, s);
+    case 2: return launch_w<2>(p, s);
+    case 3: return launch_w<3>(p, s);
+    case 4: return launch_w<4>(p, s);
+    case 5: return launch_w<5>(p, s);
+    case 6: return launch_w<6>(p, s);
+    case 7: return launch_w<7>(p, s);
+    case 8: return launch_w<8>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Algorithm 1's per-round bookkeeping, one thread per problem: a round best
+// strictly below the running best replaces it (so the earliest round wins
+// ties, and inside a round the lowest walk index wins through the atomicMin
+// key); then the budget / target stop rule is applied.
+__global__ void finalize_kernel(const FinalizeParams f) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= f.n_problems || f.done[p]) return;
+  const unsigned long long rb = f.p_round_best[p];
+  f.p_round_best[p] = ~0ull;
+  if (rb != ~0ull) {
+    const int64_t E = (int64_t)(rb >> 32);
+    const uint32_t w = (uint32_t)(rb & 0xFFFFFFFFu);
+    if (E < f.p_bestE[p]) {
+      f.p_bestE[p] = E;
+      const size_t gw = (size_t)p * (size_t)f.walks_per_problem + w;
+      for (int i = 0; i < kKeyWords; ++i) f.p_key[(size_t)p * kKeyWords + i] = f.w_key[gw * kKeyWords + i];
+      f.p_best_round[p] = (int32_t)f.round;
+      f.p_best_walk[p] = (int32_t)w;
+    }
+  }
+  f.p_rounds[p] = (int32_t)f.round + 1;
+  if (f.p_evals[p] >= f.budget[p] || (f.target[p] >= 0 && f.p_bestE[p] <= f.target[p])) f.done[p] = 1;
+}
+
+cudaError_t launch_finalize(const FinalizeParams &f, cudaStream_t s) {
+  finalize_kernel<<<(f.n_problems + 127) / 128, 128, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+__global__ void init_problems_kernel(int n, int64_t *p_bestE, unsigned long long *p_evals,
+                                     unsigned long long *p_round_best, int32_t *done, int32_t *p_rounds,
+                                     int32_t *p_best_round, int32_t *p_best_walk, uint32_t *p_key) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  p_bestE[p] = INT64_MAX;
+  p_evals[p] = 0;
+  p_round_best[p] = ~0ull;
+  done[p] = 0;
+  p_rounds[p] = 0;
+  p_best_round[p] = -1;
+  p_best_walk[p] = -1;
+  for (int i = 0; i < kKeyWords; ++i) p_key[(size_t)p * kKeyWords + i] = 0u;
+}
+
+cudaError_t launch_init_problems(int n, int64_t *p_bestE, unsigned long long *p_evals,
+                                 unsigned long long *p_round_best, int32_t *done, int32_t *p_rounds,
+                                 int32_t *p_best_round, int32_t *p_best_walk, uint32_t *p_key, cudaStream_t s) {
+  init_problems_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, p_bestE, p_evals, p_round_best, done, p_rounds,
+                                                      p_best_round, p_best_walk, p_key);
+  return cudaGetLastError();
+}
+
+// Eq. 2: sequence s_0..s_{L-1} (+1/-1) from the D key bits (bit 1 <-> -1).
+__global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * (size_t)L) return;
+  const int p = (int)(idx / (size_t)L);
+  const int a = (int)(idx - (size_t)p * (size_t)L);
+  const int c = (L - 1) / 2;
+  const uint32_t *k = keys + (size_t)p * key_stride;
+  uint32_t b;
+  if (a <= c) {
+    b = (k[a >> 5] >> (a & 31)) & 1u;
+  } else {
+    const int i = a - c, src = c - i;
+    b = ((k[src >> 5] >> (src & 31)) & 1u) ^ (uint32_t)(i & 1);
+  }
+  seq_out[(size_t)p * L + a] = b ? (int8_t)-1 : (int8_t)1;
+}
+
+cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t total = (size_t)n * (size_t)L;
+  expand_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, keys, key_stride, seq_out);
+  return cudaGetLastError();
+}
+
+// Eq. 1 for arbitrary +-1 sequences: one warp per sequence, the sequence
+// bit-packed in shared memory, lanes split the lags, each C_k by XOR + popc
+// of the sequence against itself shifted by k.
+constexpr int kEnergyWarps = 4;
+
+__global__ void energy_kernel(const int8_t *seqs, int n, int L, int64_t *E_out, int32_t *err) {
+  extern __shared__ uint32_t sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seq = blockIdx.x * kEnergyWarps + warp;
+  const int NW = (L + 31) / 32;
+  uint32_t *bits = sm + (size_t)warp * (NW + 1);
+  if (seq < n) {
+    const int8_t *s = seqs + (size_t)seq * L;
+    for (int w = lane; w <= NW; w += 32) {
+      uint32_t v = 0;
+      if (w < NW) {
+        for (int b = 0; b < 32; ++b) {
+          const int pos = 32 * w + b;
+          if (pos < L) {
+            const int8_t x = s[pos];
+            if (x != 1 && x != -1) atomicOr(err, 1);
+            v |= (x < 0 ? 1u : 0u) << b;
+          }
+        }
+      }
+      bits[w] = v;
+    }
+  }
+  __syncwarp();
+  if (seq >= n) return;
+  long long acc = 0;
+  for (int k = 1 + lane; k < L; k += 32) {
+    const int pairs = L - k;
+    const int ws = k >> 5;
+    const uint32_t bs = (uint32_t)(k & 31);
+    int dis = 0;
+    for (int w = 0; 32 * w < pairs; ++w) {
+      const uint32_t lo = bits[w + ws];
+      const uint32_t hi = (w + ws + 1 <= NW) ? bits[w + ws + 1] : 0u;
+      const uint32_t sh = fshr(lo, hi, bs);
+      dis += (int)popc32((bits[w] ^ sh) & low_mask_word(pairs, w));
+    }
+    const long long C = pairs - 2 * dis;
+    acc += C * C;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+  if (lane == 0) E_out[seq] = acc;
+}
+
+cudaError_t launch_energy(const int8_t *seqs, int n, int L, int64_t *E_out, int32_t *err, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int NW = (L + 31) / 32;
+  const size_t smem = (size_t)kEnergyWarps * (NW + 1) * sizeof(uint32_t);
+  energy_kernel<<<(n + kEnergyWarps - 1) / kEnergyWarps, 32 * kEnergyWarps, smem, s>>>(seqs, n, L, E_out, err);
+  return cudaGetLastError();
+}
+
+}  // namespace psaw

@@ -1,0 +1,80 @@
+// Device kernels of the parallel self-avoiding-walk round (Eq. 4, Algorithm 2)
+// and their launch parameters.  Shared by the plain entry points and the
+// persistent batched/serving scheduler.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "walk_core.cuh"
+
+namespace psaw {
+
+constexpr int kWalkBlock = 128;   // threads (= walks) per block
+constexpr int kTopK = 4;          // candidates kept per pass of the neighbourhood scan
+
+enum ErrorBits : int32_t {
+  kErrRecheck = 1,   // incremental state disagreed with the XOR+popc recheck
+  kErrOverflow = 2,  // a visited table ran out of slots
+};
+
+// One launch = walks [g_begin, g_begin + g_count) of one round of one or more
+// problems of the same L; global walk id gw = problem * walks_per_problem + walk.
+struct WalkParams {
+  int32_t L;
+  int32_t walk_len;
+  int32_t walks_per_problem;
+  int32_t n_problems;
+  uint32_t round;
+  uint32_t g_begin;
+  uint32_t g_count;
+  uint32_t cap;           // visited-table slots per walk (power of two)
+  int32_t kw64;           // 64-bit words per slot
+  int32_t recheck_every;  // 0 = off
+  const uint64_t *seeds;  // [n_problems]
+  const int32_t *done;    // [n_problems], nonzero = skip (may be null)
+  uint64_t *tables;       // [g_count][cap][kw64]
+  // per-walk results, indexed by gw
+  int32_t *w_bestE;
+  int32_t *w_moves;
+  int32_t *w_stuck;
+  int32_t *w_best_step;
+  uint32_t *w_key;        // [gw][kKeyWords]
+  // per-problem accumulators
+  unsigned long long *p_evals;
+  unsigned long long *p_round_best;  // (E << 32) | walk, atomicMin
+  // optional trajectory capture for gw in [trace_begin, trace_begin + trace_count)
+  int32_t *trace_flips;   // [trace_count][walk_len]
+  uint32_t trace_begin;
+  uint32_t trace_count;
+  int32_t *err;
+};
+
+struct FinalizeParams {
+  int32_t n_problems;
+  int32_t walks_per_problem;
+  uint32_t round;
+  int32_t *done;
+  const uint64_t *budget;   // [n] neighbour-evaluation budget
+  const int64_t *target;    // [n] target energy, < 0 = none
+  const uint32_t *w_key;
+  unsigned long long *p_evals;
+  unsigned long long *p_round_best;
+  int64_t *p_bestE;
+  uint32_t *p_key;          // [n][kKeyWords]
+  int32_t *p_rounds;
+  int32_t *p_best_round;
+  int32_t *p_best_walk;
+};
+
+// Launch one round chunk for lag-word class W (L = 2m+1 with m <= 32W).
+cudaError_t launch_walk_round(int W, const WalkParams &p, cudaStream_t s);
+cudaError_t launch_finalize(const FinalizeParams &f, cudaStream_t s);
+cudaError_t launch_init_problems(int n, int64_t *p_bestE, unsigned long long *p_evals,
+                                 unsigned long long *p_round_best, int32_t *done, int32_t *p_rounds,
+                                 int32_t *p_best_round, int32_t *p_best_walk, uint32_t *p_key, cudaStream_t s);
+cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s);
+cudaError_t launch_energy(const int8_t *seqs, int n, int L, int64_t *E_out, int32_t *err, cudaStream_t s);
+
+inline int lag_words(int L) { return ((L - 1) / 2 + 31) / 32; }
+
+}  // namespace psaw

@@ -1,0 +1,141 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/labs.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(labs_\w+)\s*\(", text, flags=re.M):
+            if "typedef" not in m.group(0) and "#define" not in m.group(0):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2210_15962_gb300 import build
+    build.build()
+    import paper_2210_15962_gb300 as m
+    return m.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["labs_energy", "labs_walks", "labs_saw_round", "labs_walks_workspace_size",
+                     "labs_energy_batch", "labs_opts_init", "labs_status_str"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    import paper_2210_15962_gb300 as m
+    assert m.status_str(m.LABS_OK) == "ok"
+    assert m.status_str(m.LABS_EINVAL) == "invalid argument"
+    assert m.status_str(12345) == "unknown status"
+
+
+def test_opts_layout_matches_header(lib):
+    import paper_2210_15962_gb300 as m
+    o = m.labs_opts()
+    lib.labs_opts_init(ctypes.byref(o))
+    assert o.target_E == -1 and o.max_rounds == 0 and o.recheck_every == 0 and o.device_buffers == 0
+
+
+def test_struct_layouts_match_c_compiler(tmp_path):
+    # compile a probe against the header with the host C compiler and compare with the ctypes mirrors
+    import subprocess
+    import paper_2210_15962_gb300 as m
+    src = tmp_path / "probe.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "labs.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(labs_opts), sizeof(labs_stats),'
+                   ' offsetof(labs_opts, workspace), offsetof(labs_opts, rounds_per_seed),'
+                   ' offsetof(labs_stats, device_ms));return 0;}\n')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(m.labs_opts), ctypes.sizeof(m.labs_stats), m.labs_opts.workspace.offset,
+            m.labs_opts.rounds_per_seed.offset, m.labs_stats.device_ms.offset]
+    assert got == want
+
+
+@pytest.mark.parametrize("L", [4, 6, 3, 1, 513, 1001, -7])
+def test_walks_rejects_bad_L(lib, L):
+    import paper_2210_15962_gb300 as m
+    seeds = np.array([1], dtype=np.uint64)
+    seq = np.zeros(max(L, 1), dtype=np.int8)
+    E = np.zeros(1, dtype=np.int64)
+    st = lib.labs_walks(L, m._ptr(seeds), 1, 4, 8, 100, m._ptr(seq), m._ptr(E), None, None)
+    assert st == m.LABS_EINVAL
+    assert lib.labs_walks_workspace_size(L, 1, 4, 8) == 0
+
+
+def test_walks_rejects_bad_sizes(lib):
+    import paper_2210_15962_gb300 as m
+    seeds = np.array([1], dtype=np.uint64)
+    seq = np.zeros(27, dtype=np.int8)
+    E = np.zeros(1, dtype=np.int64)
+    p = m._ptr
+    assert lib.labs_walks(27, p(seeds), 0, 4, 8, 100, p(seq), p(E), None, None) == m.LABS_EINVAL  # no seeds
+    assert lib.labs_walks(27, p(seeds), 1, 0, 8, 100, p(seq), p(E), None, None) == m.LABS_EINVAL  # no walks
+    assert lib.labs_walks(27, p(seeds), 1, 4, 0, 100, p(seq), p(E), None, None) == m.LABS_EINVAL  # no steps
+    assert lib.labs_walks(27, p(seeds), 1, 4, 8, 0, p(seq), p(E), None, None) == m.LABS_EINVAL  # no budget
+    assert lib.labs_walks(27, None, 1, 4, 8, 100, p(seq), p(E), None, None) == m.LABS_EINVAL  # null seeds
+    assert lib.labs_walks(27, p(seeds), 1, 4, 8, 100, None, p(E), None, None) == m.LABS_EINVAL
+    assert lib.labs_walks(27, p(seeds), 65536, 65536, 8, 100, p(seq), p(E), None, None) == m.LABS_EINVAL
+    o = m.labs_opts()
+    lib.labs_opts_init(ctypes.byref(o))
+    o.recheck_every = -1
+    assert lib.labs_walks(27, p(seeds), 1, 4, 8, 100, p(seq), p(E), ctypes.byref(o), None) == m.LABS_EINVAL
+
+
+def test_energy_rejects_bad_args(lib):
+    import paper_2210_15962_gb300 as m
+    assert lib.labs_energy(None, 5) == m.LABS_EINVAL
+    s = np.ones(3, dtype=np.int8)
+    assert lib.labs_energy(m._ptr(s), 0) == m.LABS_EINVAL
+    assert lib.labs_energy_batch(None, 1, 5, None, None, 1) == m.LABS_EINVAL
+
+
+def test_saw_round_rejects_bad_args(lib):
+    import paper_2210_15962_gb300 as m
+    assert lib.labs_saw_round(28, 1, 0, 4, 8, 0, None, None, None, None, None, None, 0, 0, -1, None, 0,
+                              None) == m.LABS_EINVAL
+    t = np.zeros(64, dtype=np.int32)
+    assert lib.labs_saw_round(27, 1, 0, 4, 8, 0, None, None, None, None, None, m._ptr(t), 2, 4, -1, None, 0,
+                              None) == m.LABS_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_2210_15962_gb300 as m
+    monkeypatch.setattr(m, "_lib", None)
+    monkeypatch.setattr(m, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        m.load()
+
+
+def test_hex_helpers_roundtrip_table1():
+    import paper_2210_15962_gb300 as m
+    import oracle
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "table1_skew_sequences.txt"))
+            if l.strip() and not l.startswith("#")]
+    for r in rows:
+        L, E, hx = int(r[0]), int(r[1]), r[4]
+        s = m.from_hex(hx, L)
+        assert oracle.energy(s) == E
+        assert int(m.to_hex(s), 16) == int(hx, 16)
