@@ -150,6 +150,39 @@ labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_w
                            int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
                            int32_t *visited_count);
 
+/* Size of the fixed device scratch used by labs_saw_round_noalloc. */
+#define LABS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* labs_saw_round_noalloc -- the same round as labs_saw_round (walks
+ * 0..n_walks-1 of the problem `seed` in round `round`), for callers that
+ * cannot allocate device memory: code whose device memory belongs to another
+ * allocator that must not be bypassed (a framework or serving process that
+ * reserves the GPU up front), processes under a hard device-memory quota, or
+ * code that must not allocate on its call path.  The paper has no
+ * counterpart; this is a deployment variant of its walk round.
+ *
+ * It calls no allocator.  Its scratch (visited tables, per-walk state,
+ * counters) is one static device array of LABS_NOALLOC_SCRATCH_BYTES that
+ * every process loading this library holds on every GPU it uses until exit.
+ *   walk_best_E[n_walks]      device out: each walk's best energy;
+ *   walk_best_seq[n_walks*L]  device out: each walk's best sequence (+-1);
+ *   walk_moves, walk_stuck    device out [n_walks] or NULL;
+ *   stream                    cudaStream_t or NULL; the call synchronises it
+ *                             before returning.
+ * The first call on a device looks up the scratch's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls in a process share the one scratch array, which keeps the last
+ * call's contents (the call clears what must start at zero): calls that can
+ * overlap on the GPU (other threads, other streams) race and must be
+ * serialised by the caller.
+ * Returns LABS_OK, LABS_EINVAL (bad L, sizes or NULL outputs), LABS_ENOMEM
+ * if the round's scratch (about n_walks * (slots * 8 * ceil((D+1)/64) + 52)
+ * bytes, slots = the power of two >= 1.5 * (walk_len + 1), at least 64)
+ * exceeds LABS_NOALLOC_SCRATCH_BYTES, or LABS_ECUDA. */
+labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
+                                   int64_t *walk_best_E, int8_t *walk_best_seq, int32_t *walk_moves,
+                                   int32_t *walk_stuck, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *labs_status_str(labs_status s);
 

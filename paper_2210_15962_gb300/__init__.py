@@ -83,6 +83,9 @@ _EXPORTS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_void_p]),
+    "labs_saw_round_noalloc": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -230,6 +233,17 @@ def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, 
         out["visited"] = visited[:min(int(vcount[0]), vcap)]
         out["visited_count"] = int(vcount[0])
     return out
+
+
+def labs_saw_round_noalloc(L: int, seed: int, round_: int, n_walks: int, walk_len: int, walk_best_E, walk_best_seq,
+                           walk_moves=None, walk_stuck=None, stream=None) -> None:
+    """labs_saw_round into caller-owned CUDA tensors, using only the library's fixed static scratch
+    (for callers that may not allocate device memory; see include/labs.h)."""
+    def p(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(load().labs_saw_round_noalloc(L, seed, round_, n_walks, walk_len, p(walk_best_E), p(walk_best_seq),
+                                         p(walk_moves), p(walk_stuck), st), "labs_saw_round_noalloc")
 
 
 def to_hex(seq) -> str:
