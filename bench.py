@@ -31,7 +31,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L = 121
+DEFAULT_L = 121
+L = DEFAULT_L
 WALKS = 131072
 WALK_LEN = 8192
 BUDGET = 10 ** 11
@@ -48,11 +49,12 @@ def digits_for(L):
     return T
 
 
-def core_alu_ops_per_eval(L):
+def core_alu_ops_per_eval(L, planes):
     """ALU-pipe lane-ops of the bit-sliced Delta core per neighbour evaluation:
-    per 32 lags and digit plane, two masked XORs and a full adder (4 LOP3)."""
+    per 32 lags and digit plane, two masked XORs and a carry-save full adder
+    (4 LOP3), for the number of digit planes the scan used."""
     m = (L - 1) // 2
-    return 4.0 * digits_for(L) * m / 32.0
+    return 4.0 * planes * m / 32.0
 
 
 class ClockSampler:
@@ -118,7 +120,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED):
+def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS):
     """The oracle on a bounded sample of the benchmark's walks, all host cores."""
     import oracle
     cores = os.cpu_count() or 1
@@ -129,7 +131,7 @@ def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED):
     ev = int(r["evals"].sum())
     return {"value": ev / dt, "unit": "neighbour_evals/s", "cores": cores, "kind": "oracle",
             "sample": "%d of the %d walks of round 0 (L=%d, %d steps each), %d evaluations in %.1f s"
-                      % (n, WALKS, L, walk_len, ev, dt)}
+                      % (n, total_walks, L, walk_len, ev, dt)}
 
 
 def run_reference(args, world, rank):
@@ -162,11 +164,13 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--L", type=int, default=DEFAULT_L)
     ap.add_argument("--walks", type=int, default=WALKS)
     ap.add_argument("--walk-len", type=int, default=WALK_LEN)
     ap.add_argument("--budget", type=int, default=BUDGET)
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
     args = ap.parse_args()
     world, rank, local = dist_setup()
 
@@ -186,6 +190,7 @@ def main():
     pkg.load()
     stream = torch.cuda.Stream()
     seed = SEED + rank
+    L = args.L
     walks, wl, budget = args.walks, args.walk_len, args.budget
     ws_bytes = pkg.labs_walks_workspace_size(L, 1, walks, wl)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
@@ -216,9 +221,11 @@ def main():
     launches = 0
     walk_ms = 0.0
     walk_launches = 0
+    planes = 0
     for _ in range(args.steps):
         st = device_step()
         total_evals += st["evals"]
+        planes += st["plane_steps"]
         launches += st["launches"]
         walk_ms += st["walk_kernel_ms"]
         walk_launches += st["walk_launches"]
@@ -232,15 +239,16 @@ def main():
     del ws
     torch.cuda.synchronize()
     e2e_evals = 0
-    h2d = d2h = 0
-    pkg.labs_walks(L, [seed], walks, wl, budget)  # first call maps the allocator pool
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r = pkg.labs_walks(L, [seed], walks, wl, budget)
-        e2e_evals += int(r["evals"].sum())
-    t1 = time.perf_counter()
-    barrier()
+    t0 = t1 = 0.0
+    if not args.device_only:
+        pkg.labs_walks(L, [seed], walks, wl, budget)  # first call maps the allocator pool
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = pkg.labs_walks(L, [seed], walks, wl, budget)
+            e2e_evals += int(r["evals"].sum())
+        t1 = time.perf_counter()
+        barrier()
     h2d = 8 + 8 + 8          # seed, budget, target per problem
     d2h = L + 8 + 8 + 4 + 4  # best sequence, best E, evaluations, rounds, stop flag
     e2e_s = t1 - t0
@@ -259,30 +267,36 @@ def main():
         value = tot_evals / dev_s
         per_launch_ms = walk_ms / max(walk_launches, 1)
         evals_per_launch = total_evals / max(walk_launches, 1)
-        achieved = evals_per_launch * core_alu_ops_per_eval(L) / (per_launch_ms / 1e3) / 1e12
+        D = (L + 1) // 2
+        avg_planes = planes / max(total_evals / D, 1.0)
+        ops_per_eval = core_alu_ops_per_eval(L, avg_planes)
+        achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3) / 1e12
         peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         line = {
             "metric": "neighbour_evals_per_s", "value": value, "unit": "neighbour_evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (Philox-drawn uniform +-1 starts, seed %d per rank)" % SEED,
-            "config": {"workload": "plain_L121_131072x8192_budget1e11", "L": L, "walks": walks, "walk_len": wl,
+            "config": {"workload": ("plain_L121_131072x8192_budget1e11" if (L, walks, wl, budget) == (121, WALKS, WALK_LEN, BUDGET)
+                                    else "plain_L%d_%dx%d_budget%d" % (L, walks, wl, budget)),
+                       "L": L, "walks": walks, "walk_len": wl,
                        "budget": budget, "rounds_per_step": int(round(total_evals / args.steps /
                                                                      (walks * wl * ((L + 1) // 2)))),
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GiB of visited tables per round" % (ws_bytes / 2 ** 30)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "walk_kernel<W=2,T=7,K=4>", "kernel_ms_per_launch": per_launch_ms,
-                         "ops_per_eval": core_alu_ops_per_eval(L),
+                         "kernel": "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32),
+                         "kernel_ms_per_launch": per_launch_ms,
+                         "ops_per_eval": ops_per_eval, "avg_digit_planes": avg_planes,
                          "peak_basis": "152 SMs x 64 lanes/clk (measured LOP3 rate) x 2070 MHz max clock"},
-            "e2e": {"value": tot_e2e / e2e_s, "unit": "neighbour_evals/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": ({"value": tot_e2e / e2e_s, "unit": "neighbour_evals/s", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h} if e2e_s > 0 else None),
             "gpu_launches": launches,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -94,6 +94,8 @@ typedef struct labs_stats {
   int32_t reserved0;
   double walk_kernel_ms;     /* sum of the walk kernels' durations (CUDA events) */
   double device_ms;          /* first to last kernel of the call (CUDA events) */
+  uint64_t plane_steps;      /* sum over walk steps of the digit planes the scan used
+                                (evals / D steps in all; see the design notes) */
 } labs_stats;
 
 void labs_opts_init(labs_opts *o);

@@ -59,6 +59,7 @@ class labs_stats(ctypes.Structure):
         ("reserved0", ctypes.c_int32),
         ("walk_kernel_ms", ctypes.c_double),
         ("device_ms", ctypes.c_double),
+        ("plane_steps", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

@@ -53,6 +53,7 @@ struct Buffers {
   int64_t *target;
   int8_t *best_seq;
   int32_t *err;
+  unsigned long long *plane_steps;
   uint64_t *tables;
 };
 
@@ -77,6 +78,7 @@ size_t carve(Buffers &b, void *base, int L, int n_seeds, size_t n_walks, size_t 
   b.target = c.take<int64_t>(n_seeds);
   b.best_seq = c.take<int8_t>((size_t)n_seeds * L);
   b.err = c.take<int32_t>(1);
+  b.plane_steps = c.take<unsigned long long>(1);
   b.tables = c.take<uint64_t>(g_chunk * (table_bytes / 8));
   return c.off;
 }
@@ -286,6 +288,8 @@ struct Run {
     p.p_evals = b.p_evals;
     p.p_round_best = b.p_round_best;
     p.err = b.err;
+    p.plane_steps = b.plane_steps;
+    set_muls(p);
     return p;
   }
 
@@ -329,6 +333,7 @@ struct Run {
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.budget, bud.data(), sizeof(uint64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.target, tgt.data(), sizeof(int64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.plane_steps, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {
       ++launches;
       e = launch_init_problems(cfg.n_seeds, b.p_bestE, b.p_evals, b.p_round_best, b.done, b.p_rounds,
@@ -414,6 +419,8 @@ extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_se
   if (stats) {
     std::vector<unsigned long long> ev(n_seeds);
     std::vector<int32_t> rounds(n_seeds);
+    unsigned long long planes = 0;
+    LABS_CU(cudaMemcpyAsync(&planes, run.b.plane_steps, sizeof(planes), cudaMemcpyDeviceToHost, run.s));
     LABS_CU(cudaMemcpyAsync(ev.data(), run.b.p_evals, sizeof(uint64_t) * n_seeds, cudaMemcpyDeviceToHost, run.s));
     LABS_CU(cudaMemcpyAsync(rounds.data(), run.b.p_rounds, sizeof(int32_t) * n_seeds, cudaMemcpyDeviceToHost, run.s));
     LABS_CU(cudaStreamSynchronize(run.s));
@@ -427,6 +434,7 @@ extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_se
     stats->walk_launches = run.walk_launches;
     stats->walk_kernel_ms = run.walk_ms;
     stats->device_ms = elapsed(t0, t1);
+    stats->plane_steps = planes;
   }
 done:
   if (st == LABS_OK) {

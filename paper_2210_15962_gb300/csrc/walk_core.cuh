@@ -293,82 +293,194 @@ LABS_HD void top_insert(uint32_t (&top)[K], uint32_t x) {
   }
 }
 
+// Integer multiply-adds with a multiplier that is a run-time value, so that
+// they execute on the FMA pipe as IMAD (the ALU pipe carries the bit logic).
+// With m = 2, 2^31 or 2^30 they implement shifts: umulhi(x, 2^31) = x >> 1,
+// x * 2^31 = (x & 1) << 31, umulhi(x, 2) = x >> 31.
+struct Muls {
+  uint32_t one, two, four, h31, h30;
+};
+
+LABS_HD uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+#else
+  return a * b + c;
+#endif
+}
+
+LABS_HD uint32_t imadhi(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32) + c;
+#endif
+}
+
+// Smallest number of digit planes TP (T-3 <= TP <= T) that represents every
+// current C_{2i}: |C| <= 2^TP - 1 holds iff the digit bits TP-1 .. T-2 of
+// every e_i differ from its top bit T-1.  The TP-digit form of C then uses
+// planes 0 .. TP-2 and plane T-1 (as digit TP-1); any TP at or above this
+// minimum gives the same exact sums.
+template <int W, int T>
+LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
+  uint32_t M[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) M[w] = 0xFFFFFFFFu;
+  int tp = T;
+#pragma unroll
+  for (int u = T - 2; u >= T - 4 && u >= 1; --u) {  // tp = u + 1 >= T - 3
+    bool all = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      M[w] &= st.ep[u][w] ^ st.ep[T - 1][w];
+      const uint32_t valid = low_mask_word(g.m, w);
+      all = all && ((M[w] & valid) == valid);
+    }
+    if (!all) break;
+    tp = u + 1;
+  }
+  return tp;
+}
+
+// One flip of the neighbourhood scan.  B, F: bits at a-2i and a+2i of the
+// flip's class (lags i = 1.. on bits 0..); Vx, Vye: valid lags of each side
+// (Vye without the flip's own mirror pair); ba: the bit of position a.
+// Returns the packed key ((Delta + bias) << 8) | a.
+//   Q0 = sum_i (s_{a-2i} [i in Vx] + s_{a+2i} [i in Vye]) C_{2i}
+//      = 2 P - (2^TP - 1)(|Vx| + |Vye|),  P = sum_t 2^t popc over both sides of (V & (window ^ e_t)),
+//   Q = s_a Q0,  R = |Vx| + |Vye| + 2 |Vx & Vye| - 4 popc(Vx & Vye & (B ^ F)),
+//   Delta = 16 R - 8 Q.
+// With Z = Vx & Vye & (B ^ F ^ [s_a = -1]), popc(Z) is popc(Vx & Vye & (B ^ F))
+// for s_a = +1 and |Vx & Vye| minus it for s_a = -1, so that
+//   Delta = s_a (-16 (P + 4 popc(Z))) + c(s_a),  c = 8 (2^TP - 1) s_a n + 16 (n + 2 nxy) - 64 nxy [s_a = -1],
+// with n = |Vx| + |Vye|: one weighted popcount sum per flip.
+template <int W, int T, int TP, bool CENTRE>
+LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
+                          const uint32_t (&Vx)[W], const uint32_t (&Vy)[W], const uint32_t (&Pm)[W], uint32_t ba,
+                          uint32_t bm, int a, int n, int nxy) {
+  uint32_t acc = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t vx = Vx[w];
+    uint32_t p[TP + 1];
+    uint32_t v;
+    if (CENTRE) {
+#pragma unroll
+      for (int tt = 0; tt < TP; ++tt) {
+        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
+        p[tt] = popc32(vx & (B[w] ^ e));
+      }
+      v = p[TP - 1];
+#pragma unroll
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);
+    } else {
+      const uint32_t vy = Vy[w] & ~Pm[w];
+      uint32_t carry = 0;
+#pragma unroll
+      for (int tt = 0; tt < TP; ++tt) {
+        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
+        const uint32_t A = vx & (B[w] ^ e);
+        const uint32_t Bv = vy & (F[w] ^ e);
+        const uint32_t sum = A ^ Bv ^ carry;
+        carry = (A & Bv) | (carry & (A ^ Bv));
+        p[tt] = popc32(sum);
+      }
+      p[TP] = popc32(carry);
+      const uint32_t z = popc32(vx & vy & (B[w] ^ F[w] ^ bm));
+      v = p[TP];
+#pragma unroll
+      for (int tt = TP - 1; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);  // Horner: sum_t 2^t p_t
+      v = imad(z, mu.four, v);
+    }
+    acc = imad(acc, mu.one, v);
+  }
+  // Delta = -16 s_a acc + c
+  const int sgn = 1 - 2 * (int)ba;
+  const int c = 8 * ((1 << TP) - 1) * sgn * n + 16 * (n + 2 * nxy) - (ba ? 64 * nxy : 0);
+  const uint32_t delta = imad(acc, (uint32_t)(-16 * sgn), (uint32_t)(c + kDeltaBias));
+  return imad(delta, 256u, (uint32_t)a);
+}
+
 // Delta_j of every flip j of the pivot (Algorithm 2, CalculateNeighborhoodDelta)
-// and the K smallest packed keys ((Delta_j + bias) << 8 | j) that are >= floor,
-// skipping j == jprev (the previous pivot, always visited).
-template <int W, int T, int K>
-LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, int jprev, uint32_t floor,
-                             uint32_t (&top)[K]) {
-  constexpr int NS = W + 1;
+// with TP digit planes, and the K smallest packed keys (>= floor when RESCAN),
+// skipping j == jprev (the previous pivot, always visited).  Flips are scanned
+// class by class; the windows advance by one lag per flip.
+template <int W, int T, int TP, int K, bool RESCAN>
+LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int jprev,
+                                uint32_t floor, uint32_t (&top)[K]) {
 #pragma unroll
   for (int r = 0; r < K; ++r) top[r] = kNone;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int Nq = g.N[q];
     uint32_t F[W], B[W], Vx[W], Vy[W], Pm[W];
-    // F bit (i-1) = b at class index t+i; B bit (i-1) = b at class index t-i
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       F[w] = fshr(st.cls[q][w], st.cls[q][w + 1], 1u);
       B[w] = 0;
       Vx[w] = 0;
       Vy[w] = low_mask_word(Nq - 1, w);
-      // pair lag i0 = c - a of the flip's own mirror: bit (c - q - 1) at t = 0
       Pm[w] = ((g.c - q - 1) >> 5) == w ? (1u << ((g.c - q - 1) & 31)) : 0u;
     }
     uint32_t ba = st.cls[q][0] & 1u;
-    (void)NS;
-    for (int t = 0; t < g.nfree[q]; ++t) {
+    const bool has_centre = (g.c & 1) == q;
+    const int nloop = g.nfree[q] - (has_centre ? 1 : 0);
+    const int n = Nq - 2;  // |Vx| + |Vye| for every non-centre flip
+    for (int t = 0; t < nloop; ++t) {
       const int a = 2 * t + q;
-      const bool centre = (a == g.c);
-      const uint32_t bm = 0u - ba;
-      int accq = 0, accr = 0;
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        const uint32_t X = B[w] ^ bm;
-        const uint32_t Y = F[w] ^ bm;
-        const uint32_t vx = Vx[w];
-        const uint32_t vy = centre ? 0u : (Vy[w] & ~Pm[w]);
-        uint32_t carry = 0;
-#pragma unroll
-        for (int tt = 0; tt < T; ++tt) {
-          const uint32_t A = vx & (X ^ st.ep[tt][w]);
-          const uint32_t Bv = vy & (Y ^ st.ep[tt][w]);
-          const uint32_t s = A ^ Bv ^ carry;
-          carry = (A & Bv) | (carry & (A ^ Bv));
-          accq += (int)popc32(s) << tt;
-        }
-        accq += (int)popc32(carry) << T;
-        accr += (int)popc32(vx & vy & (X ^ Y));
-      }
-      const int nx = t;
-      const int ny = centre ? 0 : (Nq - 2 - t);
-      int nxy = 0;
-      if (!centre) {
-        const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
-        nxy = lim - ((g.c - a) <= lim ? 1 : 0);
-      }
-      const int Q = 2 * accq - ((1 << T) - 1) * (nx + ny);  // sum u_i C_{2i}
-      const int R = nx + ny + 2 * (nxy - 2 * accr);          // sum u_i^2
-      const int delta = 16 * R - 8 * Q;
-      uint32_t x = ((uint32_t)(delta + kDeltaBias) << 8) | (uint32_t)a;
-      x = (a == jprev || x < floor) ? kNone : x;
+      const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
+      const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
+      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, n, nxy);
+      x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
-      // advance to t + 1
+      // advance the windows and masks by one lag (shifts as IMAD on the FMA pipe)
+      const uint32_t ba_next = F[0] & 1u;
 #pragma unroll
-      for (int w = W - 1; w >= 0; --w) {
-        B[w] = (B[w] << 1) | (w ? (B[w - 1] >> 31) : ba);
-        Vx[w] = (Vx[w] << 1) | (w ? (Vx[w - 1] >> 31) : 1u);
+      for (int w = W - 1; w >= 1; --w) {
+        B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
+        Vx[w] = imadhi(Vx[w - 1], mu.two, imad(Vx[w], mu.two, 0u));
       }
-      ba = F[0] & 1u;
+      B[0] = imad(B[0], mu.two, ba);
+      Vx[0] = imad(Vx[0], mu.two, 1u);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
-        F[w] = fshr(F[w], (w + 1 < W) ? F[w + 1] : 0u, 1u);
-        Vy[w] = fshr(Vy[w], (w + 1 < W) ? Vy[w + 1] : 0u, 1u);
-        Pm[w] = fshr(Pm[w], (w + 1 < W) ? Pm[w + 1] : 0u, 2u);
+        F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
+        Vy[w] = imadhi(Vy[w], mu.h31, (w + 1 < W) ? imad(Vy[w + 1], mu.h31, 0u) : 0u);
+        Pm[w] = imadhi(Pm[w], mu.h30, (w + 1 < W) ? imad(Pm[w + 1], mu.h30, 0u) : 0u);
       }
+      ba = ba_next;
+    }
+    if (has_centre) {
+      const int t = nloop, a = g.c;
+      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, t, 0);
+      x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
+      top_insert(top, x);
     }
   }
+}
+
+// Dispatch on the plane count (the caller may pass any tp >= planes_needed);
+// floor > 0 selects the rescan variant (candidates at or above floor only).
+template <int W, int T, int K, bool RESCAN>
+LABS_HD void eval_neighbours_r(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int tp, int jprev,
+                               uint32_t floor, uint32_t (&top)[K]) {
+  constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
+  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN>(st, g, mu, jprev, floor, top);
+  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN>(st, g, mu, jprev, floor, top);
+  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN>(st, g, mu, jprev, floor, top);
+  else eval_neighbours_tp<W, T, T3, K, RESCAN>(st, g, mu, jprev, floor, top);
+}
+
+template <int W, int T, int K>
+LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int tp, int jprev,
+                             uint32_t floor, uint32_t (&top)[K]) {
+  if (floor == 0) eval_neighbours_r<W, T, K, false>(st, g, mu, tp, jprev, 0u, top);
+  else eval_neighbours_r<W, T, K, true>(st, g, mu, tp, jprev, floor, top);
 }
 
 LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }

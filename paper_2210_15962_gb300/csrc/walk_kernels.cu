@@ -14,8 +14,8 @@ namespace psaw {
 // strict best".  The candidate scan keeps the kTopK smallest (Delta, flip)
 // keys; if all of them are visited it rescans above the last one, so the
 // choice is exactly the minimum over unvisited neighbours.
-template <int W, int T, int K>
-__global__ void __launch_bounds__(kWalkBlock) walk_kernel(const WalkParams p) {
+template <int W, int T, int K, int MINB>
+__global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams p) {
   constexpr int NS = W + 1;
   const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kWalkBlock) walk_kernel(const WalkParams p) {
   if (!live) return;
 
   const Geometry g = make_geometry(p.L, T);
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
   WalkState<W, T> st;
   init_walk(st, g, p.seeds[prob], walk, p.round);
   uint64_t *table = p.tables + (size_t)lid * table_words;
@@ -57,14 +58,19 @@ __global__ void __launch_bounds__(kWalkBlock) walk_kernel(const WalkParams p) {
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
 
   int jprev = -1;
+  unsigned long long plane_sum = 0;
   for (int step = 1; step <= p.walk_len; ++step) {
     uint32_t floor = 0;
     int chosen = -1, cdelta = 0;
     uint32_t cslot = 0;
     bool need = true;
+    int tp = planes_needed(st, g);
+    tp = __reduce_max_sync(__activemask(), (unsigned)tp);  // one plane count per warp (any larger count is exact)
+    tp = tp < T - 3 ? T - 3 : tp;
+    plane_sum += (unsigned)tp;
     while (need) {
       uint32_t top[K];
-      eval_neighbours<W, T, K>(st, g, jprev, floor, top);
+      eval_neighbours<W, T, K>(st, g, mu, tp, jprev, floor, top);
 #pragma unroll
       for (int r = 0; r < K; ++r) {
         if (need) {
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(kWalkBlock) walk_kernel(const WalkParams p) {
 #pragma unroll
   for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? best_key[w] : 0u;
   atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(moves + stuck));
+  if (p.plane_steps) atomicAdd(p.plane_steps, plane_sum);
   atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)bestE << 32) | walk);
 }
 
@@ -125,11 +132,18 @@ struct PlanesFor {
   static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
 };
 
+// resident blocks of kWalkBlock walks per SM each class is compiled for
+// (the register budget per thread is 65536 / (128 * MINB))
+template <int W>
+struct MinBlocksFor {
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
+};
+
 template <int W>
 static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
   constexpr int T = PlanesFor<W>::value;
   const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
-  walk_kernel<W, T, kTopK><<<blocks, kWalkBlock, 0, s>>>(p);
+  walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,19 @@ struct WalkParams {
   uint32_t trace_begin;
   uint32_t trace_count;
   int32_t *err;
+  // multipliers 1, 2, 4, 2^31, 2^30 as run-time values (see Muls)
+  uint32_t mul_one, mul_two, mul_four, mul_h31, mul_h30;
+  // sum over walk steps of the digit planes used (for the work accounting)
+  unsigned long long *plane_steps;
 };
+
+inline void set_muls(WalkParams &p) {
+  p.mul_one = 1u;
+  p.mul_two = 2u;
+  p.mul_four = 4u;
+  p.mul_h31 = 0x80000000u;
+  p.mul_h30 = 0x40000000u;
+}
 
 struct FinalizeParams {
   int32_t n_problems;
