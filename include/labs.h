@@ -152,6 +152,55 @@ labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_w
                            int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
                            int32_t *visited_count);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent problems of uneven L solved together (Eq. 4 rounds of
+ * Algorithm 2 walks for several instances at once): a persistent kernel per
+ * lag-word class W = ceil(((L-1)/2)/32) whose warps take tasks of 32 walks of
+ * one round of one problem from a device counter, longest tasks first, and an
+ * in-order per-problem finalize (Algorithm 1's best update and stop rule).
+ * Each problem's result is exactly what labs_walks gives for it alone with
+ * the same (L, seed, walks, walk_len, step_budget, target_E). */
+typedef struct labs_problem {
+  int32_t L;            /* odd, LABS_L_MIN..LABS_L_MAX */
+  int32_t walks;        /* walks per round, 1..2^24 */
+  int32_t walk_len;     /* steps per walk, 1..2^26 */
+  int32_t reserved;     /* 0 */
+  uint64_t seed;
+  uint64_t step_budget; /* neighbour evaluations, >= 1 */
+  int64_t target_E;     /* stop at the first round whose best E <= target_E; < 0 = none */
+} labs_problem;
+
+typedef struct labs_batch_opts {
+  void *stream;              /* cudaStream_t; NULL = the batch creates its own stream */
+  int32_t use_graph;         /* 1: when no problem has a target, the first launch sequence is
+                                captured as a CUDA graph on the first run and replayed after */
+  int32_t autotune;          /* 1: pick walks per CTA and table capacity per class by timing
+                                candidates on a sample (cached per process) */
+  int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
+  int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 15 or autotuned */
+  int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
+  int32_t reserved;
+} labs_batch_opts;
+
+typedef struct labs_batch labs_batch; /* opaque, owns its device memory */
+
+/* Validate the problems and allocate the batch (visited-table pools sized
+ * for the device's resident lanes of each class).  problems[n] is copied.
+ * Returns LABS_EINVAL for a bad problem or option, LABS_ENOMEM, LABS_ECUDA. */
+labs_status labs_batch_create(const labs_problem *problems, int32_t n, const labs_batch_opts *opts,
+                              labs_batch **out);
+/* Solve every problem from scratch (one run = the whole solve); blocks until
+ * done.  stats may be NULL. */
+labs_status labs_batch_run(labs_batch *b, labs_stats *stats);
+/* Result of problem i of the last run (host pointers, any may be NULL):
+ * best_seq[L], best_E, evaluations, rounds.  LABS_PENDING before a run. */
+labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t *best_seq, int64_t *best_E, uint64_t *evals,
+                              int32_t *rounds);
+/* Launch shape chosen for class W: walks per CTA, table factor x 10, walks resident at once. */
+labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads, int32_t *table_factor_x10,
+                             int32_t *resident_walks);
+labs_status labs_batch_destroy(labs_batch *b);
+
 /* Size of the fixed device scratch used by labs_saw_round_noalloc. */
 #define LABS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -66,6 +66,30 @@ class labs_stats(ctypes.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_ if not f[0].startswith("reserved")}
 
 
+class labs_problem(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("walks", ctypes.c_int32),
+        ("walk_len", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("step_budget", ctypes.c_uint64),
+        ("target_E", ctypes.c_int64),
+    ]
+
+
+class labs_batch_opts(ctypes.Structure):
+    _fields_ = [
+        ("stream", ctypes.c_void_p),
+        ("use_graph", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("table_factor_x10", ctypes.c_int32),
+        ("rounds_per_launch", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 _EXPORTS = {
@@ -87,6 +111,14 @@ _EXPORTS = {
     "labs_saw_round_noalloc": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "labs_batch_create": (ctypes.c_int32, [ctypes.POINTER(labs_problem), ctypes.c_int32,
+                                           ctypes.POINTER(labs_batch_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "labs_batch_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_stats)]),
+    "labs_batch_result": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "labs_batch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "labs_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
 }
 
 
@@ -245,6 +277,73 @@ def labs_saw_round_noalloc(L: int, seed: int, round_: int, n_walks: int, walk_le
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(load().labs_saw_round_noalloc(L, seed, round_, n_walks, walk_len, p(walk_best_E), p(walk_best_seq),
                                          p(walk_moves), p(walk_stuck), st), "labs_saw_round_noalloc")
+
+
+def make_problem(L, walks, walk_len, seed, step_budget, target_E=-1) -> labs_problem:
+    return labs_problem(int(L), int(walks), int(walk_len), 0, int(seed), int(step_budget), int(target_E))
+
+
+class Batch:
+    """labs_batch_*: many problems of uneven L solved together by the persistent batch kernel.
+
+    problems: iterable of labs_problem or (L, walks, walk_len, seed, step_budget[, target_E]) tuples.
+    """
+
+    def __init__(self, problems, *, use_graph=False, autotune=False, block_threads=0, table_factor_x10=0,
+                 rounds_per_launch=0, stream=None):
+        probs = [p if isinstance(p, labs_problem) else make_problem(*p) for p in problems]
+        self.problems = probs
+        arr = (labs_problem * len(probs))(*probs)
+        o = labs_batch_opts()
+        if stream is not None:
+            o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        o.use_graph = int(bool(use_graph))
+        o.autotune = int(bool(autotune))
+        o.block_threads = int(block_threads)
+        o.table_factor_x10 = int(table_factor_x10)
+        o.rounds_per_launch = int(rounds_per_launch)
+        h = ctypes.c_void_p()
+        _check(load().labs_batch_create(arr, len(probs), ctypes.byref(o), ctypes.byref(h)), "labs_batch_create")
+        self._h = h
+
+    def run(self) -> dict:
+        st = labs_stats()
+        _check(load().labs_batch_run(self._h, ctypes.byref(st)), "labs_batch_run")
+        return st.as_dict()
+
+    def result(self, i: int) -> dict:
+        L = self.problems[i].L
+        seq = np.zeros(L, dtype=np.int8)
+        E = np.zeros(1, dtype=np.int64)
+        ev = np.zeros(1, dtype=np.uint64)
+        rd = np.zeros(1, dtype=np.int32)
+        _check(load().labs_batch_result(self._h, i, _ptr(seq), _ptr(E), _ptr(ev), _ptr(rd)), "labs_batch_result")
+        return {"best_seq": seq, "best_E": int(E[0]), "evals": int(ev[0]), "rounds": int(rd[0])}
+
+    def results(self) -> list:
+        return [self.result(i) for i in range(len(self.problems))]
+
+    def shape(self, W: int) -> dict:
+        v = np.zeros(3, dtype=np.int32)
+        _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3])), "labs_batch_shape")
+        return {"block_threads": int(v[0]), "table_factor_x10": int(v[1]), "resident_walks": int(v[2])}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().labs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def to_hex(seq) -> str:

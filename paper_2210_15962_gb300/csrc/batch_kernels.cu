@@ -1,0 +1,162 @@
+// Persistent batch kernel: every warp repeatedly takes the next task (32
+// walks of one round of one problem) from a device counter and runs it, so
+// problems of different L and cost share the GPU without per-problem
+// launches.  One kernel per lag-word class W (each with the register budget
+// of the per-round walk kernel of that class).
+#include "batch.cuh"
+#include "walk_device.cuh"
+
+namespace psaw {
+
+constexpr int kBatchMaxThreads = 256;
+
+// register budget per thread of each class (set so that no class spills;
+// the task loop keeps a little more state live than the per-round kernel)
+template <int W>
+struct MaxRegsFor {
+  static constexpr int value = W == 1 ? 88 : (W == 2 ? 96 : (W <= 4 ? 128 : (W == 5 ? 168 : (W == 6 ? 208 : 255))));
+};
+
+template <int W>
+__global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::value)
+    batch_kernel(const BatchKernelParams p) {
+  constexpr int T = PlanesFor<W>::value;
+  constexpr int NS = W + 1;
+  const int lane = threadIdx.x & 31;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t *table = p.pool + gtid * p.pool_words;
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  unsigned long long planes = 0;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(p.task_next, 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= p.n_tasks) break;
+    const BatchTask task = p.tasks[t];
+    if (p.done && p.done[task.problem]) continue;
+    const BatchProblem pr = p.probs[task.problem];
+    const uint32_t walk = task.chunk * 32u + (uint32_t)lane;
+    const bool active = walk < (uint32_t)pr.walks;
+    clear_tables_warp(table, (size_t)pr.cap * (size_t)pr.kw64, active);
+    unsigned long long packed = ~0ull;
+    uint32_t evals = 0;
+    WalkOut<NS> o;
+    if (active) {
+      const Geometry g = make_geometry(pr.L, T);
+      run_walk<W, T, kTopK>(g, mu, pr.seed, walk, task.round, pr.walk_len, table, pr.cap, pr.kw64, 0, nullptr, p.err,
+                            o);
+      packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
+      evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);
+      planes += o.planes;
+    }
+    // the chunk's best (lowest E, then lowest walk) publishes its key
+    unsigned long long m = packed;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, m, off);
+      m = v < m ? v : m;
+    }
+    if (active && packed == m) {
+      uint32_t *k = p.slot_keys + ((size_t)task.slot * p.max_chunks + task.chunk) * kKeyWords;
+#pragma unroll
+      for (int w = 0; w < kKeyWords; ++w) k[w] = w < NS ? o.best_key[w] : 0u;
+    }
+    const uint32_t ev = __reduce_add_sync(0xFFFFFFFFu, evals);
+    if (lane == 0) {
+      atomicMin(&p.slot_best[task.slot], m);
+      atomicAdd(&p.slot_evals[task.slot], (unsigned long long)ev);
+    }
+  }
+  if (p.plane_steps && planes) atomicAdd(p.plane_steps, planes);
+}
+
+template <int W>
+static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = per_sm * sms;
+  if (grid_out) *grid_out = grid;
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  batch_kernel<W><<<grid, block, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int W>
+static int resident_w(int block) {
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, 0) != cudaSuccess) return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return per_sm * sms * block;
+}
+
+cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out) {
+  if (block < 32 || block > kBatchMaxThreads || block % 32) return cudaErrorInvalidValue;
+  switch (W) {
+    case 1: return launch_batch_w<1>(block, p, s, grid_out);
+    case 2: return launch_batch_w<2>(block, p, s, grid_out);
+    case 3: return launch_batch_w<3>(block, p, s, grid_out);
+    case 4: return launch_batch_w<4>(block, p, s, grid_out);
+    case 5: return launch_batch_w<5>(block, p, s, grid_out);
+    case 6: return launch_batch_w<6>(block, p, s, grid_out);
+    case 7: return launch_batch_w<7>(block, p, s, grid_out);
+    case 8: return launch_batch_w<8>(block, p, s, grid_out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batch_resident_lanes(int W, int block) {
+  switch (W) {
+    case 1: return resident_w<1>(block);
+    case 2: return resident_w<2>(block);
+    case 3: return resident_w<3>(block);
+    case 4: return resident_w<4>(block);
+    case 5: return resident_w<5>(block);
+    case 6: return resident_w<6>(block);
+    case 7: return resident_w<7>(block);
+    case 8: return resident_w<8>(block);
+    default: return 0;
+  }
+}
+
+// Algorithm 1's bookkeeping for a batch launch: each problem takes its rounds
+// of this launch in round order (rounds beyond its stop point, run
+// speculatively, are ignored), keeping the strict best (earliest round, then
+// lowest walk on ties) and stopping at the budget or the target.
+__global__ void batch_finalize_kernel(const BatchFinalizeParams f) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= f.n_problems || f.done[p]) return;
+  for (uint32_t k = 0; k < f.n_slots[p]; ++k) {
+    const uint32_t slot = f.first_slot[p] + k;
+    f.evals[p] += f.slot_evals[slot];
+    const unsigned long long rb = f.slot_best[slot];
+    if (rb != ~0ull) {
+      const int64_t E = (int64_t)(rb >> 32);
+      const uint32_t w = (uint32_t)(rb & 0xFFFFFFFFu);
+      if (E < f.bestE[p]) {
+        f.bestE[p] = E;
+        const uint32_t *src = f.slot_keys + ((size_t)slot * f.max_chunks + (w >> 5)) * kKeyWords;
+        for (int i = 0; i < kKeyWords; ++i) f.key[(size_t)p * kKeyWords + i] = src[i];
+        f.best_round[p] = (int32_t)f.slot_round[slot];
+        f.best_walk[p] = (int32_t)w;
+      }
+    }
+    f.rounds[p] = (int32_t)f.slot_round[slot] + 1;
+    if (f.evals[p] >= f.budget[p] || (f.target[p] >= 0 && f.bestE[p] <= f.target[p])) {
+      f.done[p] = 1;
+      break;
+    }
+  }
+}
+
+cudaError_t launch_batch_finalize(const BatchFinalizeParams &f, cudaStream_t s) {
+  if (f.n_problems <= 0) return cudaSuccess;
+  batch_finalize_kernel<<<(f.n_problems + 127) / 128, 128, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+}  // namespace psaw

@@ -1,0 +1,133 @@
+// Device-side body of one contiguous self-avoiding walk (Eq. 3, Algorithm 2)
+// on one lane, shared by the per-round walk kernel and the persistent batch
+// kernel, plus small warp helpers.
+#pragma once
+#include "walk_kernels.cuh"
+
+namespace psaw {
+
+// digit planes used for lag-word class W (covers every L with m <= 32W)
+template <int W>
+struct PlanesFor {
+  static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
+};
+
+// resident blocks of kWalkBlock walks per SM each class is compiled for
+// (the register budget per thread is 65536 / (128 * MINB))
+template <int W>
+struct MinBlocksFor {
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
+};
+
+template <int NS>
+struct WalkOut {
+  int32_t bestE, best_step, moves, stuck;
+  uint32_t best_key[NS];
+  unsigned long long planes;  // sum over steps of the digit planes scanned
+};
+
+// Zero the `words` 64-bit words of every live lane's table with coalesced
+// 16-byte stores by the whole warp.  All 32 lanes must call it.
+__device__ __forceinline__ void clear_tables_warp(uint64_t *my_table, size_t words, bool live) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t live_lanes = __ballot_sync(0xFFFFFFFFu, live);
+  const size_t n16 = words / 2;
+  for (int l = 0; l < 32; ++l) {
+    const unsigned long long base = __shfl_sync(0xFFFFFFFFu, (unsigned long long)my_table, l);
+    if ((live_lanes >> l) & 1u) {
+      uint4 *b = reinterpret_cast<uint4 *>(base);
+      for (size_t i = (size_t)lane; i < n16; i += 32) b[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  __syncwarp();
+}
+
+// One walk: random P_1, then walk_len steps of "evaluate all D flips -> best
+// unvisited neighbour (ties to the lowest flip) -> insert -> update C, E ->
+// keep the strict best".  The scan keeps the K smallest (Delta, flip) keys; if
+// all are visited it rescans above the last one, so the choice is exactly the
+// minimum over unvisited neighbours.  `table` must be zeroed.
+template <int W, int T, int K>
+__device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, uint64_t seed, uint32_t walk, uint32_t round,
+                                         int walk_len, uint64_t *table, uint32_t cap, int kw64, int recheck_every,
+                                         int32_t *trace, int32_t *err, WalkOut<W + 1> &out) {
+  constexpr int NS = W + 1;
+  WalkState<W, T> st;
+  init_walk(st, g, seed, walk, round);
+  {
+    uint32_t slot;
+    table_find(table, cap, kw64, st.key, g.D, &slot);
+    table_store(table, slot, kw64, st.key, g.D);
+  }
+  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
+  uint32_t best_key[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+  int jprev = -1;
+  unsigned long long plane_sum = 0;
+  for (int step = 1; step <= walk_len; ++step) {
+    uint32_t floor = 0;
+    int chosen = -1, cdelta = 0;
+    uint32_t cslot = 0;
+    bool need = true;
+    int tp = planes_needed(st, g);
+    tp = __reduce_max_sync(__activemask(), (unsigned)tp);  // one plane count per warp (any larger count is exact)
+    tp = tp < T - 3 ? T - 3 : tp;
+    plane_sum += (unsigned)tp;
+    while (need) {
+      uint32_t top[K];
+      eval_neighbours<W, T, K>(st, g, mu, tp, jprev, floor, top);
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        if (need) {
+          if (top[r] == kNone) {
+            need = false;  // every neighbour not below `floor` is visited: stuck
+          } else {
+            const int a = key_flip(top[r]);
+            uint32_t nk[NS];
+#pragma unroll
+            for (int w = 0; w < NS; ++w) nk[w] = st.key[w];
+            xor_bit(nk, a, 1u);
+            uint32_t s;
+            if (!table_find(table, cap, kw64, nk, g.D, &s)) {
+              need = false;
+              if (s == kNone) {
+                atomicOr(err, kErrOverflow);
+              } else {
+                chosen = a;
+                cdelta = key_delta(top[r]);
+                cslot = s;
+              }
+            }
+          }
+        }
+      }
+      if (need) floor = top[K - 1] + 1u;
+    }
+    if (chosen < 0) {
+      stuck = 1;
+      break;
+    }
+    apply_move(st, g, chosen, cdelta);
+    table_store(table, cslot, kw64, st.key, g.D);
+    jprev = chosen;
+    moves = step;
+    if (trace) trace[step - 1] = chosen;
+    if (st.E < bestE) {
+      bestE = st.E;
+      best_step = step;
+#pragma unroll
+      for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+    }
+    if (recheck_every > 0 && (step % recheck_every) == 0 && !recheck_walk(st, g)) atomicOr(err, kErrRecheck);
+  }
+  out.bestE = bestE;
+  out.best_step = best_step;
+  out.moves = moves;
+  out.stuck = stuck;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
+  out.planes = plane_sum;
+}
+
+}  // namespace psaw

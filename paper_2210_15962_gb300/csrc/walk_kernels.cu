@@ -3,141 +3,44 @@
 // Algorithm 1, the key -> sequence expansion (Eq. 2) and the Eq. 1 energy.
 #include <climits>
 
-#include "walk_kernels.cuh"
+#include "walk_device.cuh"
 
 namespace psaw {
 
-// One thread = one walk.  The warp first zeroes the visited tables of its 32
-// walks with coalesced 16-byte stores, then every lane runs its walk:
-// random P_1, then walk_len steps of "evaluate all D flips -> best unvisited
-// neighbour (ties to the lowest flip) -> insert -> update C, E -> keep the
-// strict best".  The candidate scan keeps the kTopK smallest (Delta, flip)
-// keys; if all of them are visited it rescans above the last one, so the
-// choice is exactly the minimum over unvisited neighbours.
+// One thread = one walk (Algorithm 2 with one lane in place of one block).
+// The warp zeroes the visited tables of its live lanes, then every lane runs
+// its walk (run_walk) and publishes its best to the round's accumulators.
 template <int W, int T, int K, int MINB>
 __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams p) {
   constexpr int NS = W + 1;
   const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
   const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
   const uint32_t gw = p.g_begin + lid;
   const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
   const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
   const bool live = lid < p.g_count && !(p.done && p.done[prob]);
-  {
-    const uint32_t first = lid - (uint32_t)lane;
-    const uint32_t live_lanes = __ballot_sync(0xFFFFFFFFu, live);
-    const size_t n16 = table_words / 2;
-    for (int l = 0; l < 32; ++l) {
-      const uint32_t s = first + (uint32_t)l;
-      if ((live_lanes >> l) & 1u) {
-        uint4 *base = reinterpret_cast<uint4 *>(p.tables + (size_t)s * table_words);
-        for (size_t i = (size_t)lane; i < n16; i += 32) base[i] = make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
-    __syncwarp();
-  }
+  uint64_t *table = p.tables + (size_t)lid * table_words;
+  clear_tables_warp(table, table_words, live);
   if (!live) return;
 
   const Geometry g = make_geometry(p.L, T);
   const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
-  WalkState<W, T> st;
-  init_walk(st, g, p.seeds[prob], walk, p.round);
-  uint64_t *table = p.tables + (size_t)lid * table_words;
-  {
-    uint32_t slot;
-    table_find(table, p.cap, p.kw64, st.key, g.D, &slot);
-    table_store(table, slot, p.kw64, st.key, g.D);
-  }
-  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
-  uint32_t best_key[NS];
-#pragma unroll
-  for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
   int32_t *trace = nullptr;
   if (p.trace_flips && gw - p.trace_begin < p.trace_count)
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
-
-  int jprev = -1;
-  unsigned long long plane_sum = 0;
-  for (int step = 1; step <= p.walk_len; ++step) {
-    uint32_t floor = 0;
-    int chosen = -1, cdelta = 0;
-    uint32_t cslot = 0;
-    bool need = true;
-    int tp = planes_needed(st, g);
-    tp = __reduce_max_sync(__activemask(), (unsigned)tp);  // one plane count per warp (any larger count is exact)
-    tp = tp < T - 3 ? T - 3 : tp;
-    plane_sum += (unsigned)tp;
-    while (need) {
-      uint32_t top[K];
-      eval_neighbours<W, T, K>(st, g, mu, tp, jprev, floor, top);
+  WalkOut<NS> o;
+  run_walk<W, T, K>(g, mu, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64, p.recheck_every, trace,
+                    p.err, o);
+  p.w_bestE[gw] = o.bestE;
+  p.w_moves[gw] = o.moves;
+  p.w_stuck[gw] = o.stuck;
+  p.w_best_step[gw] = o.best_step;
 #pragma unroll
-      for (int r = 0; r < K; ++r) {
-        if (need) {
-          if (top[r] == kNone) {
-            need = false;  // every neighbour not below `floor` is visited: stuck
-          } else {
-            const int a = key_flip(top[r]);
-            uint32_t nk[NS];
-#pragma unroll
-            for (int w = 0; w < NS; ++w) nk[w] = st.key[w];
-            xor_bit(nk, a, 1u);
-            uint32_t s;
-            if (!table_find(table, p.cap, p.kw64, nk, g.D, &s)) {
-              need = false;
-              if (s == kNone) {
-                atomicOr(p.err, kErrOverflow);
-              } else {
-                chosen = a;
-                cdelta = key_delta(top[r]);
-                cslot = s;
-              }
-            }
-          }
-        }
-      }
-      if (need) floor = top[K - 1] + 1u;
-    }
-    if (chosen < 0) {
-      stuck = 1;
-      break;
-    }
-    apply_move(st, g, chosen, cdelta);
-    table_store(table, cslot, p.kw64, st.key, g.D);
-    jprev = chosen;
-    moves = step;
-    if (trace) trace[step - 1] = chosen;
-    if (st.E < bestE) {
-      bestE = st.E;
-      best_step = step;
-#pragma unroll
-      for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
-    }
-    if (p.recheck_every > 0 && (step % p.recheck_every) == 0 && !recheck_walk(st, g)) atomicOr(p.err, kErrRecheck);
-  }
-  p.w_bestE[gw] = bestE;
-  p.w_moves[gw] = moves;
-  p.w_stuck[gw] = stuck;
-  p.w_best_step[gw] = best_step;
-#pragma unroll
-  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? best_key[w] : 0u;
-  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(moves + stuck));
-  if (p.plane_steps) atomicAdd(p.plane_steps, plane_sum);
-  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)bestE << 32) | walk);
+  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
+  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
+  if (p.plane_steps) atomicAdd(p.plane_steps, o.planes);
+  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
 }
-
-// digit planes used for lag-word class W (covers every L with m <= 32W)
-template <int W>
-struct PlanesFor {
-  static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
-};
-
-// resident blocks of kWalkBlock walks per SM each class is compiled for
-// (the register budget per thread is 65536 / (128 * MINB))
-template <int W>
-struct MinBlocksFor {
-  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
-};
 
 template <int W>
 static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {

@@ -65,12 +65,16 @@ def test_struct_layouts_match_c_compiler(tmp_path):
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "labs.h"\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(labs_opts), sizeof(labs_stats),'
                    ' offsetof(labs_opts, workspace), offsetof(labs_opts, rounds_per_seed),'
-                   ' offsetof(labs_stats, device_ms));return 0;}\n')
+                   ' offsetof(labs_stats, device_ms));'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(labs_problem), offsetof(labs_problem, target_E),'
+                   ' sizeof(labs_batch_opts), offsetof(labs_batch_opts, rounds_per_launch));return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(m.labs_opts), ctypes.sizeof(m.labs_stats), m.labs_opts.workspace.offset,
-            m.labs_opts.rounds_per_seed.offset, m.labs_stats.device_ms.offset]
+            m.labs_opts.rounds_per_seed.offset, m.labs_stats.device_ms.offset,
+            ctypes.sizeof(m.labs_problem), m.labs_problem.target_E.offset, ctypes.sizeof(m.labs_batch_opts),
+            m.labs_batch_opts.rounds_per_launch.offset]
     assert got == want
 
 
@@ -139,3 +143,20 @@ def test_hex_helpers_roundtrip_table1():
         s = m.from_hex(hx, L)
         assert oracle.energy(s) == E
         assert int(m.to_hex(s), 16) == int(hx, 16)
+
+
+@pytest.mark.parametrize("bad", [(6, 32, 10, 1, 100), (27, 0, 10, 1, 100), (27, 32, 0, 1, 100), (27, 32, 10, 1, 0),
+                                 (513, 32, 10, 1, 100)])
+def test_batch_rejects_bad_problems(lib, bad):
+    import paper_2210_15962_gb300 as m
+    with pytest.raises(m.LabsError) as ei:
+        m.Batch([(27, 64, 100, 1, 1000), bad])
+    assert ei.value.status == m.LABS_EINVAL
+
+
+def test_batch_rejects_bad_options(lib):
+    import paper_2210_15962_gb300 as m
+    for kw in [dict(block_threads=48), dict(block_threads=512), dict(table_factor_x10=5)]:
+        with pytest.raises(m.LabsError) as ei:
+            m.Batch([(27, 64, 100, 1, 1000)], **kw)
+        assert ei.value.status == m.LABS_EINVAL

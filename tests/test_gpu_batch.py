@@ -1,0 +1,105 @@
+"""Batched persistent path: every problem's result is exactly what labs_walks
+gives for it alone (same L, seed, walks, walk length, budget, target), for
+mixes of lag-word classes, uneven budgets, targets, stuck walks, CUDA graph
+replay and autotuned launch shapes; plus oracle checks on small problems."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2210_15962_gb300 import build
+    build.build()
+    import paper_2210_15962_gb300 as mod
+    mod.load()
+    return mod
+
+
+def alone(m, p):
+    L, walks, wl, seed, budget = p[:5]
+    tgt = p[5] if len(p) > 5 else -1
+    r = m.labs_walks(L, [seed], walks, wl, budget, target_E=tgt)
+    return {"best_E": int(r["best_E"][0]), "best_seq": r["best_seq"][0], "evals": int(r["evals"][0]),
+            "rounds": int(r["rounds"][0])}
+
+
+def check_same(m, probs, results):
+    for p, g in zip(probs, results):
+        a = alone(m, p)
+        assert g["best_E"] == a["best_E"], p
+        assert np.array_equal(g["best_seq"], a["best_seq"]), p
+        assert g["evals"] == a["evals"] and g["rounds"] == a["rounds"], (p, g["evals"], a["evals"])
+
+
+MIX = [
+    # L, walks, walk_len, seed, budget[, target]
+    (27, 64, 300, 1, 64 * 300 * 14 * 3 + 1),          # W=1, 4 rounds
+    (61, 100, 250, 2, 1),                              # W=1 edge (m=30), 1 round, ragged chunk
+    (65, 70, 200, 3, 70 * 200 * 33 * 2),               # W=1 (m=32)
+    (67, 96, 200, 4, 96 * 200 * 34 * 2 + 5),           # W=2 (m=33)
+    (121, 128, 300, 5, 128 * 300 * 61 * 2),            # W=2
+    (131, 33, 150, 6, 33 * 150 * 66 * 3),              # W=3
+    (199, 40, 120, 7, 1, -1),                          # W=4
+    (223, 64, 100, 8, 10 ** 12, 4600),                 # W=4 with a target (reached in round 0; later rounds speculative)
+    (301, 32, 80, 9, 32 * 80 * 151 * 2),               # W=5
+]
+
+
+def test_mixed_batch_equals_alone(m):
+    with m.Batch(MIX) as b:
+        st = b.run()
+        check_same(m, MIX, b.results())
+        assert st["walk_launches"] >= 1 and st["evals"] == sum(b.result(i)["evals"] for i in range(len(MIX)))
+        # a second run of the same batch gives the same results
+        b.run()
+        check_same(m, MIX, b.results())
+
+
+def test_graph_replay_and_autotune_equal_alone(m):
+    probs = [p for p in MIX if len(p) == 5]  # graphs are used when no problem has a target
+    with m.Batch(probs, use_graph=True, autotune=True) as b:
+        for _ in range(3):
+            b.run()
+            check_same(m, probs, b.results())
+        for W in {((p[0] - 1) // 2 + 31) // 32 for p in probs}:
+            sh = b.shape(W)
+            assert sh["block_threads"] in (64, 128, 256) and sh["table_factor_x10"] in (15, 30)
+            assert sh["resident_walks"] > 0
+
+
+def test_stuck_walks_need_continuation_launches(m):
+    # tiny spaces: walks get stuck, rounds fall short of the estimate and the
+    # batch must launch again to reach the budget
+    probs = [(5, 40, 30, 3, 40 * 30 * 3 * 4), (7, 40, 60, 4, 40 * 60 * 4 * 3), (9, 64, 100, 5, 64 * 100 * 5 * 2)]
+    with m.Batch(probs, use_graph=True) as b:
+        for _ in range(2):
+            st = b.run()
+            check_same(m, probs, b.results())
+        assert st["walk_launches"] > 1
+
+
+def test_batch_vs_oracle_small(m):
+    import oracle
+    probs = [(27, 64, 4096, 1, 64 * 4096 * 14), (33, 50, 500, 12, 50 * 500 * 17 * 2)]
+    with m.Batch(probs) as b:
+        b.run()
+        for p, g in zip(probs, b.results()):
+            o = oracle.solve(p[0], [p[3]], p[1], p[2], p[4], threads=8)
+            assert g["best_E"] == int(o["best_E"][0])
+            assert np.array_equal(g["best_seq"], o["best_seq"][0])
+            assert g["evals"] == int(o["evals"][0]) and g["rounds"] == int(o["rounds"][0])
+
+
+def test_many_instances_config3_shape(m):
+    # the shape of the batched workload (odd L in [101, 223], walk length 8*D,
+    # log-uniform budgets, seed 1000+i), scaled down to 12 instances x 256 walks
+    from paper_2210_15962_gb300 import workloads
+    wl = workloads.batched_instances(n=12, walks=256, bmin=2e6, bmax=2e7)
+    probs = [(p.L, p.walks, p.walk_len, p.seed, p.step_budget) for p in wl.problems]
+    with m.Batch(probs, use_graph=True) as b:
+        b.run()
+        check_same(m, probs, b.results())
