@@ -158,6 +158,107 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """64 instances of odd L in [101, 223], 2048 walks each, walk length 8*D,
+    log-uniform budgets in [1e8, 1e10], seed 1000+i (weak scaling: rank r adds
+    1000*r to the seeds).  The batched persistent path (one CUDA-graph replay,
+    autotuned shapes) against one labs_walks launch sequence per instance."""
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    from paper_2210_15962_gb300 import workloads
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.load()
+    wl = workloads.batched_instances(n=args.instances, walks=args.batch_walks)
+    probs = [(p.L, p.walks, p.walk_len, p.seed + 1000 * rank, p.step_budget) for p in wl.problems]
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    b = pkg.Batch(probs, use_graph=True, autotune=True, stream=stream)
+    for _ in range(args.warmup):
+        b.run()
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ev = launches = planes = 0
+    kms = 0.0
+    wlaunch = 0
+    for _ in range(args.steps):
+        st = b.run()
+        ev += st["evals"]
+        launches += st["launches"]
+        planes += st["plane_steps"]
+        kms += st["walk_kernel_ms"]
+        wlaunch += st["walk_launches"]
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    res = b.results()
+    shapes = {W: b.shape(W) for W in sorted({((p[0] - 1) // 2 + 31) // 32 for p in probs})}
+    b.close()
+    barrier()
+    # the plain path: one solve per instance, each its own launch sequence
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    plain_ev = 0
+    same = True
+    t0.record(stream)
+    for i, p in enumerate(probs[:args.plain_instances]):
+        r = pkg.labs_walks(p[0], [p[3]], p[1], p[2], p[4], stream=stream)
+        plain_ev += int(r["evals"][0])
+        same = same and int(r["best_E"][0]) == res[i]["best_E"] and int(r["evals"][0]) == res[i]["evals"]
+    t1.record(stream)
+    t1.synchronize()
+    plain_s = t0.elapsed_time(t1) / 1e3
+    vals = torch.tensor([dev_s, float(ev), plain_s, float(plain_ev)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = vals.clone()
+        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(mx[2:3], op=dist.ReduceOp.MAX)
+        sm = vals.clone()
+        dist.all_reduce(sm[1:2], op=dist.ReduceOp.SUM)
+        dist.all_reduce(sm[3:4], op=dist.ReduceOp.SUM)
+        vals = torch.stack([mx[0], sm[1], mx[2], sm[3]])
+    dev_s, tot_ev, plain_s, tot_plain = [float(x) for x in vals.cpu()]
+    if rank == 0:
+        Ls = [p[0] for p in probs]
+        line = {
+            "metric": "neighbour_evals_per_s", "value": tot_ev / dev_s, "unit": "neighbour_evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (Philox starts; instances from SplitMix64 seed %d)" % workloads.MANIFEST_SEED,
+            "config": {"workload": wl.name, "instances": len(probs), "walks": args.batch_walks,
+                       "L_range": [min(Ls), max(Ls)], "walk_len": "8*D",
+                       "budget_range": [min(p[4] for p in probs), max(p[4] for p in probs)],
+                       "path": "batched persistent kernel, CUDA graph replay, autotuned shapes",
+                       "shapes": {str(k): v for k, v in shapes.items()},
+                       "l2": "visited-table pools larger than L2"},
+            "plain": {"value": tot_plain / plain_s, "unit": "neighbour_evals/s",
+                      "instances": min(args.plain_instances, len(probs)),
+                      "path": "labs_walks per instance (one launch sequence per L)",
+                      "same_results": bool(same)},
+            "gpu_launches": launches,
+            "walk_kernel_ms": kms, "walk_launches": wlaunch,
+            "plane_steps": planes,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -171,8 +272,15 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--batch-walks", type=int, default=2048)
+    ap.add_argument("--plain-instances", type=int, default=64)
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    if args.workload == "batched" and args.impl != "reference":
+        run_batched(args, world, rank, local)
+        return
 
     if args.impl == "reference":
         run_reference(args, world, rank)
