@@ -201,6 +201,75 @@ labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_thre
                              int32_t *resident_walks);
 labs_status labs_batch_destroy(labs_batch *b);
 
+/* ---------------------------------------------------------------- serving
+ * A server takes solve requests (one labs_problem each) at any time and runs
+ * them with continuous batching: a scheduler thread admits queued requests in
+ * arrival order while a slot is free and the memory budget holds their
+ * working set, runs every admitted request's next rounds together in the
+ * persistent batch kernels, hands back finished requests and admits new ones
+ * at the next launch boundary.  A request's result is exactly what labs_walks
+ * gives for it alone.  Thread-safe: any host thread may submit, poll or wait;
+ * destroy must not overlap other calls on the same server. */
+typedef struct labs_serve_cfg {
+  void *stream;              /* cudaStream_t for the server's work; NULL = its own stream */
+  size_t mem_bytes;          /* admission budget: sum over admitted requests of
+                                walks x visited-table bytes + round state (default 8 GiB) */
+  int32_t max_active;        /* requests admitted at once (slots), default 64 */
+  int32_t max_L;             /* largest L accepted (sizes the table pools), default 301 */
+  int32_t max_walks;         /* largest walks per round accepted, default 2048 */
+  int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
+  int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 2 */
+  int32_t block_threads;     /* walks per CTA of the batch kernels, default 128 */
+} labs_serve_cfg;
+
+typedef struct labs_result {
+  int32_t status;            /* LABS_OK, or why the request ended without a result
+                                (LABS_ESHUTDOWN, LABS_ECUDA, ...) */
+  int32_t L;
+  int64_t best_E;
+  double F;                  /* L^2 / (2 best_E) */
+  uint64_t evals;            /* neighbour evaluations spent */
+  int32_t rounds;
+  int32_t reached_target;    /* 1 if best_E <= the request's target */
+  uint64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady clock of the server's host */
+} labs_result;
+
+typedef struct labs_serve_stats {
+  uint64_t submitted, completed, pending, active;
+  uint64_t evals;            /* neighbour evaluations done so far */
+  uint64_t launches, walk_launches;
+  double busy_ms;            /* device time of the launches (CUDA events) */
+  uint64_t mem_used;         /* admission budget in use */
+  int32_t status;            /* LABS_OK, or the error that stopped the server */
+  int32_t reserved;
+} labs_serve_stats;
+
+typedef struct labs_server labs_server; /* opaque */
+
+/* Defaults: mem_bytes 8 GiB, max_active 64, max_L 301, max_walks 2048,
+ * max_walk_len 8 * (max_L + 1) / 2, rounds_per_launch 2, block_threads 128. */
+void labs_serve_cfg_init(labs_serve_cfg *cfg);
+/* Allocate the server (visited-table pools for every lag-word class up to
+ * max_L) and start its scheduler thread on the current device. */
+labs_status labs_serve_create(const labs_serve_cfg *cfg, labs_server **out);
+/* Queue a request; never blocks on the GPU.  LABS_EINVAL for a bad problem,
+ * LABS_ENOMEM if it can never be admitted (L, walks or walk length above the
+ * server's limits, or a working set above mem_bytes), LABS_ESHUTDOWN while
+ * destroying, or the error that stopped the server. */
+labs_status labs_serve_submit(labs_server *s, const labs_problem *req, uint64_t *ticket);
+/* LABS_PENDING while the request runs; otherwise fills *out (and best_seq[L]
+ * if not NULL), forgets the ticket and returns the request's status.
+ * LABS_ENOTFOUND for an unknown or already consumed ticket. */
+labs_status labs_serve_poll(labs_server *s, uint64_t ticket, labs_result *out, int8_t *best_seq);
+/* Like poll, but waits up to timeout_ms for the request to finish
+ * (LABS_ETIMEOUT if it has not). */
+labs_status labs_serve_wait(labs_server *s, uint64_t ticket, int64_t timeout_ms, labs_result *out,
+                            int8_t *best_seq);
+labs_status labs_serve_get_stats(labs_server *s, labs_serve_stats *out);
+/* Stop the scheduler after its current launch; requests not finished by then
+ * end with LABS_ESHUTDOWN.  Frees the server. */
+labs_status labs_serve_destroy(labs_server *s);
+
 /* Size of the fixed device scratch used by labs_saw_round_noalloc. */
 #define LABS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

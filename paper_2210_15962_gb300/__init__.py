@@ -90,6 +90,50 @@ class labs_batch_opts(ctypes.Structure):
     ]
 
 
+class labs_serve_cfg(ctypes.Structure):
+    _fields_ = [
+        ("stream", ctypes.c_void_p),
+        ("mem_bytes", ctypes.c_size_t),
+        ("max_active", ctypes.c_int32),
+        ("max_L", ctypes.c_int32),
+        ("max_walks", ctypes.c_int32),
+        ("max_walk_len", ctypes.c_int32),
+        ("rounds_per_launch", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+    ]
+
+
+class labs_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("L", ctypes.c_int32),
+        ("best_E", ctypes.c_int64),
+        ("F", ctypes.c_double),
+        ("evals", ctypes.c_uint64),
+        ("rounds", ctypes.c_int32),
+        ("reached_target", ctypes.c_int32),
+        ("t_submit_ns", ctypes.c_uint64),
+        ("t_admit_ns", ctypes.c_uint64),
+        ("t_done_ns", ctypes.c_uint64),
+    ]
+
+
+class labs_serve_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("pending", ctypes.c_uint64),
+        ("active", ctypes.c_uint64),
+        ("evals", ctypes.c_uint64),
+        ("launches", ctypes.c_uint64),
+        ("walk_launches", ctypes.c_uint64),
+        ("busy_ms", ctypes.c_double),
+        ("mem_used", ctypes.c_uint64),
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 _EXPORTS = {
@@ -119,6 +163,16 @@ _EXPORTS = {
     "labs_batch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "labs_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "labs_serve_cfg_init": (None, [ctypes.POINTER(labs_serve_cfg)]),
+    "labs_serve_create": (ctypes.c_int32, [ctypes.POINTER(labs_serve_cfg), ctypes.POINTER(ctypes.c_void_p)]),
+    "labs_serve_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_problem),
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "labs_serve_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(labs_result),
+                                         ctypes.c_void_p]),
+    "labs_serve_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.POINTER(labs_result), ctypes.c_void_p]),
+    "labs_serve_get_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_serve_stats)]),
+    "labs_serve_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
 }
 
 
@@ -331,6 +385,78 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().labs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """labs_serve_*: a continuous-batching solve server on the current device."""
+
+    def __init__(self, *, mem_bytes=None, max_active=None, max_L=None, max_walks=None, max_walk_len=None,
+                 rounds_per_launch=None, block_threads=None, stream=None):
+        c = labs_serve_cfg()
+        load().labs_serve_cfg_init(ctypes.byref(c))
+        for k, v in dict(mem_bytes=mem_bytes, max_active=max_active, max_L=max_L, max_walks=max_walks,
+                         max_walk_len=max_walk_len, rounds_per_launch=rounds_per_launch,
+                         block_threads=block_threads).items():
+            if v is not None:
+                setattr(c, k, int(v))
+        if stream is not None:
+            c.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = ctypes.c_void_p()
+        _check(load().labs_serve_create(ctypes.byref(c), ctypes.byref(h)), "labs_serve_create")
+        self._h = h
+        self._L = {}
+
+    def submit(self, L, walks, walk_len, seed, step_budget, target_E=-1) -> int:
+        p = make_problem(L, walks, walk_len, seed, step_budget, target_E)
+        t = ctypes.c_uint64()
+        _check(load().labs_serve_submit(self._h, ctypes.byref(p), ctypes.byref(t)), "labs_serve_submit")
+        self._L[t.value] = L
+        return t.value
+
+    def _out(self, st, r, seq):
+        d = {f[0]: getattr(r, f[0]) for f in labs_result._fields_}
+        d["best_seq"] = seq
+        d["latency_s"] = (r.t_done_ns - r.t_submit_ns) / 1e9 if r.t_done_ns else None
+        return d
+
+    def poll(self, ticket):
+        """None while pending, else the result dict (raises on an error status)."""
+        r = labs_result()
+        seq = np.zeros(self._L.get(ticket, LABS_L_MAX), dtype=np.int8)
+        st = load().labs_serve_poll(self._h, ticket, ctypes.byref(r), _ptr(seq))
+        if st == LABS_PENDING:
+            return None
+        _check(st, "labs_serve_poll")
+        return self._out(st, r, seq)
+
+    def wait(self, ticket, timeout_s=600.0):
+        r = labs_result()
+        seq = np.zeros(self._L.get(ticket, LABS_L_MAX), dtype=np.int8)
+        st = load().labs_serve_wait(self._h, ticket, int(timeout_s * 1000), ctypes.byref(r), _ptr(seq))
+        _check(st, "labs_serve_wait")
+        return self._out(st, r, seq)
+
+    def stats(self) -> dict:
+        s = labs_serve_stats()
+        _check(load().labs_serve_get_stats(self._h, ctypes.byref(s)), "labs_serve_get_stats")
+        return {f[0]: getattr(s, f[0]) for f in labs_serve_stats._fields_ if f[0] != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().labs_serve_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["walk_kernels.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu"]
+SOURCES = ["walk_kernels.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu", "serve.cu"]
 HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "walk_device.cuh", "batch.cuh"]
 
 

@@ -66,5 +66,7 @@ cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStrea
 // Lanes the persistent kernel of class W keeps resident with `block` threads per block.
 int batch_resident_lanes(int W, int block);
 cudaError_t launch_batch_finalize(const BatchFinalizeParams &f, cudaStream_t s);
+cudaError_t launch_init_slots(const int32_t *slots, int n, int64_t *bestE, unsigned long long *evals, int32_t *done,
+                              int32_t *rounds, int32_t *best_round, int32_t *best_walk, uint32_t *key, cudaStream_t s);
 
 }  // namespace psaw

@@ -3,6 +3,8 @@
 // problems of different L and cost share the GPU without per-problem
 // launches.  One kernel per lag-word class W (each with the register budget
 // of the per-round walk kernel of that class).
+#include <climits>
+
 #include "batch.cuh"
 #include "walk_device.cuh"
 
@@ -156,6 +158,30 @@ __global__ void batch_finalize_kernel(const BatchFinalizeParams f) {
 cudaError_t launch_batch_finalize(const BatchFinalizeParams &f, cudaStream_t s) {
   if (f.n_problems <= 0) return cudaSuccess;
   batch_finalize_kernel<<<(f.n_problems + 127) / 128, 128, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+// Reset the per-problem state of the listed slots (a serving slot taking a new request).
+__global__ void init_slots_kernel(const int32_t *slots, int n, int64_t *bestE, unsigned long long *evals,
+                                  int32_t *done, int32_t *rounds, int32_t *best_round, int32_t *best_walk,
+                                  uint32_t *key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = slots[i];
+  bestE[p] = INT64_MAX;
+  evals[p] = 0;
+  done[p] = 0;
+  rounds[p] = 0;
+  best_round[p] = -1;
+  best_walk[p] = -1;
+  for (int k = 0; k < kKeyWords; ++k) key[(size_t)p * kKeyWords + k] = 0u;
+}
+
+cudaError_t launch_init_slots(const int32_t *slots, int n, int64_t *bestE, unsigned long long *evals, int32_t *done,
+                              int32_t *rounds, int32_t *best_round, int32_t *best_walk, uint32_t *key,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  init_slots_kernel<<<(n + 127) / 128, 128, 0, s>>>(slots, n, bestE, evals, done, rounds, best_round, best_walk, key);
   return cudaGetLastError();
 }
 

@@ -67,14 +67,19 @@ def test_struct_layouts_match_c_compiler(tmp_path):
                    ' offsetof(labs_opts, workspace), offsetof(labs_opts, rounds_per_seed),'
                    ' offsetof(labs_stats, device_ms));'
                    'printf("%zu %zu %zu %zu\\n", sizeof(labs_problem), offsetof(labs_problem, target_E),'
-                   ' sizeof(labs_batch_opts), offsetof(labs_batch_opts, rounds_per_launch));return 0;}\n')
+                   ' sizeof(labs_batch_opts), offsetof(labs_batch_opts, rounds_per_launch));'
+                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(labs_serve_cfg), sizeof(labs_result),'
+                   ' offsetof(labs_result, t_done_ns), sizeof(labs_serve_stats), offsetof(labs_serve_stats, status));'
+                   'return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(m.labs_opts), ctypes.sizeof(m.labs_stats), m.labs_opts.workspace.offset,
             m.labs_opts.rounds_per_seed.offset, m.labs_stats.device_ms.offset,
             ctypes.sizeof(m.labs_problem), m.labs_problem.target_E.offset, ctypes.sizeof(m.labs_batch_opts),
-            m.labs_batch_opts.rounds_per_launch.offset]
+            m.labs_batch_opts.rounds_per_launch.offset, ctypes.sizeof(m.labs_serve_cfg),
+            ctypes.sizeof(m.labs_result), m.labs_result.t_done_ns.offset, ctypes.sizeof(m.labs_serve_stats),
+            m.labs_serve_stats.status.offset]
     assert got == want
 
 
@@ -160,3 +165,15 @@ def test_batch_rejects_bad_options(lib):
         with pytest.raises(m.LabsError) as ei:
             m.Batch([(27, 64, 100, 1, 1000)], **kw)
         assert ei.value.status == m.LABS_EINVAL
+
+
+def test_serve_rejects_bad_config(lib):
+    import paper_2210_15962_gb300 as m
+    for kw in [dict(max_active=0), dict(max_L=100), dict(max_L=1001), dict(rounds_per_launch=0),
+               dict(block_threads=40), dict(mem_bytes=0), dict(max_walks=0)]:
+        with pytest.raises(m.LabsError) as ei:
+            m.Server(**kw)
+        assert ei.value.status == m.LABS_EINVAL
+    assert lib.labs_serve_submit(None, None, None) == m.LABS_EINVAL
+    assert lib.labs_serve_poll(None, 1, None, None) == m.LABS_EINVAL
+    assert lib.labs_serve_destroy(None) == m.LABS_EINVAL

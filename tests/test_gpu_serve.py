@@ -1,0 +1,126 @@
+"""Serving with continuous batching: every request's result is exactly what
+labs_walks gives for it alone, whether submitted at once, while others run,
+or throttled by memory admission; plus the server's error paths (bad or
+oversized requests, unknown tickets, timeouts, shutdown with work in flight).
+All failures here are made on the host: no GPU fault is involved."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2210_15962_gb300 import build
+    build.build()
+    import paper_2210_15962_gb300 as mod
+    mod.load()
+    return mod
+
+
+def alone(m, p):
+    L, walks, wl, seed, budget = p[:5]
+    tgt = p[5] if len(p) > 5 else -1
+    r = m.labs_walks(L, [seed], walks, wl, budget, target_E=tgt)
+    return int(r["best_E"][0]), r["best_seq"][0], int(r["evals"][0]), int(r["rounds"][0])
+
+
+def check(m, p, res):
+    E, seq, ev, rd = alone(m, p)
+    assert res["status"] == m.LABS_OK
+    assert res["best_E"] == E and np.array_equal(res["best_seq"], seq), p
+    assert res["evals"] == ev and res["rounds"] == rd, p
+    assert res["t_submit_ns"] <= res["t_admit_ns"] <= res["t_done_ns"]
+
+
+REQS = [
+    (27, 64, 216, 1, 64 * 216 * 14 * 3),
+    (121, 256, 488, 2, 256 * 488 * 61 * 2),
+    (131, 128, 528, 3, 128 * 528 * 66 * 3),
+    (223, 96, 896, 4, 1),
+    (301, 64, 1208, 5, 64 * 1208 * 151 * 2),
+    (161, 200, 648, 6, 10 ** 12, 3300),  # target: stops after the first round reaching E <= 3300
+]
+
+
+def test_requests_same_alone_and_mixed(m):
+    with m.Server(max_walks=256) as sv:
+        tickets = [sv.submit(*p) for p in REQS]
+        results = [sv.wait(t) for t in tickets]
+        for p, r in zip(REQS, results):
+            check(m, p, r)
+        st = sv.stats()
+        assert st["completed"] == len(REQS) and st["pending"] == 0 and st["active"] == 0
+        assert st["evals"] == sum(r["evals"] for r in results)
+
+
+def test_requests_arriving_while_others_run(m):
+    with m.Server(max_walks=256, rounds_per_launch=1) as sv:
+        tickets = []
+        seen_active = 0
+        for p in REQS:
+            tickets.append(sv.submit(*p))
+            time.sleep(0.05)
+            seen_active = max(seen_active, sv.stats()["active"])
+        results = [sv.wait(t) for t in tickets]
+        for p, r in zip(REQS, results):
+            check(m, p, r)
+        assert seen_active >= 2  # later requests joined while earlier ones were on the GPU
+
+
+def test_memory_admission_serialises_and_rejects(m):
+    big = (121, 256, 488, 7, 256 * 488 * 61 * 3)
+    # a budget that holds one such request at a time
+    one = 256 * 1024 * 8 + 4096 * 2  # 256 walks x 1024-slot tables x 8 B + round state
+    with m.Server(max_walks=256, mem_bytes=int(one * 1.5)) as sv:
+        t1 = sv.submit(*big)
+        t2 = sv.submit(121, 256, 488, 8, 256 * 488 * 61)
+        r1, r2 = sv.wait(t1), sv.wait(t2)
+        check(m, big, r1)
+        check(m, (121, 256, 488, 8, 256 * 488 * 61), r2)
+        assert r2["t_admit_ns"] >= r1["t_done_ns"]  # admitted only once the first left
+        with pytest.raises(m.LabsError) as ei:
+            sv.submit(121, 256, 4000, 9, 10 ** 9)  # working set above the budget
+        assert ei.value.status == m.LABS_ENOMEM
+        with pytest.raises(m.LabsError) as ei:
+            sv.submit(401, 64, 100, 9, 10 ** 6)  # above the server's max_L
+        assert ei.value.status == m.LABS_ENOMEM
+        with pytest.raises(m.LabsError) as ei:
+            sv.submit(120, 64, 100, 9, 10 ** 6)  # even L
+        assert ei.value.status == m.LABS_EINVAL
+
+
+def test_tickets_timeouts_and_shutdown(m):
+    sv = m.Server(max_walks=2048, max_active=2)
+    with pytest.raises(m.LabsError) as ei:
+        sv.poll(12345)
+    assert ei.value.status == m.LABS_ENOTFOUND
+    long_req = (301, 2048, 1208, 11, 2048 * 1208 * 151 * 4)
+    t = sv.submit(*long_req)
+    with pytest.raises(m.LabsError) as ei:
+        sv.wait(t, timeout_s=0.001)
+    assert ei.value.status == m.LABS_ETIMEOUT
+    assert sv.poll(t) is None  # still pending
+    queued = [sv.submit(121, 2048, 488, 20 + i, 10 ** 10) for i in range(4)]
+    # concurrent pollers from other threads while the server runs
+    seen = []
+
+    def poller():
+        for _ in range(20):
+            try:
+                seen.append(sv.poll(queued[-1]))
+            except m.LabsError:
+                pass
+            time.sleep(0.005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    th.join()
+    t0 = time.time()
+    sv.close()  # shutdown with work in flight and queued: must not hang
+    assert time.time() - t0 < 120
