@@ -259,6 +259,83 @@ def run_batched(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_serving(args, world, rank, local):
+    """Poisson request stream (mean args.rate/s for args.serve_seconds s) of odd L
+    uniform in [121, 301], 2048 walks, walk length 8*D, budget 1e10, stop at
+    the budget or at a per-L target energy; continuous batching with memory
+    admission.  Targets: for each L, the best energy the plain path reaches
+    with a calibration budget (args.target_budget) and seed 99."""
+    import numpy as np
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    from paper_2210_15962_gb300 import workloads
+    torch.cuda.set_device(local)
+    pkg.load()
+    wl = workloads.serving_stream(duration_s=args.serve_seconds, rate_per_s=args.rate, budget=args.serve_budget)
+    reqs = wl.problems
+    # per-L targets from the plain path
+    targets = {}
+    for L in sorted({p.L for p in reqs}):
+        wlen = workloads.paper_walk_len(L)
+        r = pkg.labs_walks(L, [99], 2048, wlen, args.target_budget)
+        targets[L] = int(r["best_E"][0])
+    sampler = ClockSampler(local)
+    sv = pkg.Server(max_L=301, max_walks=2048, max_active=args.max_active, mem_bytes=args.mem_gib << 30,
+                    rounds_per_launch=args.rounds_per_launch)
+    # warm-up: a few requests end to end
+    for i in range(args.warmup):
+        p = reqs[i % len(reqs)]
+        sv.wait(sv.submit(p.L, p.walks, p.walk_len, 10 ** 6 + i, p.walk_len * p.walks))
+    sampler.start()
+    tickets = []
+    t0 = time.perf_counter()
+    for p in reqs:
+        delay = t0 + p.arrival_s - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(sv.submit(p.L, p.walks, p.walk_len, p.seed, p.step_budget, targets[p.L]))
+    results = [sv.wait(t, timeout_s=3600) for t in tickets]
+    t1 = time.perf_counter()
+    clocks = sampler.stop()
+    st = sv.stats()
+    sv.close()
+    lat = np.array([r["latency_s"] for r in results])
+    qwait = np.array([(r["t_admit_ns"] - r["t_submit_ns"]) / 1e9 for r in results])
+    evals = sum(r["evals"] for r in results)
+    reached = sum(r["reached_target"] for r in results)
+    # the plain path on the first requests, one labs_walks per request
+    tp0 = time.perf_counter()
+    plain_ev = 0
+    same = True
+    for p, r in list(zip(reqs, results))[:args.plain_requests]:
+        g = pkg.labs_walks(p.L, [p.seed], p.walks, p.walk_len, p.step_budget, target_E=targets[p.L])
+        plain_ev += int(g["evals"][0])
+        same = same and int(g["best_E"][0]) == r["best_E"] and int(g["evals"][0]) == r["evals"]
+    tp1 = time.perf_counter()
+    line = {
+        "metric": "neighbour_evals_per_s", "value": evals / (t1 - t0), "unit": "neighbour_evals/s",
+        "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": (t1 - t0) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic request stream (SplitMix64 seed %d)" % workloads.MANIFEST_SEED,
+        "config": {"workload": wl.name, "requests": len(reqs), "duration_s": args.serve_seconds,
+                   "rate_per_s": args.rate, "walks": 2048, "walk_len": "8*D", "budget": args.serve_budget,
+                   "targets": "per L: plain-path best with budget %g, seed 99" % args.target_budget,
+                   "max_active": args.max_active, "mem_gib": args.mem_gib,
+                   "rounds_per_launch": args.rounds_per_launch},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
+        "completed": len(results), "reached_target": int(reached),
+        "device_busy_frac": st["busy_ms"] / 1e3 / (t1 - t0),
+        "plain": {"value": plain_ev / (tp1 - tp0), "unit": "neighbour_evals/s",
+                  "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
+                  "same_results": bool(same)},
+        "gpu_launches": st["launches"], "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,7 +349,15 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--serve-budget", type=int, default=10 ** 10)
+    ap.add_argument("--target-budget", type=int, default=2 * 10 ** 9)
+    ap.add_argument("--max-active", type=int, default=64)
+    ap.add_argument("--mem-gib", type=int, default=16)
+    ap.add_argument("--rounds-per-launch", type=int, default=4)
+    ap.add_argument("--plain-requests", type=int, default=10)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=64)
@@ -280,6 +365,9 @@ def main():
     world, rank, local = dist_setup()
     if args.workload == "batched" and args.impl != "reference":
         run_batched(args, world, rank, local)
+        return
+    if args.workload == "serving" and args.impl != "reference":
+        run_serving(args, world, rank, local)
         return
 
     if args.impl == "reference":

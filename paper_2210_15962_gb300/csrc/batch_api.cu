@@ -115,12 +115,20 @@ struct labs_batch {
   bool graph_plan_built = false;
   int launches_per_graph = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> graph_events;
+  // one stream per class so the classes' persistent kernels overlap (each
+  // class's tail runs beside the next class's work)
+  std::vector<cudaStream_t> cs;
+  std::vector<cudaEvent_t> cs_done;
+  cudaEvent_t fork = nullptr;
 
   ~labs_batch();
 };
 
 labs_batch::~labs_batch() {
   if (graph) cudaGraphExecDestroy(graph);
+  for (auto x : cs) cudaStreamDestroy(x);
+  for (auto e : cs_done) cudaEventDestroy(e);
+  if (fork) cudaEventDestroy(fork);
   for (auto &pe : graph_events) {
     cudaEventDestroy(pe.first);
     cudaEventDestroy(pe.second);
@@ -313,21 +321,28 @@ labs_status enqueue_launch(labs_batch *b, size_t n_slots, std::vector<std::pair<
     BCU(cudaMemsetAsync(b->d_slot_evals, 0, sizeof(unsigned long long) * n_slots, b->s));
   }
   BCU(cudaMemsetAsync(b->d_task_next, 0, sizeof(unsigned int) * b->cls.size(), b->s));
+  // fork: every class's kernel on its own stream after the resets, join before the finalize
+  BCU(cudaEventRecord(b->fork, b->s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ev) {
+    BCU(cudaEventCreate(&e0));
+    BCU(cudaEventCreate(&e1));
+    BCU(cudaEventRecord(e0, b->s));
+  }
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
     ClassPlan &c = b->cls[ci];
-    if (c.n_tasks == 0) continue;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ev) {
-      BCU(cudaEventCreate(&e0));
-      BCU(cudaEventCreate(&e1));
-      BCU(cudaEventRecord(e0, b->s));
+    cudaStream_t x = b->cs[ci];
+    BCU(cudaStreamWaitEvent(x, b->fork, 0));
+    if (c.n_tasks) {
+      BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr));
+      ++*launches;
     }
-    BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), b->s, nullptr));
-    if (ev) {
-      BCU(cudaEventRecord(e1, b->s));
-      ev->push_back({e0, e1});
-    }
-    ++*launches;
+    BCU(cudaEventRecord(b->cs_done[ci], x));
+    BCU(cudaStreamWaitEvent(b->s, b->cs_done[ci], 0));
+  }
+  if (ev) {
+    BCU(cudaEventRecord(e1, b->s));
+    ev->push_back({e0, e1});
   }
   BatchFinalizeParams f{};
   f.n_problems = (int32_t)b->pr.size();
@@ -536,6 +551,15 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (cudaMemcpy(b->d_budget, bud.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_target, tgt.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(LABS_ECUDA);
+  for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+    cudaStream_t x;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
+    b->cs.push_back(x);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
+    b->cs_done.push_back(e);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
   if ((st = build_pools(b)) != LABS_OK) return fail(st);
   if (opts.autotune) {
     for (size_t ci = 0; ci < b->cls.size(); ++ci) {
@@ -596,9 +620,9 @@ extern "C" labs_status labs_batch_run(labs_batch *b, labs_stats *stats) {
       size_t n_slots = 0;
       if ((st = plan_launch(b, next_round, done, evals, &n_slots)) != LABS_OK) return st;
       if (first && (st = reset_state(b, &launches)) != LABS_OK) return st;
-      const size_t before = ev.size();
+      const int before = launches;
       if ((st = enqueue_launch(b, n_slots, &ev, &launches)) != LABS_OK) return st;
-      walk_launches += (int)(ev.size() - before);
+      walk_launches += launches - before - 1;  // the finalize is the one non-walk launch
       continued = continued || !first;
     }
     first = false;

@@ -117,6 +117,9 @@ struct labs_server {
   int32_t *d_err = nullptr;
   int8_t *d_seq = nullptr;
   std::vector<ClassPool> pools;  // index W-1
+  std::vector<cudaStream_t> cs;  // one stream per class (overlapping kernels)
+  std::vector<cudaEvent_t> cs_done;
+  cudaEvent_t fork = nullptr;
 
   ~labs_server();
   void loop();
@@ -124,6 +127,9 @@ struct labs_server {
 };
 
 labs_server::~labs_server() {
+  for (auto x : cs) cudaStreamDestroy(x);
+  for (auto e : cs_done) cudaEventDestroy(e);
+  if (fork) cudaEventDestroy(fork);
   for (auto &c : pools) {
     cudaFree(c.pool);
     cudaFree(c.tasks);
@@ -228,9 +234,11 @@ labs_status labs_server::step(std::vector<int> &active) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
+  if (cudaEventRecord(fork, s) != cudaSuccess) return LABS_ECUDA;
   for (size_t ci = 0; ci < pools.size(); ++ci) {
     ClassPool &c = pools[ci];
     if (!c.n_tasks) continue;
+    if (cudaStreamWaitEvent(cs[ci], fork, 0) != cudaSuccess) return LABS_ECUDA;
     BatchKernelParams k{};
     k.probs = d_probs;
     k.tasks = c.tasks;
@@ -250,7 +258,9 @@ labs_status labs_server::step(std::vector<int> &active) {
     k.mul_h30 = 0x40000000u;
     k.plane_steps = d_planes;
     k.err = d_err;
-    if (launch_batch(c.W, cfg.block_threads, k, s, nullptr) != cudaSuccess) return LABS_ECUDA;
+    if (launch_batch(c.W, cfg.block_threads, k, cs[ci], nullptr) != cudaSuccess) return LABS_ECUDA;
+    if (cudaEventRecord(cs_done[ci], cs[ci]) != cudaSuccess || cudaStreamWaitEvent(s, cs_done[ci], 0) != cudaSuccess)
+      return LABS_ECUDA;
     ++walk_launches;
     ++launches;
   }
@@ -439,7 +449,7 @@ extern "C" void labs_serve_cfg_init(labs_serve_cfg *c) {
   c->max_L = 301;
   c->max_walks = 2048;
   c->max_walk_len = 0;
-  c->rounds_per_launch = 2;
+  c->rounds_per_launch = 4;
   c->block_threads = 128;
 }
 
@@ -501,7 +511,14 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
     if (c.resident <= 0) return fail(LABS_ECUDA);
     sv->pools.push_back(c);
     if (dalloc(&sv->pools.back().pool, (size_t)c.resident * c.words)) return fail(LABS_ENOMEM);
+    cudaStream_t x;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
+    sv->cs.push_back(x);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
+    sv->cs_done.push_back(e);
   }
+  if (cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
   try {
     sv->th = std::thread([sv]() { sv->loop(); });
   } catch (...) {
