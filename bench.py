@@ -42,6 +42,23 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
+# DRAM traffic of one walk-kernel launch of the default workload, from the ncu
+# capture summarised in profiles/walk_kernel_L121_107008x1024_ncu_full.md
+# (18.19 GB for 107008 walks x 1024 steps, scaled by walk-steps to 131072 x 8192),
+# valid only for the kernel sources it was captured from.
+TRAFFIC = {"sources_sha256_prefix": "b9fc60650ccdad84", "bytes_per_launch": 18.19e9 * (131072 * 8192) / (107008 * 1024)}
+WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_kernels.cu", "walk_kernels.cuh"]
+
+
+def walk_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in WALK_SOURCES:
+        with open(os.path.join(ROOT, "paper_2210_15962_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def digits_for(L):
     T = 1
     while (1 << T) < L - 1:
@@ -111,6 +128,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rank_seed(rank):
+    """Each rank solves its own independent problem (weak scaling)."""
+    return SEED + rank
+
+
+def combine_ranks(times, counts, dist=None, device="cpu"):
+    """Whole-job totals over ranks: the maximum of each time, the sum of each count.
+    Host-side control only (no data-path collective); works with nccl or gloo."""
+    import torch
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()], [float(x) for x in c.cpu()]
 
 
 def dist_setup():
@@ -222,16 +256,7 @@ def run_batched(args, world, rank, local):
     t1.record(stream)
     t1.synchronize()
     plain_s = t0.elapsed_time(t1) / 1e3
-    vals = torch.tensor([dev_s, float(ev), plain_s, float(plain_ev)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        mx = vals.clone()
-        dist.all_reduce(mx[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(mx[2:3], op=dist.ReduceOp.MAX)
-        sm = vals.clone()
-        dist.all_reduce(sm[1:2], op=dist.ReduceOp.SUM)
-        dist.all_reduce(sm[3:4], op=dist.ReduceOp.SUM)
-        vals = torch.stack([mx[0], sm[1], mx[2], sm[3]])
-    dev_s, tot_ev, plain_s, tot_plain = [float(x) for x in vals.cpu()]
+    (dev_s, plain_s), (tot_ev, tot_plain) = combine_ranks([dev_s, plain_s], [ev, plain_ev], dist, "cuda")
     if rank == 0:
         Ls = [p[0] for p in probs]
         line = {
@@ -385,7 +410,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.load()
     stream = torch.cuda.Stream()
-    seed = SEED + rank
+    seed = rank_seed(rank)
     L = args.L
     walks, wl, budget = args.walks, args.walk_len, args.budget
     ws_bytes = pkg.labs_walks_workspace_size(L, 1, walks, wl)
@@ -450,14 +475,7 @@ def main():
     e2e_s = t1 - t0
 
     # ---- max over ranks, totals over ranks
-    vals = torch.tensor([dev_s, e2e_s, float(total_evals), float(e2e_evals)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        mx = vals.clone()
-        dist.all_reduce(mx[0:2], op=dist.ReduceOp.MAX)
-        sm = vals.clone()
-        dist.all_reduce(sm[2:4], op=dist.ReduceOp.SUM)
-        vals = torch.cat([mx[0:2], sm[2:4]])
-    dev_s, e2e_s, tot_evals, tot_e2e = [float(x) for x in vals.cpu()]
+    (dev_s, e2e_s), (tot_evals, tot_e2e) = combine_ranks([dev_s, e2e_s], [total_evals, e2e_evals], dist, "cuda")
 
     if rank == 0:
         value = tot_evals / dev_s
@@ -481,7 +499,10 @@ def main():
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GiB of visited tables per round" % (ws_bytes / 2 ** 30)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (TRAFFIC["bytes_per_launch"]
+                                     if (walk_sources_hash() == TRAFFIC["sources_sha256_prefix"]
+                                         and (L, walks, wl) == (DEFAULT_L, WALKS, WALK_LEN)) else None),
                          "kernel": "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32),
                          "kernel_ms_per_launch": per_launch_ms,
                          "ops_per_eval": ops_per_eval, "avg_digit_planes": avg_planes,
