@@ -361,6 +361,62 @@ def run_serving(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_large(args, world, rank, local):
+    """L=449 (D=225), 65536 walks x 16384 steps per round, seed 1+rank.  The plain
+    path (labs_walks: one walk-kernel launch per round) runs R rounds; its best
+    energy is the target.  Time-to-target of the plain path and of the
+    persistent batch path (one round per launch, no wave quantisation) for that
+    target; both reach it in the same round, so the difference is speed only."""
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    L, walks, wl, seed = 449, args.walks_large, args.walk_len_large, rank_seed(rank)
+    D = (L + 1) // 2
+    per_round = walks * wl * D
+    budget = args.large_rounds * per_round
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ref, t_ref = timed(lambda: pkg.labs_walks(L, [seed], walks, wl, budget, stream=stream))
+    target = int(ref["best_E"][0])
+    plain, t_plain = timed(lambda: pkg.labs_walks(L, [seed], walks, wl, budget, target_E=target, stream=stream))
+    b = pkg.Batch([(L, walks, wl, seed, budget, target)], rounds_per_launch=1, stream=stream)
+    bst, t_batch = timed(b.run)
+    bres = b.result(0)
+    b.close()
+    b2 = pkg.Batch([(L, walks, wl, seed, budget)], stream=stream)
+    b2st, t_batch_full = timed(b2.run)
+    b2res = b2.result(0)
+    b2.close()
+    clocks = sampler.stop()
+    line = {
+        "metric": "neighbour_evals_per_s", "value": b2st["evals"] / t_batch_full, "unit": "neighbour_evals/s",
+        "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": t_batch_full * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox starts, seed %d)" % seed,
+        "config": {"workload": "plain_vs_batched_L449_%dx%d_%drounds" % (walks, wl, args.large_rounds), "L": L,
+                   "walks": walks, "walk_len": wl, "rounds": args.large_rounds},
+        "plain": {"value": int(ref["evals"][0]) / t_ref, "seconds": t_ref, "best_E": target,
+                  "F": L * L / (2.0 * target)},
+        "batched": {"value": b2st["evals"] / t_batch_full, "seconds": t_batch_full, "best_E": b2res["best_E"],
+                    "same_result": b2res["best_E"] == target and b2res["evals"] == int(ref["evals"][0])},
+        "time_to_target_s": {"target_E": target, "plain": t_plain, "batched": t_batch,
+                             "round_reached": int(plain["rounds"][0]),
+                             "same_round": int(plain["rounds"][0]) == bres["rounds"]},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,7 +430,10 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
+    ap.add_argument("--large-rounds", type=int, default=3)
+    ap.add_argument("--walks-large", type=int, default=65536)
+    ap.add_argument("--walk-len-large", type=int, default=16384)
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--serve-budget", type=int, default=10 ** 10)
@@ -393,6 +452,9 @@ def main():
         return
     if args.workload == "serving" and args.impl != "reference":
         run_serving(args, world, rank, local)
+        return
+    if args.workload == "large" and args.impl != "reference":
+        run_large(args, world, rank, local)
         return
 
     if args.impl == "reference":

@@ -42,6 +42,7 @@ constexpr int kMaxWords = 8;      // 32-bit words of lags (m <= 32 * kMaxWords)
 constexpr int kKeyWords = 9;      // 32-bit words of a key (D bits + occupancy flag)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kDeltaBias = 1 << 22;  // |Delta| < 2^21 for L <= 511
+constexpr int kSkipMaxWords = 4;     // classes up to this many lag words skip empty word sides
 
 LABS_HD uint32_t popc32(uint32_t x) {
 #if defined(__CUDA_ARCH__)
@@ -362,23 +363,21 @@ LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
 template <int W, int T, int TP, bool CENTRE>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
                           const uint32_t (&Vx)[W], const uint32_t (&Vy)[W], const uint32_t (&Pm)[W], uint32_t ba,
-                          uint32_t bm, int a, int n, int nxy) {
+                          uint32_t bm, int a, int n, int nxy, int t, int Nq) {
   uint32_t acc = 0;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
+    // which sides have valid lags in this word (the same for every lane of the warp):
+    // x lags i <= t, y lags i <= Nq-1-t; a word with one side needs no carry-save adder.
+    // Wide classes keep every word on the two-sided path: with few resident warps
+    // they rely on the compiler interleaving the words' independent chains.
+    constexpr bool kSkip = W <= kSkipMaxWords;
+    const bool xa = kSkip ? (t > 32 * w) : true;
+    const bool ya = kSkip ? (!CENTRE && (Nq - 1 - t > 32 * w)) : !CENTRE;
     const uint32_t vx = Vx[w];
     uint32_t p[TP + 1];
-    uint32_t v;
-    if (CENTRE) {
-#pragma unroll
-      for (int tt = 0; tt < TP; ++tt) {
-        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
-        p[tt] = popc32(vx & (B[w] ^ e));
-      }
-      v = p[TP - 1];
-#pragma unroll
-      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);
-    } else {
+    uint32_t v = 0;
+    if (xa && ya) {
       const uint32_t vy = Vy[w] & ~Pm[w];
       uint32_t carry = 0;
 #pragma unroll
@@ -396,6 +395,17 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
 #pragma unroll
       for (int tt = TP - 1; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);  // Horner: sum_t 2^t p_t
       v = imad(z, mu.four, v);
+    } else if (xa || ya) {
+      const uint32_t m = xa ? vx : (Vy[w] & ~Pm[w]);
+      const uint32_t g = xa ? B[w] : F[w];
+#pragma unroll
+      for (int tt = 0; tt < TP; ++tt) {
+        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
+        p[tt] = popc32(m & (g ^ e));
+      }
+      v = p[TP - 1];
+#pragma unroll
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);
     }
     acc = imad(acc, mu.one, v);
   }
@@ -435,7 +445,7 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
       const int a = 2 * t + q;
       const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
       const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
-      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, n, nxy);
+      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, n, nxy, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
       // advance the windows and masks by one lag (shifts as IMAD on the FMA pipe)
@@ -457,7 +467,7 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
     }
     if (has_centre) {
       const int t = nloop, a = g.c;
-      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, t, 0);
+      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, t, 0, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
     }
