@@ -431,6 +431,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
+    ap.add_argument("--kernel", type=int, default=0, help="0 library choice, 1 full scan, 2 incremental")
     ap.add_argument("--large-rounds", type=int, default=3)
     ap.add_argument("--walks-large", type=int, default=65536)
     ap.add_argument("--walk-len-large", type=int, default=16384)
@@ -483,7 +484,7 @@ def main():
 
     def device_step():
         return pkg.labs_walks_device(L, seeds_d, walks, wl, budget, best_seq_d, best_E_d, stream=stream,
-                                     workspace=ws)
+                                     workspace=ws, kernel=args.kernel)
 
     def barrier():
         if dist is not None:
@@ -524,11 +525,11 @@ def main():
     e2e_evals = 0
     t0 = t1 = 0.0
     if not args.device_only:
-        pkg.labs_walks(L, [seed], walks, wl, budget)  # first call maps the allocator pool
+        pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel)  # first call maps the allocator pool
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            r = pkg.labs_walks(L, [seed], walks, wl, budget)
+            r = pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel)
             e2e_evals += int(r["evals"].sum())
         t1 = time.perf_counter()
         barrier()

@@ -77,7 +77,11 @@ typedef struct labs_opts {
   int64_t target_E;       /* stop a problem after the first round whose best E <= target_E;
                              < 0 = no target.  Set to -1 by labs_opts_init. */
   int32_t max_rounds;     /* 0 = no limit; else stop every problem after this many rounds */
-  int32_t reserved0;
+  int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (the full
+                             scan, the faster of the two on GB300 at every L),
+                             1 = full scan (every neighbour from the correlations each step),
+                             2 = incremental (stored neighbour deltas updated after each move);
+                             all give the same results; other values: LABS_EINVAL */
   void *workspace;        /* optional device scratch of workspace_bytes bytes (e.g. from
                              PyTorch); NULL = the library allocates and frees it itself */
   size_t workspace_bytes;
@@ -143,14 +147,15 @@ size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_s
  *     of walks trace_begin..trace_begin+trace_count-1 (unused tail = -1);
  *   visited_keys[visited_cap*((D+63)/64)]: if not NULL, the free-bit keys of
  *     every pivot of walk `visited_walk` (bit j = 1 <-> s_{j+1} = -1), one
- *     per entry in table order, and *visited_count = how many.
+ *     per entry in table order, and *visited_count = how many;
+ *   kernel: as labs_opts.kernel.
  * Returns like labs_walks. */
 labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
                            int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
                            int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
                            int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
                            int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
-                           int32_t *visited_count);
+                           int32_t *visited_count, int32_t kernel);
 
 /* ---------------------------------------------------------------- batches
  * Many independent problems of uneven L solved together (Eq. 4 rounds of

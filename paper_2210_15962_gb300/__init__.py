@@ -27,6 +27,9 @@ LABS_ECHECK = -7
 LABS_ESHUTDOWN = -8
 LABS_L_MIN = 5
 LABS_L_MAX = 511
+KERNEL_AUTO = 0
+KERNEL_FULL_SCAN = 1
+KERNEL_INCREMENTAL = 2
 
 
 class LabsError(RuntimeError):
@@ -42,7 +45,7 @@ class labs_opts(ctypes.Structure):
         ("recheck_every", ctypes.c_int32),
         ("target_E", ctypes.c_int64),
         ("max_rounds", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("kernel", ctypes.c_int32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("evals_per_seed", ctypes.c_void_p),
@@ -151,7 +154,7 @@ _EXPORTS = {
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
-                                        ctypes.c_int32, ctypes.c_void_p]),
+                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32]),
     "labs_saw_round_noalloc": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
@@ -233,7 +236,7 @@ def labs_energy_batch(seqs, stream=None, check: bool = True):
 
 
 def make_opts(stream=None, device_buffers=False, recheck_every=0, target_E=-1, max_rounds=0, workspace=None,
-              evals_per_seed=None, rounds_per_seed=None) -> labs_opts:
+              evals_per_seed=None, rounds_per_seed=None, kernel=0) -> labs_opts:
     o = labs_opts()
     load().labs_opts_init(ctypes.byref(o))
     if stream is not None:
@@ -242,6 +245,7 @@ def make_opts(stream=None, device_buffers=False, recheck_every=0, target_E=-1, m
     o.recheck_every = int(recheck_every)
     o.target_E = int(target_E)
     o.max_rounds = int(max_rounds)
+    o.kernel = int(kernel)
     if workspace is not None:
         o.workspace = ctypes.c_void_p(workspace.data_ptr())
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -259,7 +263,7 @@ def labs_walks_workspace_size(L: int, n_seeds: int, walks_per_seed: int, walk_le
 
 
 def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, *, target_E: int = -1,
-               max_rounds: int = 0, recheck_every: int = 0, stream=None, workspace=None) -> dict:
+               max_rounds: int = 0, recheck_every: int = 0, stream=None, workspace=None, kernel: int = 0) -> dict:
     """Algorithm 1 around Algorithm 2 for every seed; host buffers in and out.
 
     Returns dict(best_seq=(n, L) int8, best_E=(n,) int64, evals=(n,) uint64,
@@ -272,7 +276,7 @@ def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: i
     evals = np.zeros(n, dtype=np.uint64)
     rounds = np.zeros(n, dtype=np.int32)
     o = make_opts(stream=stream, recheck_every=recheck_every, target_E=target_E, max_rounds=max_rounds,
-                  workspace=workspace, evals_per_seed=evals, rounds_per_seed=rounds)
+                  workspace=workspace, evals_per_seed=evals, rounds_per_seed=rounds, kernel=kernel)
     stats = labs_stats()
     _check(load().labs_walks(L, _ptr(sd), n, walks_per_seed, walk_len, step_budget, _ptr(best_seq), _ptr(best_E),
                              ctypes.byref(o), ctypes.byref(stats)), "labs_walks")
@@ -281,12 +285,12 @@ def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: i
 
 def labs_walks_device(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, best_seq, best_E, *,
                       target_E: int = -1, max_rounds: int = 0, recheck_every: int = 0, stream=None,
-                      workspace=None, evals_per_seed=None, rounds_per_seed=None) -> dict:
+                      workspace=None, evals_per_seed=None, rounds_per_seed=None, kernel: int = 0) -> dict:
     """labs_walks on device-resident buffers (torch CUDA tensors): seeds int64/uint64 (n,),
     best_seq int8 (n, L), best_E int64 (n,).  Stream-ordered; returns the call's stats."""
     o = make_opts(stream=stream, device_buffers=True, recheck_every=recheck_every, target_E=target_E,
                   max_rounds=max_rounds, workspace=workspace, evals_per_seed=evals_per_seed,
-                  rounds_per_seed=rounds_per_seed)
+                  rounds_per_seed=rounds_per_seed, kernel=kernel)
     stats = labs_stats()
     _check(load().labs_walks(L, ctypes.c_void_p(seeds.data_ptr()), seeds.numel(), walks_per_seed, walk_len,
                              step_budget, ctypes.c_void_p(best_seq.data_ptr()), ctypes.c_void_p(best_E.data_ptr()),
@@ -295,7 +299,7 @@ def labs_walks_device(L: int, seeds, walks_per_seed: int, walk_len: int, step_bu
 
 
 def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, *, recheck_every: int = 0,
-                   trace_begin: int = 0, trace_count: int = 0, visited_walk: int = -1) -> dict:
+                   trace_begin: int = 0, trace_count: int = 0, visited_walk: int = -1, kernel: int = 0) -> dict:
     """One round of walks 0..n_walks-1 with per-walk results (and optional traces / visited keys)."""
     D = (L + 1) // 2
     best_E = np.zeros(n_walks, dtype=np.int64)
@@ -312,7 +316,7 @@ def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, 
                                  _ptr(moves), _ptr(stuck), _ptr(best_step), _ptr(trace) if trace is not None else None,
                                  trace_begin, trace_count, visited_walk,
                                  _ptr(visited) if visited is not None else None, vcap,
-                                 _ptr(vcount) if visited is not None else None), "labs_saw_round")
+                                 _ptr(vcount) if visited is not None else None, kernel), "labs_saw_round")
     out = {"best_E": best_E, "best_seq": best_seq, "moves": moves, "stuck": stuck, "best_step": best_step}
     if trace is not None:
         out["trace"] = trace

@@ -136,7 +136,17 @@ struct RunConfig {
   uint64_t budget;
   int64_t target;
   int32_t max_rounds;
+  int32_t kernel;
 };
+
+// The library's choice of neighbourhood evaluation for labs_opts.kernel == 0.
+// The library's choice: the full scan, measured faster than the incremental
+// variant at every lag-word class (the incremental pass pays a fixed per-flip
+// cost at small W and is occupancy-limited by its shared-memory state at large W).
+int32_t resolve_variant(int32_t kernel) {
+  if (kernel == kVariantFullScan || kernel == kVariantIncremental) return kernel;
+  return kVariantFullScan;
+}
 
 }  // namespace
 }  // namespace psaw
@@ -289,6 +299,7 @@ struct Run {
     p.p_round_best = b.p_round_best;
     p.err = b.err;
     p.plane_steps = b.plane_steps;
+    p.variant = resolve_variant(cfg.kernel);
     set_muls(p);
     return p;
   }
@@ -372,13 +383,14 @@ extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_se
   if (opts_in) opts = *opts_in;
   else labs_opts_init(&opts);
   if (!valid_L(L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1 ||
-      walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0)
+      walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0 ||
+      opts.kernel < 0 || opts.kernel > 2)
     return LABS_EINVAL;
   if ((uint64_t)n_seeds * (uint64_t)walks_per_seed > (1ull << 31)) return LABS_EINVAL;
   labs_status st = LABS_OK;
   Run run;
   run.cfg = RunConfig{L, n_seeds, walks_per_seed, walk_len, opts.recheck_every, step_budget, opts.target_E,
-                      opts.max_rounds};
+                      opts.max_rounds, opts.kernel};
   run.s = (cudaStream_t)opts.stream;
   const cudaMemcpyKind in_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind out_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -449,15 +461,17 @@ extern "C" labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, 
                                       int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
                                       int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
                                       int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
-                                      int32_t *visited_count) {
-  if (!valid_L(L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0) return LABS_EINVAL;
+                                      int32_t *visited_count, int32_t kernel) {
+  if (!valid_L(L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 || kernel < 0 ||
+      kernel > 2)
+    return LABS_EINVAL;
   if (trace_flips && (trace_begin < 0 || trace_count < 0 || trace_begin + trace_count > n_walks)) return LABS_EINVAL;
   if (visited_keys && (visited_walk < 0 || visited_walk >= n_walks || visited_cap < 0 || !visited_count))
     return LABS_EINVAL;
   const int D = (L + 1) / 2;
   labs_status st = LABS_OK;
   Run run;
-  run.cfg = RunConfig{L, 1, n_walks, walk_len, recheck_every, ~0ull, -1, 1};
+  run.cfg = RunConfig{L, 1, n_walks, walk_len, recheck_every, ~0ull, -1, 1, kernel};
   run.s = 0;
   int32_t *d_trace = nullptr;
   int8_t *d_seqs = nullptr;

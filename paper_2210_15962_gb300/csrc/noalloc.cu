@@ -127,6 +127,7 @@ extern "C" labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t
   p.trace_begin = 0;
   p.trace_count = 0;
   p.plane_steps = nullptr;
+  p.variant = kVariantFullScan;
   set_muls(p);
 
   // counters and the error word start at zero (the scratch keeps the previous

@@ -2,6 +2,8 @@
 // on one lane, shared by the per-round walk kernel and the persistent batch
 // kernel, plus small warp helpers.
 #pragma once
+#include <type_traits>
+#include "walk_incr.cuh"
 #include "walk_kernels.cuh"
 
 namespace psaw {
@@ -128,6 +130,104 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, uint
 #pragma unroll
   for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
   out.planes = plane_sum;
+}
+
+// Storage of the incremental variant per lag-word class: C_{2i} fits int8 up
+// to m = 64 (|C| <= L - 2 <= 127); Delta / 8 fits int16 while 2 m^2 + 8 m < 2^15.
+template <int W>
+struct IncrTypes {
+  using CT = typename std::conditional<W <= 2, int8_t, int16_t>::type;
+  using DT = typename std::conditional<W <= 3, int16_t, int32_t>::type;
+};
+
+template <int W>
+__host__ __device__ constexpr int incr_lane_bytes() {
+  return 32 * W * (int)sizeof(typename IncrTypes<W>::CT) + (32 * W + 1) * (int)sizeof(typename IncrTypes<W>::DT);
+}
+
+// One walk with the incremental neighbourhood (walk_incr.cuh): the lane's
+// correlations and neighbour deltas live in shared memory `v`.
+template <int W, typename CT, typename DT, int K>
+__device__ __forceinline__ void run_walk_incr(const Geometry &g, const Muls &mu, const IncrView<CT, DT> &v,
+                                              uint64_t seed, uint32_t walk, uint32_t round, int walk_len,
+                                              uint64_t *table, uint32_t cap, int kw64, int recheck_every,
+                                              int32_t *trace, int32_t *err, WalkOut<W + 1> &out) {
+  constexpr int NS = W + 1;
+  IncrState<W> st;
+  init_incr(st, g, v, seed, walk, round);
+  {
+    uint32_t slot;
+    table_find(table, cap, kw64, st.key, g.D, &slot);
+    table_store(table, slot, kw64, st.key, g.D);
+  }
+  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
+  uint32_t best_key[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+  int jprev = -1;
+  uint32_t top[K];
+  scan_stored<W, CT, DT, K>(g, v, -1, 0u, top);
+  for (int step = 1; step <= walk_len; ++step) {
+    uint32_t floor = 0;
+    int chosen = -1;
+    uint32_t cslot = 0;
+    bool need = true;
+    while (need) {
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        if (need) {
+          if (top[r] == kNone) {
+            need = false;  // every neighbour not below `floor` is visited: stuck
+          } else {
+            const int a = key_flip(top[r]);
+            uint32_t nk[NS];
+#pragma unroll
+            for (int w = 0; w < NS; ++w) nk[w] = st.key[w];
+            xor_bit(nk, a, 1u);
+            uint32_t s;
+            if (!table_find(table, cap, kw64, nk, g.D, &s)) {
+              need = false;
+              if (s == kNone) {
+                atomicOr(err, kErrOverflow);
+              } else {
+                chosen = a;
+                cslot = s;
+              }
+            }
+          }
+        }
+      }
+      if (need) {
+        floor = top[K - 1] + 1u;
+        scan_stored<W, CT, DT, K>(g, v, jprev, floor, top);
+      }
+    }
+    if (chosen < 0) {
+      stuck = 1;
+      break;
+    }
+    MoveData<W> md;
+    apply_move_incr(st, g, v, chosen, md);
+    table_store(table, cslot, kw64, st.key, g.D);
+    jprev = chosen;
+    moves = step;
+    if (trace) trace[step - 1] = chosen;
+    if (st.E < bestE) {
+      bestE = st.E;
+      best_step = step;
+#pragma unroll
+      for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+    }
+    update_neighbours_fast<W, CT, DT, K>(st, g, v, md, mu, top);
+    if (recheck_every > 0 && (step % recheck_every) == 0 && !recheck_incr(st, g, v)) atomicOr(err, kErrRecheck);
+  }
+  out.bestE = bestE;
+  out.best_step = best_step;
+  out.moves = moves;
+  out.stuck = stuck;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
+  out.planes = 0;
 }
 
 }  // namespace psaw

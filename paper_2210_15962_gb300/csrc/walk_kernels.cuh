@@ -12,6 +12,10 @@ namespace psaw {
 constexpr int kWalkBlock = 128;   // threads (= walks) per block
 constexpr int kTopK = 4;          // candidates kept per pass of the neighbourhood scan
 
+// neighbourhood evaluation variants (labs_opts.kernel)
+constexpr int32_t kVariantFullScan = 1;     // every Delta_j from the digit planes each step
+constexpr int32_t kVariantIncremental = 2;  // stored Delta_j updated after each move
+
 enum ErrorBits : int32_t {
   kErrRecheck = 1,   // incremental state disagreed with the XOR+popc recheck
   kErrOverflow = 2,  // a visited table ran out of slots
@@ -51,6 +55,7 @@ struct WalkParams {
   uint32_t mul_one, mul_two, mul_four, mul_h31, mul_h30;
   // sum over walk steps of the digit planes used (for the work accounting)
   unsigned long long *plane_steps;
+  int32_t variant;  // kVariantFullScan or kVariantIncremental
 };
 
 inline void set_muls(WalkParams &p) {

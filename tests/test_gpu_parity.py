@@ -71,10 +71,14 @@ def test_energy_batch_and_bad_values(m, orc):
 
 
 # ------------------------------------------------------- one round, per walk
-def compare_round(m, orc, L, seed, rnd, n_walks, walk_len, check_walks, trace_walks=(), recheck=0):
+KERNELS = [1, 2]  # full scan, incremental: both must give the oracle's results
+
+
+def compare_round(m, orc, L, seed, rnd, n_walks, walk_len, check_walks, trace_walks=(), recheck=0, kernel=1):
     """GPU round of n_walks walks; oracle on the sampled walk indices."""
     tb, tc = (min(trace_walks), max(trace_walks) - min(trace_walks) + 1) if trace_walks else (0, 0)
-    g = m.labs_saw_round(L, seed, rnd, n_walks, walk_len, recheck_every=recheck, trace_begin=tb, trace_count=tc)
+    g = m.labs_saw_round(L, seed, rnd, n_walks, walk_len, recheck_every=recheck, trace_begin=tb, trace_count=tc,
+                         kernel=kernel)
     D = (L + 1) // 2
     for w in check_walks:
         o = orc.walk_trace(L, seed, w, rnd, walk_len)
@@ -90,10 +94,11 @@ def compare_round(m, orc, L, seed, rnd, n_walks, walk_len, check_walks, trace_wa
     return g
 
 
-def test_config1_L27_all_walks_and_trajectories(m, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_config1_L27_all_walks_and_trajectories(m, orc, kernel):
     # L=27 (D=14), seed 1, 64 walks of 4096 steps: every walk, every step
     L, wl = 27, 4096
-    compare_round(m, orc, L, 1, 0, 64, wl, range(64), trace_walks=range(64))
+    compare_round(m, orc, L, 1, 0, 64, wl, range(64), trace_walks=range(64), kernel=kernel)
 
 
 def test_config1_solve_matches_oracle(m, orc):
@@ -106,28 +111,31 @@ def test_config1_solve_matches_oracle(m, orc):
     assert int(g["evals"][0]) == int(o["evals"][0]) and int(g["rounds"][0]) == int(o["rounds"][0]) == 1
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("L", [5, 7, 9, 11, 13])
-def test_tiny_L_stuck_walks(m, orc, L):
+def test_tiny_L_stuck_walks(m, orc, L, kernel):
     # tiny spaces: walks run out of unvisited neighbours (the "stuck" reading)
     wl = 2 ** ((L + 1) // 2) + 3
-    g = compare_round(m, orc, L, 3, 1, 40, wl, range(40), trace_walks=range(40))
+    g = compare_round(m, orc, L, 3, 1, 40, wl, range(40), trace_walks=range(40), kernel=kernel)
     assert g["stuck"].sum() == 40
 
 
 @pytest.mark.parametrize("L", [15, 31, 33, 61, 63, 65, 67, 121, 127, 129, 131, 191, 193, 223, 255, 257, 259,
                                301, 383, 385, 449, 511])
-def test_lag_word_classes_and_ragged_tails(m, orc, L):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_lag_word_classes_and_ragged_tails(m, orc, L, kernel):
     # every lag-word class (m = 32W and m = 32W + 1 edges), with an every-step full recheck
     wl = 600 if L < 200 else 250
     n = 70  # more than two warps, last one ragged
     compare_round(m, orc, L, 11 + L, 2, n, wl, [0, 1, 31, 32, 33, 69], trace_walks=[0, 1, 31, 32, 33],
-                  recheck=1)
+                  recheck=1, kernel=kernel)
 
 
-def test_visited_set_is_exactly_the_pivots(m, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_visited_set_is_exactly_the_pivots(m, orc, kernel):
     for L, wl, w in [(27, 3000, 5), (121, 700, 3), (449, 200, 1)]:
         D = (L + 1) // 2
-        g = m.labs_saw_round(L, 9, 0, 8, wl, visited_walk=w)
+        g = m.labs_saw_round(L, 9, 0, 8, wl, visited_walk=w, kernel=kernel)
         o = orc.walk_trace(L, 9, w, 0, wl)
         free = orc.start_free_values(9, w, 0, D).copy()
         want = set()
@@ -195,10 +203,20 @@ def test_chunked_workspace_and_device_buffers_match(m):
     assert st["evals"] == int(ref["evals"].sum())
 
 
-def test_config2_L121_full_size_sampled(m, orc):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_config2_L121_full_size_sampled(m, orc, kernel):
     # L=121 (D=61), 131072 walks of 8192 steps: the bench's launch shape; oracle on sampled walks
     L, n, wl = 121, 131072, 8192
-    compare_round(m, orc, L, 1, 0, n, wl, [0, 1, 4095, 65536, 131071], trace_walks=[0, 1])
+    compare_round(m, orc, L, 1, 0, n, wl, [0, 1, 4095, 65536, 131071], trace_walks=[0, 1], kernel=kernel)
+
+
+@pytest.mark.parametrize("L", [27, 121, 223])
+def test_variants_agree_on_whole_solves(m, L):
+    D = (L + 1) // 2
+    wl = 8 * D
+    res = [m.labs_walks(L, [3, 4], 256, wl, 256 * wl * D * 2, kernel=k) for k in (1, 2)]
+    for key in ("best_E", "best_seq", "evals", "rounds"):
+        assert np.array_equal(res[0][key], res[1][key]), key
 
 
 def test_config5_L449_sampled(m, orc):
