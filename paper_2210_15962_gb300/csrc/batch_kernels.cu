@@ -12,11 +12,12 @@ namespace psaw {
 
 constexpr int kBatchMaxThreads = 256;
 
-// register budget per thread of each class (set so that no class spills;
-// the task loop keeps a little more state live than the per-round kernel)
+// register budget per thread of each class: the smallest that does not spill
+// (the task loop keeps more state live than the per-round kernel).  Tighter
+// budgets that keep one more block resident but spill measured slower.
 template <int W>
 struct MaxRegsFor {
-  static constexpr int value = W == 1 ? 88 : (W == 2 ? 96 : (W <= 4 ? 128 : (W == 5 ? 168 : (W == 6 ? 208 : 255))));
+  static constexpr int value = W == 1 ? 104 : (W == 2 ? 112 : (W <= 4 ? 128 : (W == 5 ? 208 : 255)));
 };
 
 template <int W>

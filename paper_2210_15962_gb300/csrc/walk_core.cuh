@@ -356,63 +356,67 @@ LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
 //      = 2 P - (2^TP - 1)(|Vx| + |Vye|),  P = sum_t 2^t popc over both sides of (V & (window ^ e_t)),
 //   Q = s_a Q0,  R = |Vx| + |Vye| + 2 |Vx & Vye| - 4 popc(Vx & Vye & (B ^ F)),
 //   Delta = 16 R - 8 Q.
-// With Z = Vx & Vye & (B ^ F ^ [s_a = -1]), popc(Z) is popc(Vx & Vye & (B ^ F))
-// for s_a = +1 and |Vx & Vye| minus it for s_a = -1, so that
-//   Delta = s_a (-16 (P + 4 popc(Z))) + c(s_a),  c = 8 (2^TP - 1) s_a n + 16 (n + 2 nxy) - 64 nxy [s_a = -1],
-// with n = |Vx| + |Vye|: one weighted popcount sum per flip.
+// The lags split into V1 = Vx ^ Vye (one side valid, bit G of that side) and
+// V2 = Vx & Vye.  A lag of V2 whose two bits differ adds 2^TP - 1 to P
+// whatever C is; one whose bits agree (M2 = V2 & ~(B ^ F)) adds twice its
+// one-sided term, i.e. its term one digit higher.  V1 and M2 are disjoint, so
+//   P = sum_{t=0..TP} 2^t popc(Z_t) + (2^TP - 1)(|V2| - |M2|),
+//   Z_t = (V1 & (G ^ e_t)) | (M2 & (G ^ e_{t-1})) = (V1 | M2) & (G ^ (V1 ? e_t : e_{t-1})),
+// two LOP3 and one POPC per plane and word.  With |V2| = nxy summed over the
+// words and M = sum of |M2|, Delta is linear in (sum 2^t popc Z_t, M) with
+// coefficients fixed by s_a.
 template <int W, int T, int TP, bool CENTRE>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
                           const uint32_t (&Vx)[W], const uint32_t (&Vy)[W], const uint32_t (&Pm)[W], uint32_t ba,
-                          uint32_t bm, int a, int n, int nxy, int t, int Nq) {
-  uint32_t acc = 0;
+                          int a, int n, int nxy, int t, int Nq) {
+  uint32_t acc = 0, mcnt = 0;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     // which sides have valid lags in this word (the same for every lane of the warp):
-    // x lags i <= t, y lags i <= Nq-1-t; a word with one side needs no carry-save adder.
-    // Wide classes keep every word on the two-sided path: with few resident warps
-    // they rely on the compiler interleaving the words' independent chains.
+    // x lags i <= t, y lags i <= Nq-1-t.  Wide classes keep every word on the
+    // two-sided path: with few resident warps they rely on the compiler
+    // interleaving the words' independent chains.
     constexpr bool kSkip = W <= kSkipMaxWords;
     const bool xa = kSkip ? (t > 32 * w) : true;
     const bool ya = kSkip ? (!CENTRE && (Nq - 1 - t > 32 * w)) : !CENTRE;
     const uint32_t vx = Vx[w];
-    uint32_t p[TP + 1];
     uint32_t v = 0;
+    // digits from the top down, each count entering the Horner sum sum_t 2^t popc(Z_t) at once
     if (xa && ya) {
       const uint32_t vy = Vy[w] & ~Pm[w];
-      uint32_t carry = 0;
+      const uint32_t v1 = vx ^ vy;
+      const uint32_t gb = (vx & B[w]) | (~vx & F[w]);
+      const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
+      const uint32_t mall = v1 | m2;
+      v = popc32(m2 & (gb ^ st.ep[T - 1][w]));
 #pragma unroll
-      for (int tt = 0; tt < TP; ++tt) {
-        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
-        const uint32_t A = vx & (B[w] ^ e);
-        const uint32_t Bv = vy & (F[w] ^ e);
-        const uint32_t sum = A ^ Bv ^ carry;
-        carry = (A & Bv) | (carry & (A ^ Bv));
-        p[tt] = popc32(sum);
+      for (int tt = TP - 1; tt >= 1; --tt) {
+        const uint32_t e1 = st.ep[tt < TP - 1 ? tt : T - 1][w];
+        const uint32_t e0 = st.ep[tt - 1][w];
+        const uint32_t et = (v1 & e1) | (~v1 & e0);
+        v = imad(v, mu.two, popc32(mall & (gb ^ et)));
       }
-      p[TP] = popc32(carry);
-      const uint32_t z = popc32(vx & vy & (B[w] ^ F[w] ^ bm));
-      v = p[TP];
-#pragma unroll
-      for (int tt = TP - 1; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);  // Horner: sum_t 2^t p_t
-      v = imad(z, mu.four, v);
+      v = imad(v, mu.two, popc32(v1 & (gb ^ st.ep[0][w])));
+      mcnt = imad(popc32(m2), mu.one, mcnt);
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : (Vy[w] & ~Pm[w]);
       const uint32_t g = xa ? B[w] : F[w];
+      v = popc32(m & (g ^ st.ep[T - 1][w]));
 #pragma unroll
-      for (int tt = 0; tt < TP; ++tt) {
-        const uint32_t e = st.ep[tt < TP - 1 ? tt : T - 1][w];
-        p[tt] = popc32(m & (g ^ e));
-      }
-      v = p[TP - 1];
-#pragma unroll
-      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, p[tt]);
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(m & (g ^ st.ep[tt][w])));
     }
     acc = imad(acc, mu.one, v);
   }
-  // Delta = -16 s_a acc + c
-  const int sgn = 1 - 2 * (int)ba;
-  const int c = 8 * ((1 << TP) - 1) * sgn * n + 16 * (n + 2 * nxy) - (ba ? 64 * nxy : 0);
-  const uint32_t delta = imad(acc, (uint32_t)(-16 * sgn), (uint32_t)(c + kDeltaBias));
+  // Delta = sig * acc + mu * M + kap, (sig, mu, kap) by s_a:
+  //   s_a = +1: (-16,  16 (K1 + 4), 8 K1 n + 16 n + 32 nxy - 16 (K1 + 4) nxy)
+  //   s_a = -1: (+16, -16 (K1 - 4), -8 K1 n + 16 n - 32 nxy + 16 K1 nxy),   K1 = 2^TP - 1
+  constexpr int K1 = (1 << TP) - 1;
+  const int kap0 = 8 * K1 * n + 16 * n + 32 * nxy - 16 * (K1 + 4) * nxy + kDeltaBias;
+  const int kap1 = -8 * K1 * n + 16 * n - 32 * nxy + 16 * K1 * nxy + kDeltaBias;
+  const uint32_t sig = imad(ba, 32u, (uint32_t)-16);
+  const uint32_t mul = imad(ba, (uint32_t)(-32 * K1), (uint32_t)(16 * (K1 + 4)));
+  const uint32_t kap = imad(ba, (uint32_t)(kap1 - kap0), (uint32_t)kap0);
+  const uint32_t delta = imad(acc, sig, imad(mcnt, mul, kap));
   return imad(delta, 256u, (uint32_t)a);
 }
 
@@ -445,7 +449,7 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
       const int a = 2 * t + q;
       const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
       const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
-      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, n, nxy, t, Nq);
+      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, a, n, nxy, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
       // advance the windows and masks by one lag (shifts as IMAD on the FMA pipe)
@@ -467,7 +471,7 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
     }
     if (has_centre) {
       const int t = nloop, a = g.c;
-      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, 0u - ba, a, t, 0, t, Nq);
+      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, a, t, 0, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
     }
