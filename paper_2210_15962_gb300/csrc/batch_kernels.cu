@@ -29,6 +29,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t *table = p.pool + gtid * p.pool_words;
   const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  // each warp's valid-lag mask table, refilled when its task's L changes
+  extern __shared__ __align__(16) uint32_t batch_smem[];
+  uint32_t *mask_rows = batch_smem + (size_t)(threadIdx.x >> 5) * MaskTable<W>::kWords;
+  int rows_L = 0;
   unsigned long long planes = 0;
   for (;;) {
     uint32_t t = 0;
@@ -41,13 +45,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
     const uint32_t walk = task.chunk * 32u + (uint32_t)lane;
     const bool active = walk < (uint32_t)pr.walks;
     clear_tables_warp(table, (size_t)pr.cap * (size_t)pr.kw64, active);
+    const Geometry g = make_geometry(pr.L, T);
+    if (pr.L != rows_L) {  // warp-uniform: every lane took the same task
+      fill_mask_rows<W>(g, mask_rows, lane, 32);
+      __syncwarp();
+      rows_L = pr.L;
+    }
     unsigned long long packed = ~0ull;
     uint32_t evals = 0;
     WalkOut<NS> o;
     if (active) {
-      const Geometry g = make_geometry(pr.L, T);
-      run_walk<W, T, kTopK>(g, mu, pr.seed, walk, task.round, pr.walk_len, table, pr.cap, pr.kw64, 0, nullptr, p.err,
-                            o);
+      run_walk<W, T, kTopK>(g, mu, mask_rows, pr.seed, walk, task.round, pr.walk_len, table, pr.cap, pr.kw64, 0,
+                            nullptr, p.err, o);
       packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
       evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);
       planes += o.planes;
@@ -73,10 +82,24 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
   if (p.plane_steps && planes) atomicAdd(p.plane_steps, planes);
 }
 
+// dynamic shared memory of a block: one mask table per warp
+template <int W>
+static size_t batch_smem_bytes(int block) {
+  return (size_t)(block / 32) * MaskTable<W>::kWords * sizeof(uint32_t);
+}
+
+template <int W>
+static cudaError_t set_batch_smem(int block) {
+  return cudaFuncSetAttribute(batch_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batch_smem_bytes<W>(block));
+}
+
 template <int W>
 static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, 0);
+  cudaError_t e = set_batch_smem<W>(block);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, batch_smem_bytes<W>(block));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -84,14 +107,17 @@ static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStr
   const int grid = per_sm * sms;
   if (grid_out) *grid_out = grid;
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  batch_kernel<W><<<grid, block, 0, s>>>(p);
+  batch_kernel<W><<<grid, block, batch_smem_bytes<W>(block), s>>>(p);
   return cudaGetLastError();
 }
 
 template <int W>
 static int resident_w(int block) {
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, 0) != cudaSuccess) return 0;
+  if (set_batch_smem<W>(block) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<W>, block, batch_smem_bytes<W>(block)) !=
+      cudaSuccess)
+    return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   return per_sm * sms * block;

@@ -21,8 +21,8 @@
 //     the digit bits e_t = (d_t+1)/2 are the bits of e = (C + 2^T - 1)/2, held
 //     as T bit planes over the lags ("ep").  With x'_i = s_a s_{a-2i} = 1-2X_i,
 //       sum_{i in V} x'_i C_{2i} = 2 sum_t 2^t popc(V & (X ^ e_t)) - (2^T-1)|V|,
-//     so a neighbour costs, per 32 lags and digit plane, two masked XORs, one
-//     carry-save full adder over the two sides and one population count.
+//     so a neighbour costs, per 32 lags and digit plane, one select, one
+//     masked XOR and one population count (both sides at once, see flip_key).
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
@@ -171,6 +171,67 @@ LABS_HD int digits_for(int L) {
   int T = 1;
   while ((1 << T) < L - 1) ++T;
   return T;
+}
+
+// ------------------------------------------------------- valid-lag masks
+// The lags a flip's windows cover depend only on its parity class q and class
+// index t (a = 2t + q), not on the sequence: x side lags 1..t, y side lags
+// 1..N_q-1-t without the lag c - a of the flip's own mirror (empty for the
+// centre).  They are tabulated once per L: row (q, t) at
+// (q * kMaskRows<W> + t) * kMaskRowWords<W> holds Vx[0..W-1] then Vye[0..W-1],
+// padded to 16 bytes.
+template <int W>
+struct MaskTable {
+  static constexpr int kRowWords = (2 * W + 3) / 4 * 4;
+  static constexpr int kRows = 16 * W + 1;  // >= nfree[0] = (D + 1) / 2 for m <= 32 W
+  static constexpr int kWords = 2 * kRows * kRowWords;
+};
+
+// Rows first, first + step, ... of the table for geometry g (rows past a
+// class's last flip are zero).
+template <int W>
+LABS_HD void fill_mask_rows(const Geometry &g, uint32_t *tab, int first, int step) {
+  using MT = MaskTable<W>;
+  for (int r = first; r < 2 * MT::kRows; r += step) {
+    const int q = r >= MT::kRows ? 1 : 0;
+    const int t = r - q * MT::kRows;
+    uint32_t *row = tab + (size_t)r * MT::kRowWords;
+    for (int k = 0; k < MT::kRowWords; ++k) row[k] = 0u;
+    if (t >= g.nfree[q]) continue;
+    const int a = 2 * t + q;
+    const bool centre = (a == g.c);
+    const int i0 = g.c - a;
+    for (int w = 0; w < W; ++w) {
+      row[w] = low_mask_word(t, w);
+      uint32_t vy = centre ? 0u : low_mask_word(g.N[q] - 1 - t, w);
+      if (!centre && ((i0 - 1) >> 5) == w) vy &= ~(1u << ((i0 - 1) & 31));
+      row[W + w] = vy;
+    }
+  }
+}
+
+// Row (q, t) of the table into registers (16-byte loads on the device).
+template <int W>
+LABS_HD void load_mask_row(const uint32_t *row, uint32_t (&Vx)[W], uint32_t (&Vye)[W]) {
+  using MT = MaskTable<W>;
+  uint32_t r[MT::kRowWords];
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+  for (int k = 0; k < MT::kRowWords / 4; ++k) {
+    const uint4 v = reinterpret_cast<const uint4 *>(row)[k];
+    r[4 * k] = v.x;
+    r[4 * k + 1] = v.y;
+    r[4 * k + 2] = v.z;
+    r[4 * k + 3] = v.w;
+  }
+#else
+  for (int k = 0; k < MT::kRowWords; ++k) r[k] = row[k];
+#endif
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Vx[w] = r[w];
+    Vye[w] = r[W + w];
+  }
 }
 
 // ------------------------------------------------------------- walk state
@@ -367,8 +428,8 @@ LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
 // coefficients fixed by s_a.
 template <int W, int T, int TP, bool CENTRE>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
-                          const uint32_t (&Vx)[W], const uint32_t (&Vy)[W], const uint32_t (&Pm)[W], uint32_t ba,
-                          int a, int n, int nxy, int t, int Nq) {
+                          const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, int a, int n, int nxy, int t,
+                          int Nq) {
   uint32_t acc = 0, mcnt = 0;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
@@ -383,7 +444,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     uint32_t v = 0;
     // digits from the top down, each count entering the Horner sum sum_t 2^t popc(Z_t) at once
     if (xa && ya) {
-      const uint32_t vy = Vy[w] & ~Pm[w];
+      const uint32_t vy = Vye[w];
       const uint32_t v1 = vx ^ vy;
       const uint32_t gb = (vx & B[w]) | (~vx & F[w]);
       const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
@@ -399,7 +460,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
       v = imad(v, mu.two, popc32(v1 & (gb ^ st.ep[0][w])));
       mcnt = imad(popc32(m2), mu.one, mcnt);
     } else if (xa || ya) {
-      const uint32_t m = xa ? vx : (Vy[w] & ~Pm[w]);
+      const uint32_t m = xa ? vx : Vye[w];
       const uint32_t g = xa ? B[w] : F[w];
       v = popc32(m & (g ^ st.ep[T - 1][w]));
 #pragma unroll
@@ -420,26 +481,26 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
   return imad(delta, 256u, (uint32_t)a);
 }
 
-// Delta_j of every flip j of the pivot (Algorithm 2, CalculateNeighborhoodDelta)
+// Delta_j of every flip j of the pivot (Algorithm 2, the neighbourhood evaluation)
 // with TP digit planes, and the K smallest packed keys (>= floor when RESCAN),
 // skipping j == jprev (the previous pivot, always visited).  Flips are scanned
-// class by class; the windows advance by one lag per flip.
+// class by class; the bit windows advance by one lag per flip and the valid-lag
+// masks come from the table mt (MaskTable<W>, filled for this geometry).
 template <int W, int T, int TP, int K, bool RESCAN>
-LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int jprev,
-                                uint32_t floor, uint32_t (&top)[K]) {
+LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt,
+                                int jprev, uint32_t floor, uint32_t (&top)[K]) {
+  using MT = MaskTable<W>;
 #pragma unroll
   for (int r = 0; r < K; ++r) top[r] = kNone;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int Nq = g.N[q];
-    uint32_t F[W], B[W], Vx[W], Vy[W], Pm[W];
+    const uint32_t *rows = mt + (size_t)q * MT::kRows * MT::kRowWords;
+    uint32_t F[W], B[W], Vx[W], Vye[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       F[w] = fshr(st.cls[q][w], st.cls[q][w + 1], 1u);
       B[w] = 0;
-      Vx[w] = 0;
-      Vy[w] = low_mask_word(Nq - 1, w);
-      Pm[w] = ((g.c - q - 1) >> 5) == w ? (1u << ((g.c - q - 1) & 31)) : 0u;
     }
     uint32_t ba = st.cls[q][0] & 1u;
     const bool has_centre = (g.c & 1) == q;
@@ -449,29 +510,23 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
       const int a = 2 * t + q;
       const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
       const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
-      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vy, Pm, ba, a, n, nxy, t, Nq);
+      load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
+      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vye, ba, a, n, nxy, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
-      // advance the windows and masks by one lag (shifts as IMAD on the FMA pipe)
+      // advance the windows by one lag (shifts as IMAD on the FMA pipe)
       const uint32_t ba_next = F[0] & 1u;
 #pragma unroll
-      for (int w = W - 1; w >= 1; --w) {
-        B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
-        Vx[w] = imadhi(Vx[w - 1], mu.two, imad(Vx[w], mu.two, 0u));
-      }
+      for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
       B[0] = imad(B[0], mu.two, ba);
-      Vx[0] = imad(Vx[0], mu.two, 1u);
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
-        Vy[w] = imadhi(Vy[w], mu.h31, (w + 1 < W) ? imad(Vy[w + 1], mu.h31, 0u) : 0u);
-        Pm[w] = imadhi(Pm[w], mu.h30, (w + 1 < W) ? imad(Pm[w + 1], mu.h30, 0u) : 0u);
-      }
+      for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
       ba = ba_next;
     }
     if (has_centre) {
       const int t = nloop, a = g.c;
-      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vy, Pm, ba, a, t, 0, t, Nq);
+      load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
+      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vye, ba, a, t, 0, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
     }
@@ -481,26 +536,26 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
 // Dispatch on the plane count (the caller may pass any tp >= planes_needed);
 // floor > 0 selects the rescan variant (candidates at or above floor only).
 template <int W, int T, int K, bool RESCAN>
-LABS_HD void eval_neighbours_r(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int tp, int jprev,
-                               uint32_t floor, uint32_t (&top)[K]) {
+LABS_HD void eval_neighbours_r(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
+                               int jprev, uint32_t floor, uint32_t (&top)[K]) {
   constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
-  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN>(st, g, mu, jprev, floor, top);
-  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN>(st, g, mu, jprev, floor, top);
-  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN>(st, g, mu, jprev, floor, top);
-  else eval_neighbours_tp<W, T, T3, K, RESCAN>(st, g, mu, jprev, floor, top);
+  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
+  else eval_neighbours_tp<W, T, T3, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
 }
 
 template <int W, int T, int K>
-LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, int tp, int jprev,
-                             uint32_t floor, uint32_t (&top)[K]) {
-  if (floor == 0) eval_neighbours_r<W, T, K, false>(st, g, mu, tp, jprev, 0u, top);
-  else eval_neighbours_r<W, T, K, true>(st, g, mu, tp, jprev, floor, top);
+LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
+                             int jprev, uint32_t floor, uint32_t (&top)[K]) {
+  if (floor == 0) eval_neighbours_r<W, T, K, false>(st, g, mu, mt, tp, jprev, 0u, top);
+  else eval_neighbours_r<W, T, K, true>(st, g, mu, mt, tp, jprev, floor, top);
 }
 
 LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }
 LABS_HD int key_delta(uint32_t k) { return (int)(k >> 8) - kDeltaBias; }
 
-// Move to the neighbour of flip a (Algorithm 2, UpdateData): C_{2i} -= 4 u_i
+// Move to the neighbour of flip a (Algorithm 2, the move): C_{2i} -= 4 u_i
 // on the digit planes by a bit-sliced add, E += delta, and flip the bits.
 template <int W, int T>
 LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta) {

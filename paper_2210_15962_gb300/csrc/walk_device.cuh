@@ -48,11 +48,13 @@ __device__ __forceinline__ void clear_tables_warp(uint64_t *my_table, size_t wor
 // unvisited neighbour (ties to the lowest flip) -> insert -> update C, E ->
 // keep the strict best".  The scan keeps the K smallest (Delta, flip) keys; if
 // all are visited it rescans above the last one, so the choice is exactly the
-// minimum over unvisited neighbours.  `table` must be zeroed.
+// minimum over unvisited neighbours.  `table` must be zeroed; `mt` is the
+// valid-lag mask table of g (MaskTable<W>, usually in shared memory).
 template <int W, int T, int K>
-__device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, uint64_t seed, uint32_t walk, uint32_t round,
-                                         int walk_len, uint64_t *table, uint32_t cap, int kw64, int recheck_every,
-                                         int32_t *trace, int32_t *err, WalkOut<W + 1> &out) {
+__device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, const uint32_t *mt, uint64_t seed,
+                                         uint32_t walk, uint32_t round, int walk_len, uint64_t *table, uint32_t cap,
+                                         int kw64, int recheck_every, int32_t *trace, int32_t *err,
+                                         WalkOut<W + 1> &out) {
   constexpr int NS = W + 1;
   WalkState<W, T> st;
   init_walk(st, g, seed, walk, round);
@@ -78,7 +80,7 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, uint
     plane_sum += (unsigned)tp;
     while (need) {
       uint32_t top[K];
-      eval_neighbours<W, T, K>(st, g, mu, tp, jprev, floor, top);
+      eval_neighbours<W, T, K>(st, g, mu, mt, tp, jprev, floor, top);
 #pragma unroll
       for (int r = 0; r < K; ++r) {
         if (need) {

@@ -20,17 +20,20 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams
   const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
   const bool live = lid < p.g_count && !(p.done && p.done[prob]);
   uint64_t *table = p.tables + (size_t)lid * table_words;
+  const Geometry g = make_geometry(p.L, T);
+  __shared__ __align__(16) uint32_t mask_rows[MaskTable<W>::kWords];
+  fill_mask_rows<W>(g, mask_rows, threadIdx.x, blockDim.x);
+  __syncthreads();
   clear_tables_warp(table, table_words, live);
   if (!live) return;
 
-  const Geometry g = make_geometry(p.L, T);
   const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
   int32_t *trace = nullptr;
   if (p.trace_flips && gw - p.trace_begin < p.trace_count)
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
   WalkOut<NS> o;
-  run_walk<W, T, K>(g, mu, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64, p.recheck_every, trace,
-                    p.err, o);
+  run_walk<W, T, K>(g, mu, mask_rows, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64, p.recheck_every,
+                    trace, p.err, o);
   p.w_bestE[gw] = o.bestE;
   p.w_moves[gw] = o.moves;
   p.w_stuck[gw] = o.stuck;
