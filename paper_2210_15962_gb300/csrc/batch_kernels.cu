@@ -20,6 +20,10 @@ struct MaxRegsFor {
   static constexpr int value = W == 1 ? 104 : (W == 2 ? 112 : (W <= 4 ? 128 : (W == 5 ? 208 : 255)));
 };
 
+// shared memory words of one warp: mask table, then (W + 2) parked words per lane
+template <int W>
+constexpr int kBatchWarpWords = MaskTable<W>::kWords + (W + 2) * 32;
+
 template <int W>
 __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::value)
     batch_kernel(const BatchKernelParams p) {
@@ -29,9 +33,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t *table = p.pool + gtid * p.pool_words;
   const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
-  // each warp's valid-lag mask table, refilled when its task's L changes
+  // each warp's valid-lag mask table (refilled when its task's L changes) and
+  // its lanes' parked best pivots
   extern __shared__ __align__(16) uint32_t batch_smem[];
-  uint32_t *mask_rows = batch_smem + (size_t)(threadIdx.x >> 5) * MaskTable<W>::kWords;
+  uint32_t *mask_rows = batch_smem + (size_t)(threadIdx.x >> 5) * kBatchWarpWords<W>;
+  uint32_t *best_park = mask_rows + MaskTable<W>::kWords + lane;
   int rows_L = 0;
   unsigned long long planes = 0;
   for (;;) {
@@ -55,8 +61,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
     uint32_t evals = 0;
     WalkOut<NS> o;
     if (active) {
-      run_walk<W, T, kTopK>(g, mu, mask_rows, pr.seed, walk, task.round, pr.walk_len, table, pr.cap, pr.kw64, 0,
-                            nullptr, p.err, o);
+      run_walk<W, T, kTopK>(g, mu, mask_rows, best_park, 32, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
+                            pr.kw64, 0, nullptr, p.err, o);
       packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
       evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);
       planes += o.planes;
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
 // dynamic shared memory of a block: one mask table per warp
 template <int W>
 static size_t batch_smem_bytes(int block) {
-  return (size_t)(block / 32) * MaskTable<W>::kWords * sizeof(uint32_t);
+  return (size_t)(block / 32) * kBatchWarpWords<W> * sizeof(uint32_t);
 }
 
 template <int W>

@@ -49,12 +49,15 @@ __device__ __forceinline__ void clear_tables_warp(uint64_t *my_table, size_t wor
 // keep the strict best".  The scan keeps the K smallest (Delta, flip) keys; if
 // all are visited it rescans above the last one, so the choice is exactly the
 // minimum over unvisited neighbours.  `table` must be zeroed; `mt` is the
-// valid-lag mask table of g (MaskTable<W>, usually in shared memory).
+// valid-lag mask table of g (MaskTable<W>, usually in shared memory).  The
+// best pivot's step and key, written only when E improves, are parked in
+// shared memory (word k at bst[k * stride]) so that they hold no registers
+// during the scan.
 template <int W, int T, int K>
-__device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, const uint32_t *mt, uint64_t seed,
-                                         uint32_t walk, uint32_t round, int walk_len, uint64_t *table, uint32_t cap,
-                                         int kw64, int recheck_every, int32_t *trace, int32_t *err,
-                                         WalkOut<W + 1> &out) {
+__device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, const uint32_t *mt, uint32_t *bst,
+                                         int stride, uint64_t seed, uint32_t walk, uint32_t round, int walk_len,
+                                         uint64_t *table, uint32_t cap, int kw64, int recheck_every, int32_t *trace,
+                                         int32_t *err, WalkOut<W + 1> &out) {
   constexpr int NS = W + 1;
   WalkState<W, T> st;
   init_walk(st, g, seed, walk, round);
@@ -63,12 +66,12 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     table_find(table, cap, kw64, st.key, g.D, &slot);
     table_store(table, slot, kw64, st.key, g.D);
   }
-  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
-  uint32_t best_key[NS];
+  int32_t bestE = st.E, moves = 0, stuck = 0;
+  bst[0] = 0u;
 #pragma unroll
-  for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+  for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
   int jprev = -1;
-  unsigned long long plane_sum = 0;
+  uint32_t plane_sum = 0;  // <= 9 * 2^26
   for (int step = 1; step <= walk_len; ++step) {
     uint32_t floor = 0;
     int chosen = -1, cdelta = 0;
@@ -77,7 +80,7 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     int tp = planes_needed(st, g);
     tp = __reduce_max_sync(__activemask(), (unsigned)tp);  // one plane count per warp (any larger count is exact)
     tp = tp < T - 3 ? T - 3 : tp;
-    plane_sum += (unsigned)tp;
+    plane_sum += (uint32_t)tp;
     while (need) {
       uint32_t top[K];
       eval_neighbours<W, T, K>(st, g, mu, mt, tp, jprev, floor, top);
@@ -119,18 +122,18 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     if (trace) trace[step - 1] = chosen;
     if (st.E < bestE) {
       bestE = st.E;
-      best_step = step;
+      bst[0] = (uint32_t)step;
 #pragma unroll
-      for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+      for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
     }
     if (recheck_every > 0 && (step % recheck_every) == 0 && !recheck_walk(st, g)) atomicOr(err, kErrRecheck);
   }
   out.bestE = bestE;
-  out.best_step = best_step;
+  out.best_step = (int32_t)bst[0];
   out.moves = moves;
   out.stuck = stuck;
 #pragma unroll
-  for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
+  for (int w = 0; w < NS; ++w) out.best_key[w] = bst[(w + 1) * stride];
   out.planes = plane_sum;
 }
 

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams
   uint64_t *table = p.tables + (size_t)lid * table_words;
   const Geometry g = make_geometry(p.L, T);
   __shared__ __align__(16) uint32_t mask_rows[MaskTable<W>::kWords];
+  __shared__ uint32_t best_park[(NS + 1) * kWalkBlock];
   fill_mask_rows<W>(g, mask_rows, threadIdx.x, blockDim.x);
   __syncthreads();
   clear_tables_warp(table, table_words, live);
@@ -32,8 +33,8 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams
   if (p.trace_flips && gw - p.trace_begin < p.trace_count)
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
   WalkOut<NS> o;
-  run_walk<W, T, K>(g, mu, mask_rows, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64, p.recheck_every,
-                    trace, p.err, o);
+  run_walk<W, T, K>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock, p.seeds[prob], walk, p.round, p.walk_len,
+                    table, p.cap, p.kw64, p.recheck_every, trace, p.err, o);
   p.w_bestE[gw] = o.bestE;
   p.w_moves[gw] = o.moves;
   p.w_stuck[gw] = o.stuck;
