@@ -12,6 +12,12 @@ namespace psaw {
 
 constexpr int kBatchMaxThreads = 256;
 
+// Widest lag-word class whose scan runs through pattern-specialised loops: the
+// classes' persistent kernels run side by side, so their code shares the SMs'
+// instruction caches and is kept smaller than in the per-round kernel (with
+// classes up to 4 words specialised the batched workload measured 13% slower).
+constexpr int kBatchPatternMaxWords = 2;
+
 // register budget per thread of each class: the smallest that does not spill
 // (the task loop keeps more state live than the per-round kernel).  Tighter
 // budgets that keep one more block resident but spill measured slower.
@@ -61,7 +67,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
     uint32_t evals = 0;
     WalkOut<NS> o;
     if (active) {
-      run_walk<W, T, kTopK>(g, mu, mask_rows, best_park, 32, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
+      run_walk<W, T, kTopK, kBatchPatternMaxWords>(g, mu, mask_rows, best_park, 32, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
                             pr.kw64, 0, nullptr, p.err, o);
       packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
       evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);

@@ -426,7 +426,10 @@ LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
 // two LOP3 and one POPC per plane and word.  With |V2| = nxy summed over the
 // words and M = sum of |M2|, Delta is linear in (sum 2^t popc Z_t, M) with
 // coefficients fixed by s_a.
-template <int W, int T, int TP, bool CENTRE>
+// NX, NY >= 0 fix at compile time how many leading words have valid x / y
+// lags (the caller guarantees NX = ceil(t/32), NY = ceil((Nq-1-t)/32));
+// -1 decides per flip.
+template <int W, int T, int TP, bool CENTRE, int NX = -1, int NY = -1>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
                           const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, int a, int n, int nxy, int t,
                           int Nq) {
@@ -438,8 +441,8 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     // two-sided path: with few resident warps they rely on the compiler
     // interleaving the words' independent chains.
     constexpr bool kSkip = W <= kSkipMaxWords;
-    const bool xa = kSkip ? (t > 32 * w) : true;
-    const bool ya = kSkip ? (!CENTRE && (Nq - 1 - t > 32 * w)) : !CENTRE;
+    const bool xa = NX >= 0 ? (w < NX) : (kSkip ? (t > 32 * w) : true);
+    const bool ya = CENTRE ? false : (NY >= 0 ? (w < NY) : (kSkip ? (Nq - 1 - t > 32 * w) : true));
     const uint32_t vx = Vx[w];
     uint32_t v = 0;
     // digits from the top down, each count entering the Horner sum sum_t 2^t popc(Z_t) at once
@@ -481,12 +484,70 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
   return imad(delta, 256u, (uint32_t)a);
 }
 
+// Flips t0 .. t1-1 of class q (none of them the centre): packed keys into
+// top, windows B, F and the bit ba of position a advanced one lag per flip.
+template <int W, int T, int TP, int K, bool RESCAN, int NX, int NY>
+LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
+                        int t0, int t1, int jprev, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W], uint32_t &ba,
+                        uint32_t (&top)[K]) {
+  using MT = MaskTable<W>;
+  const int Nq = g.N[q];
+  const int n = Nq - 2;  // |Vx| + |Vye| for every non-centre flip
+  for (int t = t0; t < t1; ++t) {
+    const int a = 2 * t + q;
+    const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
+    const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
+    uint32_t Vx[W], Vye[W];
+    load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
+    uint32_t x = flip_key<W, T, TP, false, NX, NY>(st, mu, B, F, Vx, Vye, ba, a, n, nxy, t, Nq);
+    x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
+    top_insert(top, x);
+    // advance the windows by one lag (shifts as IMAD on the FMA pipe)
+    const uint32_t ba_next = F[0] & 1u;
+#pragma unroll
+    for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
+    B[0] = imad(B[0], mu.two, ba);
+#pragma unroll
+    for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
+    ba = ba_next;
+  }
+}
+
+// Classes of kPatternMinWords .. PMAX lag words (PMAX a template parameter of
+// the scan, chosen per kernel) scan in runs of flips with a fixed pattern of
+// active word sides, each run through a loop compiled for it (one-word classes
+// have too few flips per run to gain).
+constexpr int kPatternMinWords = 2;
+
+// One run t0 .. t1-1 whose flips all have nx words with x lags and ny with y
+// lags.  The patterns compiled are nx = 0 .. ceil(W/2) (t <= 16 W) and
+// ny = max(1, W/2) .. W (the y side keeps at least half the class); any other
+// pattern decides per flip.
+template <int W, int T, int TP, int K, bool RESCAN, int NX = 0, int NY = (W / 2 > 1 ? W / 2 : 1)>
+LABS_HD void scan_run(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
+                      int nx, int ny, int t0, int t1, int jprev, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W],
+                      uint32_t &ba, uint32_t (&top)[K]) {
+  if constexpr (NX > (W + 1) / 2) {
+    scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t0, t1, jprev, floor, B, F, ba, top);
+  } else if constexpr (NY > W) {
+    scan_run<W, T, TP, K, RESCAN, NX + 1, (W / 2 > 1 ? W / 2 : 1)>(st, g, mu, rows, q, nx, ny, t0, t1, jprev, floor,
+                                                                   B, F, ba, top);
+  } else {
+    if (nx == NX && ny == NY)
+      scan_flips<W, T, TP, K, RESCAN, NX, NY>(st, g, mu, rows, q, t0, t1, jprev, floor, B, F, ba, top);
+    else
+      scan_run<W, T, TP, K, RESCAN, NX, NY + 1>(st, g, mu, rows, q, nx, ny, t0, t1, jprev, floor, B, F, ba, top);
+  }
+}
+
 // Delta_j of every flip j of the pivot (Algorithm 2, the neighbourhood evaluation)
 // with TP digit planes, and the K smallest packed keys (>= floor when RESCAN),
 // skipping j == jprev (the previous pivot, always visited).  Flips are scanned
 // class by class; the bit windows advance by one lag per flip and the valid-lag
-// masks come from the table mt (MaskTable<W>, filled for this geometry).
-template <int W, int T, int TP, int K, bool RESCAN>
+// masks come from the table mt (MaskTable<W>, filled for this geometry).  In
+// narrow classes the flips of a class split into runs where the number of
+// words with x lags, ceil(t/32), and with y lags, ceil((Nq-1-t)/32), is fixed.
+template <int W, int T, int TP, int K, bool RESCAN, int PMAX>
 LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt,
                                 int jprev, uint32_t floor, uint32_t (&top)[K]) {
   using MT = MaskTable<W>;
@@ -496,7 +557,7 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
   for (int q = 0; q < 2; ++q) {
     const int Nq = g.N[q];
     const uint32_t *rows = mt + (size_t)q * MT::kRows * MT::kRowWords;
-    uint32_t F[W], B[W], Vx[W], Vye[W];
+    uint32_t F[W], B[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       F[w] = fshr(st.cls[q][w], st.cls[q][w + 1], 1u);
@@ -505,26 +566,23 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
     uint32_t ba = st.cls[q][0] & 1u;
     const bool has_centre = (g.c & 1) == q;
     const int nloop = g.nfree[q] - (has_centre ? 1 : 0);
-    const int n = Nq - 2;  // |Vx| + |Vye| for every non-centre flip
-    for (int t = 0; t < nloop; ++t) {
-      const int a = 2 * t + q;
-      const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
-      const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
-      load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
-      uint32_t x = flip_key<W, T, TP, false>(st, mu, B, F, Vx, Vye, ba, a, n, nxy, t, Nq);
-      x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
-      top_insert(top, x);
-      // advance the windows by one lag (shifts as IMAD on the FMA pipe)
-      const uint32_t ba_next = F[0] & 1u;
-#pragma unroll
-      for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
-      B[0] = imad(B[0], mu.two, ba);
-#pragma unroll
-      for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
-      ba = ba_next;
+    if (W >= kPatternMinWords && W <= PMAX && !RESCAN) {
+      for (int t = 0; t < nloop;) {
+        const int nx = (t + 31) >> 5;
+        const int ly = Nq - 1 - t;
+        const int ny = ly > 0 ? (ly + 31) >> 5 : 0;
+        int t1 = 32 * nx + 1;                                             // next change of nx
+        if (ny > 0 && Nq - 1 - 32 * (ny - 1) < t1) t1 = Nq - 1 - 32 * (ny - 1);  // ... or of ny
+        if (t1 > nloop) t1 = nloop;
+        scan_run<W, T, TP, K, RESCAN>(st, g, mu, rows, q, nx, ny, t, t1, jprev, floor, B, F, ba, top);
+        t = t1;
+      }
+    } else {
+      scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, 0, nloop, jprev, floor, B, F, ba, top);
     }
     if (has_centre) {
       const int t = nloop, a = g.c;
+      uint32_t Vx[W], Vye[W];
       load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
       uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vye, ba, a, t, 0, t, Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
@@ -535,21 +593,21 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
 
 // Dispatch on the plane count (the caller may pass any tp >= planes_needed);
 // floor > 0 selects the rescan variant (candidates at or above floor only).
-template <int W, int T, int K, bool RESCAN>
+template <int W, int T, int K, bool RESCAN, int PMAX>
 LABS_HD void eval_neighbours_r(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
                                int jprev, uint32_t floor, uint32_t (&top)[K]) {
   constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
-  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
-  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
-  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
-  else eval_neighbours_tp<W, T, T3, K, RESCAN>(st, g, mu, mt, jprev, floor, top);
+  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
+  else eval_neighbours_tp<W, T, T3, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
 }
 
-template <int W, int T, int K>
+template <int W, int T, int K, int PMAX>
 LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
                              int jprev, uint32_t floor, uint32_t (&top)[K]) {
-  if (floor == 0) eval_neighbours_r<W, T, K, false>(st, g, mu, mt, tp, jprev, 0u, top);
-  else eval_neighbours_r<W, T, K, true>(st, g, mu, mt, tp, jprev, floor, top);
+  if (floor == 0) eval_neighbours_r<W, T, K, false, PMAX>(st, g, mu, mt, tp, jprev, 0u, top);
+  else eval_neighbours_r<W, T, K, true, PMAX>(st, g, mu, mt, tp, jprev, floor, top);
 }
 
 LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }

@@ -49,11 +49,12 @@ __device__ __forceinline__ void clear_tables_warp(uint64_t *my_table, size_t wor
 // keep the strict best".  The scan keeps the K smallest (Delta, flip) keys; if
 // all are visited it rescans above the last one, so the choice is exactly the
 // minimum over unvisited neighbours.  `table` must be zeroed; `mt` is the
-// valid-lag mask table of g (MaskTable<W>, usually in shared memory).  The
-// best pivot's step and key, written only when E improves, are parked in
-// shared memory (word k at bst[k * stride]) so that they hold no registers
-// during the scan.
-template <int W, int T, int K>
+// valid-lag mask table of g (MaskTable<W>, usually in shared memory).  From
+// two lag words up, the best pivot's step and key, written only when E
+// improves, are parked in shared memory (word k at bst[k * stride]) so that
+// they hold no registers during the scan (one-word walks measured faster
+// keeping them in registers).
+template <int W, int T, int K, int PMAX>
 __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, const uint32_t *mt, uint32_t *bst,
                                          int stride, uint64_t seed, uint32_t walk, uint32_t round, int walk_len,
                                          uint64_t *table, uint32_t cap, int kw64, int recheck_every, int32_t *trace,
@@ -66,10 +67,17 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     table_find(table, cap, kw64, st.key, g.D, &slot);
     table_store(table, slot, kw64, st.key, g.D);
   }
-  int32_t bestE = st.E, moves = 0, stuck = 0;
-  bst[0] = 0u;
+  constexpr bool kPark = W >= 2;
+  int32_t bestE = st.E, moves = 0, stuck = 0, best_step = 0;
+  uint32_t best_key[kPark ? 1 : NS];
+  if constexpr (kPark) {
+    bst[0] = 0u;
 #pragma unroll
-  for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
+    for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
+  } else {
+#pragma unroll
+    for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+  }
   int jprev = -1;
   uint32_t plane_sum = 0;  // <= 9 * 2^26
   for (int step = 1; step <= walk_len; ++step) {
@@ -83,7 +91,7 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     plane_sum += (uint32_t)tp;
     while (need) {
       uint32_t top[K];
-      eval_neighbours<W, T, K>(st, g, mu, mt, tp, jprev, floor, top);
+      eval_neighbours<W, T, K, PMAX>(st, g, mu, mt, tp, jprev, floor, top);
 #pragma unroll
       for (int r = 0; r < K; ++r) {
         if (need) {
@@ -122,18 +130,30 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     if (trace) trace[step - 1] = chosen;
     if (st.E < bestE) {
       bestE = st.E;
-      bst[0] = (uint32_t)step;
+      if constexpr (kPark) {
+        bst[0] = (uint32_t)step;
 #pragma unroll
-      for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
+        for (int w = 0; w < NS; ++w) bst[(w + 1) * stride] = st.key[w];
+      } else {
+        best_step = step;
+#pragma unroll
+        for (int w = 0; w < NS; ++w) best_key[w] = st.key[w];
+      }
     }
     if (recheck_every > 0 && (step % recheck_every) == 0 && !recheck_walk(st, g)) atomicOr(err, kErrRecheck);
   }
   out.bestE = bestE;
-  out.best_step = (int32_t)bst[0];
   out.moves = moves;
   out.stuck = stuck;
+  if constexpr (kPark) {
+    out.best_step = (int32_t)bst[0];
 #pragma unroll
-  for (int w = 0; w < NS; ++w) out.best_key[w] = bst[(w + 1) * stride];
+    for (int w = 0; w < NS; ++w) out.best_key[w] = bst[(w + 1) * stride];
+  } else {
+    out.best_step = best_step;
+#pragma unroll
+    for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
+  }
   out.planes = plane_sum;
 }
 

@@ -7,6 +7,9 @@
 
 namespace psaw {
 
+// Widest lag-word class whose scan runs through pattern-specialised loops.
+constexpr int kWalkPatternMaxWords = 4;
+
 // One thread = one walk (Algorithm 2 with one lane in place of one block).
 // The warp zeroes the visited tables of its live lanes, then every lane runs
 // its walk (run_walk) and publishes its best to the round's accumulators.
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams
   if (p.trace_flips && gw - p.trace_begin < p.trace_count)
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
   WalkOut<NS> o;
-  run_walk<W, T, K>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock, p.seeds[prob], walk, p.round, p.walk_len,
+  run_walk<W, T, K, kWalkPatternMaxWords>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock, p.seeds[prob], walk, p.round, p.walk_len,
                     table, p.cap, p.kw64, p.recheck_every, trace, p.err, o);
   p.w_bestE[gw] = o.bestE;
   p.w_moves[gw] = o.moves;
