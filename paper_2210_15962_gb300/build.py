@@ -19,8 +19,22 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["walk_kernels.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu", "serve.cu"]
+SOURCES = ["walk_kernels.cu", "walk_class.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu",
+           "serve.cu"]
 HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "walk_device.cuh", "walk_incr.cuh", "batch.cuh"]
+LAG_WORD_CLASSES = range(1, 9)  # walk_class.cu is compiled once per class W (m <= 32 W lags)
+
+
+def _units():
+    """(source, object, extra flags) of every translation unit."""
+    units = []
+    for src in SOURCES:
+        if src == "walk_class.cu":
+            for w in LAG_WORD_CLASSES:
+                units.append((src, "walk_class_w%d.o" % w, ["-DPSAW_W=%d" % w]))
+        else:
+            units.append((src, src.replace(".cu", ".o"), []))
+    return units
 
 
 def _nvcc() -> str:
@@ -43,13 +57,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
+    for src, obj_name, extra in _units():
+        obj = os.path.join(BUILD_DIR, obj_name)
         objs.append(obj)
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        procs.append((obj_name, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()

@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
     uint32_t evals = 0;
     WalkOut<NS> o;
     if (active) {
-      run_walk<W, T, kTopK, kBatchPatternMaxWords>(g, mu, mask_rows, best_park, 32, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
-                            pr.kw64, 0, nullptr, p.err, o);
+      run_walk<W, T, kTopK, kBatchPatternMaxWords>(g, mu, mask_rows, best_park, 32, pr.seed, walk, task.round,
+                                                   pr.walk_len, table, pr.cap, pr.kw64, 0, nullptr, p.err, o);
       packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
       evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);
       planes += o.planes;

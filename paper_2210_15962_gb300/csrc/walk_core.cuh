@@ -491,8 +491,8 @@ LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls
                         int t0, int t1, int jprev, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W], uint32_t &ba,
                         uint32_t (&top)[K]) {
   using MT = MaskTable<W>;
-  const int Nq = g.N[q];
-  const int n = Nq - 2;  // |Vx| + |Vye| for every non-centre flip
+  const int Nq = g.D - q;  // N_q without indexing g.N
+  const int n = Nq - 2;    // |Vx| + |Vye| for every non-centre flip
   for (int t = t0; t < t1; ++t) {
     const int a = 2 * t + q;
     const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
@@ -553,19 +553,25 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
   using MT = MaskTable<W>;
 #pragma unroll
   for (int r = 0; r < K; ++r) top[r] = kNone;
-#pragma unroll
+  // one pass per parity class, unrolled only for one-word classes (wider
+  // classes' loops are large and share the instruction caches); the class
+  // array is selected without dynamic indexing
+#pragma unroll(W == 1 ? 2 : 1)
   for (int q = 0; q < 2; ++q) {
-    const int Nq = g.N[q];
+    const int Nq = g.D - q;
     const uint32_t *rows = mt + (size_t)q * MT::kRows * MT::kRowWords;
+    const uint32_t mq = sel_mask(q != 0);
     uint32_t F[W], B[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      F[w] = fshr(st.cls[q][w], st.cls[q][w + 1], 1u);
+      const uint32_t c0 = (st.cls[1][w] & mq) | (st.cls[0][w] & ~mq);
+      const uint32_t c1 = (st.cls[1][w + 1] & mq) | (st.cls[0][w + 1] & ~mq);
+      F[w] = fshr(c0, c1, 1u);
       B[w] = 0;
     }
-    uint32_t ba = st.cls[q][0] & 1u;
+    uint32_t ba = ((st.cls[1][0] & mq) | (st.cls[0][0] & ~mq)) & 1u;
     const bool has_centre = (g.c & 1) == q;
-    const int nloop = g.nfree[q] - (has_centre ? 1 : 0);
+    const int nloop = (q ? g.D / 2 : (g.D + 1) / 2) - (has_centre ? 1 : 0);
     if (W >= kPatternMinWords && W <= PMAX && !RESCAN) {
       for (int t = 0; t < nloop;) {
         const int nx = (t + 31) >> 5;

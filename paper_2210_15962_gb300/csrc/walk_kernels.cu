@@ -1,150 +1,24 @@
 // Kernels of one round of parallel contiguous self-avoiding walks (Eq. 4 and
-// Algorithm 2 of arXiv 2210.15962), the per-round best reduction of
-// Algorithm 1, the key -> sequence expansion (Eq. 2) and the Eq. 1 energy.
+// Algorithm 2 of arXiv 2210.15962): the dispatch to the per-class walk
+// kernels (walk_class.cu), the per-round best reduction of Algorithm 1, the
+// key -> sequence expansion (Eq. 2) and the Eq. 1 energy.
 #include <climits>
 
 #include "walk_device.cuh"
 
 namespace psaw {
 
-// Widest lag-word class whose scan runs through pattern-specialised loops.
-constexpr int kWalkPatternMaxWords = 4;
-
-// One thread = one walk (Algorithm 2 with one lane in place of one block).
-// The warp zeroes the visited tables of its live lanes, then every lane runs
-// its walk (run_walk) and publishes its best to the round's accumulators.
-template <int W, int T, int K, int MINB>
-__global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams p) {
-  constexpr int NS = W + 1;
-  const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
-  const uint32_t gw = p.g_begin + lid;
-  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
-  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
-  const bool live = lid < p.g_count && !(p.done && p.done[prob]);
-  uint64_t *table = p.tables + (size_t)lid * table_words;
-  const Geometry g = make_geometry(p.L, T);
-  __shared__ __align__(16) uint32_t mask_rows[MaskTable<W>::kWords];
-  __shared__ uint32_t best_park[(NS + 1) * kWalkBlock];
-  fill_mask_rows<W>(g, mask_rows, threadIdx.x, blockDim.x);
-  __syncthreads();
-  clear_tables_warp(table, table_words, live);
-  if (!live) return;
-
-  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
-  int32_t *trace = nullptr;
-  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
-    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
-  WalkOut<NS> o;
-  run_walk<W, T, K, kWalkPatternMaxWords>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock, p.seeds[prob], walk, p.round, p.walk_len,
-                    table, p.cap, p.kw64, p.recheck_every, trace, p.err, o);
-  p.w_bestE[gw] = o.bestE;
-  p.w_moves[gw] = o.moves;
-  p.w_stuck[gw] = o.stuck;
-  p.w_best_step[gw] = o.best_step;
-#pragma unroll
-  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
-  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
-  if (p.plane_steps) atomicAdd(p.plane_steps, o.planes);
-  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
-}
-
-// The incremental variant: same contract as walk_kernel; each lane keeps its
-// correlations and neighbour deltas in dynamic shared memory, lane-major.
-template <int W, int K, int MINB>
-__global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_incr(const WalkParams p) {
-  constexpr int NS = W + 1;
-  using CT = typename IncrTypes<W>::CT;
-  using DT = typename IncrTypes<W>::DT;
-  extern __shared__ __align__(16) unsigned char incr_smem[];
-  const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
-  const uint32_t gw = p.g_begin + lid;
-  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
-  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
-  const bool live = lid < p.g_count && !(p.done && p.done[prob]);
-  uint64_t *table = p.tables + (size_t)lid * table_words;
-  clear_tables_warp(table, table_words, live);
-  if (!live) return;
-  const Geometry g = make_geometry(p.L, PlanesFor<W>::value);
-  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
-  CT *Cs = reinterpret_cast<CT *>(incr_smem);
-  DT *Ds = reinterpret_cast<DT *>(incr_smem + (size_t)g.m * blockDim.x * sizeof(CT) + 15) ;
-  Ds = reinterpret_cast<DT *>((reinterpret_cast<uintptr_t>(Ds)) & ~(uintptr_t)15);
-  const IncrView<CT, DT> v{Cs + threadIdx.x, Ds + threadIdx.x, (int)blockDim.x};
-  int32_t *trace = nullptr;
-  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
-    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
-  WalkOut<NS> o;
-  run_walk_incr<W, CT, DT, K>(g, mu, v, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64,
-                              p.recheck_every, trace, p.err, o);
-  p.w_bestE[gw] = o.bestE;
-  p.w_moves[gw] = o.moves;
-  p.w_stuck[gw] = o.stuck;
-  p.w_best_step[gw] = o.best_step;
-#pragma unroll
-  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
-  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
-  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
-}
-
-// resident blocks the incremental variant of each class is compiled for
-template <int W>
-struct MinBlocksIncr {
-  static constexpr int value = W == 1 ? 8 : (W == 2 ? 8 : (W <= 4 ? 5 : 3));
-};
-
-template <int W>
-static size_t incr_smem_bytes(int L, int block) {
-  using CT = typename IncrTypes<W>::CT;
-  using DT = typename IncrTypes<W>::DT;
-  const int m = (L - 1) / 2, D = (L + 1) / 2;
-  return ((size_t)m * block * sizeof(CT) + 15) / 16 * 16 + (size_t)D * block * sizeof(DT);
-}
-
-template <int W>
-static cudaError_t launch_w_incr(const WalkParams &p, cudaStream_t s) {
-  const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
-  const size_t smem = incr_smem_bytes<W>(p.L, kWalkBlock);
-  auto kern = walk_kernel_incr<W, kTopK, MinBlocksIncr<W>::value>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<blocks, kWalkBlock, smem, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int W>
-static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
-  constexpr int T = PlanesFor<W>::value;
-  const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
-  walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_walk_round(int W, const WalkParams &p, cudaStream_t s) {
   if (p.g_count == 0) return cudaSuccess;
-  if (p.variant == kVariantIncremental) {
-    switch (W) {
-      case 1: return launch_w_incr<1>(p, s);
-      case 2: return launch_w_incr<2>(p, s);
-      case 3: return launch_w_incr<3>(p, s);
-      case 4: return launch_w_incr<4>(p, s);
-      case 5: return launch_w_incr<5>(p, s);
-      case 6: return launch_w_incr<6>(p, s);
-      case 7: return launch_w_incr<7>(p, s);
-      case 8: return launch_w_incr<8>(p, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch (W) {
-    case 1: return launch_w<1>(p, s);
-    case 2: return launch_w<2>(p, s);
-    case 3: return launch_w<3>(p, s);
-    case 4: return launch_w<4>(p, s);
-    case 5: return launch_w<5>(p, s);
-    case 6: return launch_w<6>(p, s);
-    case 7: return launch_w<7>(p, s);
-    case 8: return launch_w<8>(p, s);
+    case 1: return launch_walk_class<1>(p, s);
+    case 2: return launch_walk_class<2>(p, s);
+    case 3: return launch_walk_class<3>(p, s);
+    case 4: return launch_walk_class<4>(p, s);
+    case 5: return launch_walk_class<5>(p, s);
+    case 6: return launch_walk_class<6>(p, s);
+    case 7: return launch_walk_class<7>(p, s);
+    case 8: return launch_walk_class<8>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }

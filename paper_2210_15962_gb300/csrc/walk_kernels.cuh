@@ -85,6 +85,18 @@ struct FinalizeParams {
 
 // Launch one round chunk for lag-word class W (L = 2m+1 with m <= 32W).
 cudaError_t launch_walk_round(int W, const WalkParams &p, cudaStream_t s);
+// One round's walk kernel of lag-word class W (p.variant selects the full
+// scan or the incremental kernel); defined in walk_class.cu, one object per W.
+template <int W>
+cudaError_t launch_walk_class(const WalkParams &p, cudaStream_t s);
+extern template cudaError_t launch_walk_class<1>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<2>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<3>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<4>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<5>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<6>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<7>(const WalkParams &, cudaStream_t);
+extern template cudaError_t launch_walk_class<8>(const WalkParams &, cudaStream_t);
 cudaError_t launch_finalize(const FinalizeParams &f, cudaStream_t s);
 cudaError_t launch_init_problems(int n, int64_t *p_bestE, unsigned long long *p_evals,
                                  unsigned long long *p_round_best, int32_t *done, int32_t *p_rounds,
