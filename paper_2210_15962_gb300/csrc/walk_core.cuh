@@ -423,9 +423,22 @@ LABS_HD int planes_needed(const WalkState<W, T> &st, const Geometry &g) {
 // one-sided term, i.e. its term one digit higher.  V1 and M2 are disjoint, so
 //   P = sum_{t=0..TP} 2^t popc(Z_t) + (2^TP - 1)(|V2| - |M2|),
 //   Z_t = (V1 & (G ^ e_t)) | (M2 & (G ^ e_{t-1})) = (V1 | M2) & (G ^ (V1 ? e_t : e_{t-1})),
-// two LOP3 and one POPC per plane and word.  With |V2| = nxy summed over the
-// words and M = sum of |M2|, Delta is linear in (sum 2^t popc Z_t, M) with
-// coefficients fixed by s_a.
+// two LOP3 and one POPC per plane and word.  The bits enter XORed with
+// [s_a = -1], so that they stand for the products s_a s_{a-+2i}: with
+// S = sum_t 2^t popc(Z_t) over the words, M = sum of |M2| and |V2| = nxy,
+//   Delta = -16 S + 16 (K1 + 4) M + (16 + 8 K1) n - (32 + 16 K1) nxy,  K1 = 2^TP - 1,
+// the same for both signs of s_a (R does not depend on it, and Q = 2 P - K1 n
+// with P taken over the products).
+// How the sign s_a enters, per lag-word class (chosen by measurement): folded
+// into the bits (one XOR per active word) or by coefficients selected by s_a
+// (three IMAD per flip).  Classes with few active words gain from the fold
+// (L=121 +1.3%, L=301 +8%); at 4 and 6..8 words the selected form measured
+// 3-7% faster.
+template <int W>
+struct FoldSign {
+  static constexpr bool value = W <= 3 || W == 5;
+};
+
 // NX, NY >= 0 fix at compile time how many leading words have valid x / y
 // lags (the caller guarantees NX = ceil(t/32), NY = ceil((Nq-1-t)/32));
 // -1 decides per flip.
@@ -433,7 +446,9 @@ template <int W, int T, int TP, bool CENTRE, int NX = -1, int NY = -1>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
                           const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, int a, int n, int nxy, int t,
                           int Nq) {
+  constexpr bool kFold = FoldSign<W>::value;
   uint32_t acc = 0, mcnt = 0;
+  const uint32_t bm = kFold ? 0u - ba : 0u;  // all ones where s_a = -1 (folded form)
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     // which sides have valid lags in this word (the same for every lane of the warp):
@@ -449,7 +464,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     if (xa && ya) {
       const uint32_t vy = Vye[w];
       const uint32_t v1 = vx ^ vy;
-      const uint32_t gb = (vx & B[w]) | (~vx & F[w]);
+      const uint32_t gb = ((vx & B[w]) | (~vx & F[w])) ^ bm;
       const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
       const uint32_t mall = v1 | m2;
       v = popc32(m2 & (gb ^ st.ep[T - 1][w]));
@@ -464,24 +479,30 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
       mcnt = imad(popc32(m2), mu.one, mcnt);
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : Vye[w];
-      const uint32_t g = xa ? B[w] : F[w];
+      const uint32_t g = (xa ? B[w] : F[w]) ^ bm;
       v = popc32(m & (g ^ st.ep[T - 1][w]));
 #pragma unroll
       for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(m & (g ^ st.ep[tt][w])));
     }
     acc = imad(acc, mu.one, v);
   }
-  // Delta = sig * acc + mu * M + kap, (sig, mu, kap) by s_a:
-  //   s_a = +1: (-16,  16 (K1 + 4), 8 K1 n + 16 n + 32 nxy - 16 (K1 + 4) nxy)
-  //   s_a = -1: (+16, -16 (K1 - 4), -8 K1 n + 16 n - 32 nxy + 16 K1 nxy),   K1 = 2^TP - 1
   constexpr int K1 = (1 << TP) - 1;
-  const int kap0 = 8 * K1 * n + 16 * n + 32 * nxy - 16 * (K1 + 4) * nxy + kDeltaBias;
-  const int kap1 = -8 * K1 * n + 16 * n - 32 * nxy + 16 * K1 * nxy + kDeltaBias;
-  const uint32_t sig = imad(ba, 32u, (uint32_t)-16);
-  const uint32_t mul = imad(ba, (uint32_t)(-32 * K1), (uint32_t)(16 * (K1 + 4)));
-  const uint32_t kap = imad(ba, (uint32_t)(kap1 - kap0), (uint32_t)kap0);
-  const uint32_t delta = imad(acc, sig, imad(mcnt, mul, kap));
-  return imad(delta, 256u, (uint32_t)a);
+  if constexpr (kFold) {
+    const uint32_t kap = (uint32_t)((16 + 8 * K1) * n - (32 + 16 * K1) * nxy + kDeltaBias);
+    const uint32_t delta = imad(acc, (uint32_t)-16, imad(mcnt, (uint32_t)(16 * (K1 + 4)), kap));
+    return imad(delta, 256u, (uint32_t)a);
+  } else {
+    // bits not folded: S and M are taken over the window bits themselves, and
+    //   s_a = +1: Delta = -16 S + 16 (K1 + 4) M + 8 K1 n + 16 n + 32 nxy - 16 (K1 + 4) nxy
+    //   s_a = -1: Delta = +16 S - 16 (K1 - 4) M - 8 K1 n + 16 n - 32 nxy + 16 K1 nxy
+    const int kap0 = 8 * K1 * n + 16 * n + 32 * nxy - 16 * (K1 + 4) * nxy + kDeltaBias;
+    const int kap1 = -8 * K1 * n + 16 * n - 32 * nxy + 16 * K1 * nxy + kDeltaBias;
+    const uint32_t sig = imad(ba, 32u, (uint32_t)-16);
+    const uint32_t mul = imad(ba, (uint32_t)(-32 * K1), (uint32_t)(16 * (K1 + 4)));
+    const uint32_t kap = imad(ba, (uint32_t)(kap1 - kap0), (uint32_t)kap0);
+    const uint32_t delta = imad(acc, sig, imad(mcnt, mul, kap));
+    return imad(delta, 256u, (uint32_t)a);
+  }
 }
 
 // Flips t0 .. t1-1 of class q (none of them the centre): packed keys into
@@ -493,12 +514,13 @@ LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls
   using MT = MaskTable<W>;
   const int Nq = g.D - q;  // N_q without indexing g.N
   const int n = Nq - 2;    // |Vx| + |Vye| for every non-centre flip
-  for (int t = t0; t < t1; ++t) {
+  const uint32_t *row = rows + (size_t)t0 * MT::kRowWords;
+  for (int t = t0; t < t1; ++t, row += MT::kRowWords) {
     const int a = 2 * t + q;
-    const int lim = t < (Nq - 1 - t) ? t : (Nq - 1 - t);
-    const int nxy = lim - ((g.c - a) <= lim ? 1 : 0);
+    // |Vx & Vye|: min(t, Nq-1-t) = t in the scan (t <= (Nq-1)/2), less the pair lag c - a if it is <= t
+    const int nxy = t - ((g.c - a) <= t ? 1 : 0);
     uint32_t Vx[W], Vye[W];
-    load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
+    load_mask_row<W>(row, Vx, Vye);
     uint32_t x = flip_key<W, T, TP, false, NX, NY>(st, mu, B, F, Vx, Vye, ba, a, n, nxy, t, Nq);
     x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
     top_insert(top, x);
