@@ -351,6 +351,9 @@ def run_serving(args, world, rank, local):
                       "mean": float(lat.mean()), "max": float(lat.max())},
         "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
         "completed": len(results), "reached_target": int(reached),
+        # Eq. 7 of the predictive model for each request's evaluations
+        "p_optimal": {"p50": float(np.percentile([r["p_optimal"] for r in results], 50)),
+                      "min": float(min(r["p_optimal"] for r in results))},
         "device_busy_frac": st["busy_ms"] / 1e3 / (t1 - t0),
         "plain": {"value": plain_ev / (tp1 - tp0), "unit": "neighbour_evals/s",
                   "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
@@ -417,6 +420,88 @@ def run_large(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def table1_rows():
+    """Table 1 of the paper (Section 4.2), from the test fixture that records it:
+    {L: (E, F, P percent, hex)}."""
+    rows = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table1_skew_sequences.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                r = line.split()
+                rows[int(r[0])] = (int(r[1]), float(r[2]), float(r[3]), r[4])
+    return rows
+
+
+def symmetry_orbit(seq):
+    """The sequences with the same energy under negation, reversal and
+    alternating signs (s_i -> (-1)^i s_i), which keep skew symmetry."""
+    import numpy as np
+    s = np.asarray(seq, dtype=np.int8)
+    alt = np.where(np.arange(s.size) % 2 == 0, 1, -1).astype(np.int8)
+    out = []
+    for a in (s, s[::-1]):
+        for b in (a, (a * alt).astype(np.int8)):
+            out += [b, (-b).astype(np.int8)]
+    return out
+
+
+def run_table1(args, world, rank, local):
+    """Time for the plain path to reach the energy Table 1 prints for L
+    (--table1-L, default 171): walks --table1-walks, walk length 8*D (the
+    paper's rule), seed --table1-seed + rank, target E of Table 1, step budget the
+    predictive model's for probability 0.999 (Eq. 6/7), capped at
+    --table1-seconds of rounds.  Reports the model's probability (Eq. 7) for the
+    evaluations spent and whether the sequence found is Table 1's up to the
+    symmetries that keep the energy."""
+    import numpy as np
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    L = args.table1_L
+    E_tab, F_tab, P_tab, hx = table1_rows()[L]
+    D = (L + 1) // 2
+    walks, wl, seed = args.table1_walks, 8 * D, args.table1_seed + rank
+    per_round = walks * wl * D
+    budget = pkg.labs_model_budget(L, 0.999)
+    stream = torch.cuda.Stream()
+    # one round to warm up and to size the time cap in rounds
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pkg.labs_walks(L, [seed + 7919], walks, wl, per_round, stream=stream)
+    torch.cuda.synchronize()
+    t_round = time.perf_counter() - t0
+    max_rounds = max(1, int(args.table1_seconds / t_round))
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = pkg.labs_walks(L, [seed], walks, wl, budget, target_E=E_tab, max_rounds=max_rounds, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    clocks = sampler.stop()
+    E = int(r["best_E"][0])
+    evals = int(r["evals"][0])
+    tab = pkg.from_hex(hx, L)
+    same = any(np.array_equal(r["best_seq"][0], o) for o in symmetry_orbit(tab))
+    line = {
+        "metric": "time_to_target_s", "value": t if E <= E_tab else None, "unit": "s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox starts, seed %d)" % seed,
+        "config": {"workload": "table1_L%d_%dx%d" % (L, walks, wl), "L": L, "walks": walks, "walk_len": wl,
+                   "target_E": E_tab, "budget": budget, "max_rounds": max_rounds},
+        "reached": E <= E_tab, "best_E": E, "F": L * L / (2.0 * E), "rounds": int(r["rounds"][0]),
+        "evals": evals, "neighbour_evals_per_s": evals / t,
+        "model": {"nses": pkg.labs_model_nses_of_evals(L, evals),
+                  "p_optimal": pkg.labs_model_p_optimal(L, pkg.labs_model_nses_of_evals(L, evals)),
+                  "nses_limit_99_per_run_of_100": pkg.labs_model_nses_limit(L, 0.99, 100)},
+        "table1": {"E": E_tab, "F": F_tab, "P_percent": P_tab, "same_sequence_up_to_symmetry": bool(same)},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,7 +515,11 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large", "table1"])
+    ap.add_argument("--table1-L", type=int, default=171)
+    ap.add_argument("--table1-walks", type=int, default=233472)  # 3 full waves of the 3-word kernel
+    ap.add_argument("--table1-seconds", type=float, default=300.0)
+    ap.add_argument("--table1-seed", type=int, default=SEED, help="seed of rank 0 (rank r uses seed + r)")
     ap.add_argument("--kernel", type=int, default=0, help="0 library choice, 1 full scan, 2 incremental")
     ap.add_argument("--large-rounds", type=int, default=3)
     ap.add_argument("--walks-large", type=int, default=65536)
@@ -456,6 +545,9 @@ def main():
         return
     if args.workload == "large" and args.impl != "reference":
         run_large(args, world, rank, local)
+        return
+    if args.workload == "table1" and args.impl != "reference":
+        run_table1(args, world, rank, local)
         return
 
     if args.impl == "reference":

@@ -237,6 +237,9 @@ typedef struct labs_result {
   int32_t rounds;
   int32_t reached_target;    /* 1 if best_E <= the request's target */
   uint64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady clock of the server's host */
+  double p_optimal;          /* Eq. 7 for the request's evaluations: the predictive
+                                model's probability that best_E is optimal
+                                (labs_model_p_optimal of labs_model_nses_of_evals) */
 } labs_result;
 
 typedef struct labs_serve_stats {
@@ -307,6 +310,34 @@ labs_status labs_serve_destroy(labs_server *s);
 labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
                                    int64_t *walk_best_E, int8_t *walk_best_seq, int32_t *walk_moves,
                                    int32_t *walk_stuck, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Predictive model of the paper (Section 4.1, Eq. 6, Eq. 7): the evaluations
+ * a run needs to reach an optimal skew-symmetric sequence are exponentially
+ * distributed with rate lambda(L).  Host arithmetic in double precision; no
+ * GPU is involved.  Invalid arguments give NaN (or 0 for the budget).
+ * ------------------------------------------------------------------------- */
+
+/* lambda(L) = 0.006753 * 0.8617^L, the authors' trend fitted on the odd
+ * L = 71..119 with known optima (Section 4.1); used beyond that range, as the
+ * paper does, as an extrapolation.  NaN unless L is odd in LABS_L_MIN..LABS_L_MAX. */
+double labs_model_lambda(int32_t L);
+/* Eq. 6: evaluations per run (the paper's count) such that N independent runs
+ * reach an optimum with probability P: ln(1 - P) / (-lambda(L) N).
+ * NaN unless 0 <= P < 1 and N >= 1. */
+double labs_model_nses_limit(int32_t L, double P, int32_t N);
+/* Eq. 7: probability that an optimum has been reached after nses evaluations
+ * (the paper's count) in total, all runs taken as one: 1 - exp(-lambda(L) nses).
+ * NaN unless nses >= 0. */
+double labs_model_p_optimal(int32_t L, double nses);
+/* The paper's evaluation count for `evals` of this library's: the paper adds
+ * D - 1 per walk step (the previous pivot is never re-evaluated), this library
+ * counts all D flips of a step, so nses = evals (D - 1) / D. */
+double labs_model_nses_of_evals(int32_t L, uint64_t evals);
+/* The step budget (this library's evaluations, for labs_problem.step_budget or
+ * labs_walks) at which Eq. 7 reaches P: ceil(nses_limit(L, P, 1) D / (D - 1)),
+ * saturating at UINT64_MAX; 0 for invalid arguments. */
+uint64_t labs_model_budget(int32_t L, double P);
 
 /* Human-readable name of a status code (static string). */
 const char *labs_status_str(labs_status s);

@@ -15,11 +15,16 @@ restates:
   (``rand{-1,+1}``), drawn from Philox4x32-10 (Salmon et al., SC'11);
 * ``walk_trace``, ``walk_batch`` -- one contiguous self-avoiding walk, Eq. 3
   and Algorithm 2;
-* ``solve`` -- the round loop of Algorithm 1 with a neighbour-evaluation budget.
+* ``solve`` -- the round loop of Algorithm 1 with a neighbour-evaluation budget;
+* ``model_lambda``, ``model_nses_limit``, ``model_p_optimal``,
+  ``model_nses_of_evals`` -- the predictive model of Section 4.1 (the fitted
+  trend of the exponential rate lambda(L), Eq. 6 and Eq. 7), plain Python in
+  double precision.
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -172,3 +177,32 @@ def solve(L: int, seeds, walks: int, walk_len: int, step_budget: int, target_E: 
     if rc != 0:
         raise ValueError("bad arguments")
     return {"best_E": best_E, "best_seq": best_seq, "evals": evals, "rounds": rounds}
+
+
+# ---------------------------------------------------------------- Section 4.1
+def model_lambda(L: int) -> float:
+    """Rate of the exponential distribution of the solution evaluations one run
+    needs to reach an optimal skew-symmetric sequence: the authors' trend fitted
+    on L = 71..119, lambda(L) = 0.006753 * 0.8617^L (Section 4.1; used beyond
+    that range, as the paper does, as an extrapolation)."""
+    return 0.006753 * 0.8617 ** L
+
+
+def model_nses_limit(L: int, P: float, N: int) -> float:
+    """Eq. 6: evaluations per run so that N independent runs reach an optimum
+    with probability P, ln(1 - P) / (-lambda(L) N)."""
+    return math.log(1.0 - P) / (-model_lambda(L) * N)
+
+
+def model_p_optimal(L: int, nses: float) -> float:
+    """Eq. 7: probability that an optimum was reached after nses evaluations in
+    total (the runs taken together as one), 1 - exp(-lambda(L) nses)."""
+    return 1.0 - math.exp(-model_lambda(L) * nses)
+
+
+def model_nses_of_evals(L: int, evals: int) -> float:
+    """The paper's evaluation count from this project's: the paper adds D - 1
+    per walk step (the previous pivot is never re-evaluated), this project
+    counts all D flips of a step."""
+    D = (L + 1) // 2
+    return evals * (D - 1) / D

@@ -118,6 +118,7 @@ class labs_result(ctypes.Structure):
         ("t_submit_ns", ctypes.c_uint64),
         ("t_admit_ns", ctypes.c_uint64),
         ("t_done_ns", ctypes.c_uint64),
+        ("p_optimal", ctypes.c_double),
     ]
 
 
@@ -176,6 +177,11 @@ _EXPORTS = {
                                          ctypes.POINTER(labs_result), ctypes.c_void_p]),
     "labs_serve_get_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_serve_stats)]),
     "labs_serve_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "labs_model_lambda": (ctypes.c_double, [ctypes.c_int32]),
+    "labs_model_nses_limit": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
+    "labs_model_p_optimal": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double]),
+    "labs_model_nses_of_evals": (ctypes.c_double, [ctypes.c_int32, ctypes.c_uint64]),
+    "labs_model_budget": (ctypes.c_uint64, [ctypes.c_int32, ctypes.c_double]),
 }
 
 
@@ -210,6 +216,32 @@ def _check(status: int, what: str):
 
 def _ptr(a: np.ndarray):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+# --------------------------------------------- predictive model (Section 4.1, Eq. 6-7)
+def labs_model_lambda(L: int) -> float:
+    """lambda(L) of the run-length model (C ABI; NaN for an invalid L)."""
+    return load().labs_model_lambda(L)
+
+
+def labs_model_nses_limit(L: int, P: float, N: int) -> float:
+    """Eq. 6: evaluations per run (the paper's count) for probability P with N runs."""
+    return load().labs_model_nses_limit(L, P, N)
+
+
+def labs_model_p_optimal(L: int, nses: float) -> float:
+    """Eq. 7: probability of an optimum after nses evaluations (the paper's count)."""
+    return load().labs_model_p_optimal(L, nses)
+
+
+def labs_model_nses_of_evals(L: int, evals: int) -> float:
+    """The paper's evaluation count (D - 1 per step) for this library's (D per step)."""
+    return load().labs_model_nses_of_evals(L, int(evals))
+
+
+def labs_model_budget(L: int, P: float) -> int:
+    """Step budget (this library's evaluations) at which Eq. 7 reaches P; 0 if invalid."""
+    return int(load().labs_model_budget(L, P))
 
 
 def labs_energy(seq) -> int:
@@ -423,7 +455,13 @@ class Server:
         self._h = h
         self._L = {}
 
-    def submit(self, L, walks, walk_len, seed, step_budget, target_E=-1) -> int:
+    def submit(self, L, walks, walk_len, seed, step_budget=None, target_E=-1, p_target=None) -> int:
+        """Queue a request.  With p_target the step budget is the predictive
+        model's (labs_model_budget: Eq. 6/7 reach p_target)."""
+        if p_target is not None:
+            step_budget = labs_model_budget(L, p_target)
+            if step_budget == 0:
+                raise LabsError(LABS_EINVAL, "labs_model_budget")
         p = make_problem(L, walks, walk_len, seed, step_budget, target_E)
         t = ctypes.c_uint64()
         _check(load().labs_serve_submit(self._h, ctypes.byref(p), ctypes.byref(t)), "labs_serve_submit")

@@ -568,6 +568,7 @@ static void fill_result(const Request &r, labs_result *out, int8_t *best_seq) {
     out->t_submit_ns = r.t_submit;
     out->t_admit_ns = r.t_admit;
     out->t_done_ns = r.t_done;
+    out->p_optimal = labs_model_p_optimal(r.p.L, labs_model_nses_of_evals(r.p.L, r.evals));
   }
   if (best_seq && r.status == LABS_OK) std::memcpy(best_seq, r.seq.data(), r.seq.size());
 }

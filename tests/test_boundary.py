@@ -70,6 +70,7 @@ def test_struct_layouts_match_c_compiler(tmp_path):
                    ' sizeof(labs_batch_opts), offsetof(labs_batch_opts, rounds_per_launch));'
                    'printf("%zu %zu %zu %zu %zu\\n", sizeof(labs_serve_cfg), sizeof(labs_result),'
                    ' offsetof(labs_result, t_done_ns), sizeof(labs_serve_stats), offsetof(labs_serve_stats, status));'
+                   'printf("%zu\\n", offsetof(labs_result, p_optimal));'
                    'return 0;}\n')
     exe = tmp_path / "probe"
     subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -79,7 +80,7 @@ def test_struct_layouts_match_c_compiler(tmp_path):
             ctypes.sizeof(m.labs_problem), m.labs_problem.target_E.offset, ctypes.sizeof(m.labs_batch_opts),
             m.labs_batch_opts.rounds_per_launch.offset, ctypes.sizeof(m.labs_serve_cfg),
             ctypes.sizeof(m.labs_result), m.labs_result.t_done_ns.offset, ctypes.sizeof(m.labs_serve_stats),
-            m.labs_serve_stats.status.offset]
+            m.labs_serve_stats.status.offset, m.labs_result.p_optimal.offset]
     assert got == want
 
 

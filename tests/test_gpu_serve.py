@@ -31,11 +31,16 @@ def alone(m, p):
 
 
 def check(m, p, res):
+    import oracle
     E, seq, ev, rd = alone(m, p)
     assert res["status"] == m.LABS_OK
     assert res["best_E"] == E and np.array_equal(res["best_seq"], seq), p
     assert res["evals"] == ev and res["rounds"] == rd, p
     assert res["t_submit_ns"] <= res["t_admit_ns"] <= res["t_done_ns"]
+    # Eq. 7 of the predictive model for the request's evaluations
+    L = p[0]
+    want = oracle.model_p_optimal(L, oracle.model_nses_of_evals(L, res["evals"]))
+    assert res["p_optimal"] == pytest.approx(want, rel=1e-12, abs=1e-15), p
 
 
 REQS = [
@@ -124,3 +129,19 @@ def test_tickets_timeouts_and_shutdown(m):
     t0 = time.time()
     sv.close()  # shutdown with work in flight and queued: must not hang
     assert time.time() - t0 < 120
+
+
+def test_probability_target_sets_the_budget(m):
+    # the stopping rule of the predictive model: run until Eq. 7 reaches P
+    import oracle
+    with m.Server(max_walks=256) as sv:
+        reqs = [(27, 64, 216, 31, 0.99), (71, 128, 288, 32, 0.5)]
+        tickets = [sv.submit(L, w, wl, seed, p_target=P) for L, w, wl, seed, P in reqs]
+        for (L, w, wl, seed, P), t in zip(reqs, tickets):
+            r = sv.wait(t)
+            budget = m.labs_model_budget(L, P)
+            # the budget is the model's evaluation count rounded up to a whole evaluation
+            assert budget == pytest.approx(oracle.model_nses_limit(L, P, 1) * ((L + 1) // 2) / ((L - 1) // 2),
+                                           rel=1e-9, abs=1.0)
+            assert r["evals"] >= budget and r["p_optimal"] >= P
+            check(m, (L, w, wl, seed, budget), r)

@@ -8,6 +8,7 @@
 * The walk (Eq. 3, Algorithm 2): replayed against a brute-force table of all
   2^D skew energies, computed here with numpy, for every step of several walks.
 """
+import math
 import os
 
 import numpy as np
@@ -280,3 +281,56 @@ def test_batch_and_solve_round_logic(oracle_mod):
     # target energy stops at the first round boundary where it is reached
     r2 = oracle_mod.solve(L, [4], walks, wl, 10 ** 9, target_E=int(max(allE)) + 1000)
     assert int(r2["rounds"][0]) == 1
+
+
+# ------------------------------------------- predictive model (Section 4.1, Eq. 6-7)
+# lambda(L) is the paper's printed fit; the pins check Eq. 6 and Eq. 7 against
+# each other, against properties of the exponential distribution, and the fit
+# together with both equations against the P(S_best) column of Table 1.
+@pytest.mark.parametrize("L", [71, 117, 171, 223, 247])
+@pytest.mark.parametrize("P", [0.5, 0.9, 0.99])
+@pytest.mark.parametrize("N", [1, 100])
+def test_model_eq6_inverts_eq7(oracle_mod, L, P, N):
+    # N runs of NSEs_lmt each, taken as one run (Section 4.2), reach probability P
+    n = oracle_mod.model_nses_limit(L, P, N)
+    assert n > 0
+    assert oracle_mod.model_p_optimal(L, N * n) == pytest.approx(P, rel=1e-12)
+
+
+@pytest.mark.parametrize("L", [71, 121, 247, 449])
+def test_model_exponential_properties(oracle_mod, L):
+    lam = oracle_mod.model_lambda(L)
+    assert oracle_mod.model_p_optimal(L, 0.0) == 0.0
+    assert oracle_mod.model_nses_limit(L, 0.0, 100) == 0.0
+    # the median of an exponential distribution is ln 2 / lambda, its mean 1 / lambda
+    assert oracle_mod.model_p_optimal(L, math.log(2.0) / lam) == pytest.approx(0.5, rel=1e-12)
+    assert oracle_mod.model_p_optimal(L, 1.0 / lam) == pytest.approx(1.0 - math.exp(-1.0), rel=1e-12)
+    assert oracle_mod.model_p_optimal(L, 50.0 / lam) == pytest.approx(1.0, abs=1e-15)
+    # longer sequences need more evaluations for the same probability
+    assert oracle_mod.model_nses_limit(L + 2, 0.99, 1) > oracle_mod.model_nses_limit(L, 0.99, 1)
+
+
+def test_model_matches_table1_probabilities(oracle_mod):
+    # Table 1: runs of L >= 225 stopped at the 4-day limit before NSEs_lmt; their
+    # printed P(S_best) then gives, through Eq. 7, the evaluations those runs did
+    # in total.  With the fitted lambda(L) that total is the same for every L of
+    # the time-limited rows, and it falls between the 99% budgets (Eq. 6, N = 100
+    # runs) of L = 223 (printed 99%) and L = 225 (printed 98%).
+    rows = [(int(r[0]), float(r[3])) for r in read_rows("table1_skew_sequences.txt")]
+    totals = [-math.log(1.0 - p / 100.0) / oracle_mod.model_lambda(L) for L, p in rows if L >= 229]
+    assert len(totals) == 9  # L = 229, 231, 235, ..., 247
+    assert max(totals) / min(totals) < 1.08  # P printed to whole percent
+    mid = sorted(totals)[len(totals) // 2]
+    assert 100 * oracle_mod.model_nses_limit(223, 0.99, 100) < mid < 100 * oracle_mod.model_nses_limit(225, 0.99, 100)
+    # with that one total, Eq. 7 gives every printed percentage to within a point
+    # (each L's runs did a few percent more or fewer evaluations than the median)
+    for L, p in rows:
+        want = 100 * oracle_mod.model_p_optimal(L, mid)
+        assert abs(want - p) <= 1.0 or (p == 99 and want >= 99), (L, p, want)
+
+
+def test_model_counts_d_minus_1_per_step(oracle_mod):
+    # the paper adds D - 1 evaluations per walk step, this project D
+    L, walks, steps = 121, 1000, 8192
+    D = (L + 1) // 2
+    assert oracle_mod.model_nses_of_evals(L, walks * steps * D) == walks * steps * (D - 1)
