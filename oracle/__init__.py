@@ -14,7 +14,9 @@ restates:
 * ``philox4x32_10``, ``start_free_values`` -- the random first pivot of Eq. 3
   (``rand{-1,+1}``), drawn from Philox4x32-10 (Salmon et al., SC'11);
 * ``walk_trace``, ``walk_batch`` -- one contiguous self-avoiding walk, Eq. 3
-  and Algorithm 2;
+  and Algorithm 2 (with ``full=True`` over all length-L sequences, the search
+  space the paper leaves to future work in Section 5: L flips of one position
+  each, the whole sequence as key);
 * ``solve`` -- the round loop of Algorithm 1 with a neighbour-evaluation budget;
 * ``model_lambda``, ``model_nses_limit``, ``model_p_optimal``,
   ``model_nses_of_evals`` -- the predictive model of Section 4.1 (the fitted
@@ -67,6 +69,11 @@ def _load():
         lib.oracle_solve.restype = ctypes.c_int32
         lib.oracle_solve.argtypes = [ctypes.c_int32, u64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, i64p, i8p, u64p, i32p]
+        for space_fn, twin in [("oracle_full_walk_trace", lib.oracle_walk_trace),
+                               ("oracle_full_walk_batch", lib.oracle_walk_batch),
+                               ("oracle_full_solve", lib.oracle_solve)]:
+            fn = getattr(lib, space_fn)
+            fn.restype, fn.argtypes = twin.restype, twin.argtypes
         _lib = lib
     return _lib
 
@@ -118,8 +125,10 @@ def start_free_values(seed: int, walk: int, round_: int, D: int) -> np.ndarray:
     return out
 
 
-def walk_trace(L: int, seed: int, walk: int, round_: int, walk_len: int, check: bool = False) -> dict:
-    """One contiguous SAW (Eq. 3, Algorithm 2) with its full trajectory."""
+def walk_trace(L: int, seed: int, walk: int, round_: int, walk_len: int, check: bool = False,
+               full: bool = False) -> dict:
+    """One contiguous SAW (Eq. 3, Algorithm 2) with its full trajectory; `full`
+    walks the whole space of length-L sequences instead of the skew-symmetric one."""
     flips = np.full(max(walk_len, 1), -1, dtype=np.int32)
     energies = np.full(walk_len + 1, -1, dtype=np.int64)
     best_seq = np.zeros(L, dtype=np.int8)
@@ -127,10 +136,10 @@ def walk_trace(L: int, seed: int, walk: int, round_: int, walk_len: int, check: 
     moves = np.zeros(1, dtype=np.int32)
     stuck = np.zeros(1, dtype=np.int32)
     best_step = np.zeros(1, dtype=np.int32)
-    rc = _load().oracle_walk_trace(L, seed, walk, round_, walk_len, int(check), _p(flips, ctypes.c_int32),
-                                   _p(energies, ctypes.c_int64), _p(best_seq, ctypes.c_int8),
-                                   _p(best_E, ctypes.c_int64), _p(moves, ctypes.c_int32),
-                                   _p(stuck, ctypes.c_int32), _p(best_step, ctypes.c_int32))
+    fn = _load().oracle_full_walk_trace if full else _load().oracle_walk_trace
+    rc = fn(L, seed, walk, round_, walk_len, int(check), _p(flips, ctypes.c_int32),
+            _p(energies, ctypes.c_int64), _p(best_seq, ctypes.c_int8), _p(best_E, ctypes.c_int64),
+            _p(moves, ctypes.c_int32), _p(stuck, ctypes.c_int32), _p(best_step, ctypes.c_int32))
     if rc < 0:
         raise ValueError("bad arguments")
     m = int(moves[0])
@@ -147,23 +156,24 @@ def walk_trace(L: int, seed: int, walk: int, round_: int, walk_len: int, check: 
 
 
 def walk_batch(L: int, seed: int, round_: int, walk_begin: int, n_walks: int, walk_len: int,
-               threads: int = 1) -> dict:
+               threads: int = 1, full: bool = False) -> dict:
     """Walks [walk_begin, walk_begin + n_walks) of one round, per-walk results."""
     best_E = np.zeros(n_walks, dtype=np.int64)
     best_seq = np.zeros((n_walks, L), dtype=np.int8)
     moves = np.zeros(n_walks, dtype=np.int32)
     stuck = np.zeros(n_walks, dtype=np.int32)
     evals = np.zeros(n_walks, dtype=np.int64)
-    rc = _load().oracle_walk_batch(L, seed, round_, walk_begin, n_walks, walk_len, threads,
-                                   _p(best_E, ctypes.c_int64), _p(best_seq, ctypes.c_int8),
-                                   _p(moves, ctypes.c_int32), _p(stuck, ctypes.c_int32), _p(evals, ctypes.c_int64))
+    fn = _load().oracle_full_walk_batch if full else _load().oracle_walk_batch
+    rc = fn(L, seed, round_, walk_begin, n_walks, walk_len, threads, _p(best_E, ctypes.c_int64),
+            _p(best_seq, ctypes.c_int8), _p(moves, ctypes.c_int32), _p(stuck, ctypes.c_int32),
+            _p(evals, ctypes.c_int64))
     if rc != 0:
         raise ValueError("bad arguments")
     return {"best_E": best_E, "best_seq": best_seq, "moves": moves, "stuck": stuck, "evals": evals}
 
 
 def solve(L: int, seeds, walks: int, walk_len: int, step_budget: int, target_E: int = -1,
-          threads: int = 1) -> dict:
+          threads: int = 1, full: bool = False) -> dict:
     """Algorithm 1: rounds of `walks` SAWs per seed until the evaluation budget (or target) is met."""
     sd = np.ascontiguousarray(seeds, dtype=np.uint64)
     n = sd.size
@@ -171,9 +181,10 @@ def solve(L: int, seeds, walks: int, walk_len: int, step_budget: int, target_E: 
     best_seq = np.zeros((n, L), dtype=np.int8)
     evals = np.zeros(n, dtype=np.uint64)
     rounds = np.zeros(n, dtype=np.int32)
-    rc = _load().oracle_solve(L, _p(sd, ctypes.c_uint64), n, walks, walk_len, step_budget, target_E, threads,
-                              _p(best_E, ctypes.c_int64), _p(best_seq, ctypes.c_int8), _p(evals, ctypes.c_uint64),
-                              _p(rounds, ctypes.c_int32))
+    fn = _load().oracle_full_solve if full else _load().oracle_solve
+    rc = fn(L, _p(sd, ctypes.c_uint64), n, walks, walk_len, step_budget, target_E, threads,
+            _p(best_E, ctypes.c_int64), _p(best_seq, ctypes.c_int8), _p(evals, ctypes.c_uint64),
+            _p(rounds, ctypes.c_int32))
     if rc != 0:
         raise ValueError("bad arguments")
     return {"best_E": best_E, "best_seq": best_seq, "evals": evals, "rounds": rounds}

@@ -15,6 +15,10 @@
 //             so the first D values are free and the rest follow from them;
 //   * a flip j (0 <= j < D) negates free value s_{j+1} and therefore also its
 //             mirror s_{L-j} (the same position when j = D-1, the centre);
+//   * the full search space (all 2^L sequences, any L; the solver the paper
+//             leaves to future work in Section 5): all L values are free, a
+//             flip j (0 <= j < L) negates s_{j+1} alone, and the key of a
+//             pivot is the whole sequence;
 //   * bit convention for starts, keys and hex strings: bit 1 <-> -1, 0 <-> +1.
 //
 // Parity status: every function here is pinned by tests that do not call
@@ -112,6 +116,16 @@ using Key = std::vector<int8_t>;  // the D free values identify a skew pivot
 
 Key key_of(const std::vector<int8_t> &s, int D) { return Key(s.begin(), s.begin() + D); }
 
+// The search space of a walk: the skew-symmetric sequences (D free values,
+// flip j negates positions j and L-1-j) or all sequences (L free values, flip
+// j negates position j).
+struct Space {
+  bool full;
+  int L;
+  int free_values() const { return full ? L : (L + 1) / 2; }
+  int mirror(int j) const { return full ? j : L - 1 - j; }
+};
+
 // Change of C_k (k = 1..L-1) when the positions in {p, q} are negated.
 // A product s_i s_{i+k} changes sign iff exactly one of its two positions is
 // negated, so dC_k = sum of -2 s_i s_{i+k} over those pairs.  This is the
@@ -151,12 +165,13 @@ void sidelobe_change(const std::vector<int8_t> &s, int L, int p, int q, std::vec
 // sidelobe array are also recomputed from Eq. 1 and compared (aborting on a
 // mismatch).  `flips_out` (walk_len entries) and `energy_out` (walk_len + 1
 // entries) optionally record the trajectory.
-WalkResult run_walk(int L, uint64_t seed, uint32_t walk, uint32_t round, int walk_len, bool check,
+WalkResult run_walk(const Space &sp, uint64_t seed, uint32_t walk, uint32_t round, int walk_len, bool check,
                     int32_t *flips_out, int64_t *energy_out, int *check_failed) {
-  const int D = (L + 1) / 2;
+  const int L = sp.L;
+  const int D = sp.free_values();  // flips per step and length of a key
   std::vector<int8_t> s(L);
   start_free_values(seed, walk, round, D, s.data());
-  skew_expand(s.data(), L);
+  if (!sp.full) skew_expand(s.data(), L);
 
   std::vector<int64_t> C(L);
   for (int k = 0; k < L; ++k) C[k] = autocorrelation(s.data(), L, k);
@@ -178,7 +193,7 @@ WalkResult run_walk(int L, uint64_t seed, uint32_t walk, uint32_t round, int wal
     int best_j = -1;
     int64_t best_delta = 0;
     for (int j = 0; j < D; ++j) {
-      const int p = j, q = L - 1 - j;
+      const int p = j, q = sp.mirror(j);
       sidelobe_change(s, L, p, q, dC);
       int64_t delta = 0;
       for (int k = 1; k < L; ++k) delta += (C[k] + dC[k]) * (C[k] + dC[k]) - C[k] * C[k];
@@ -202,7 +217,7 @@ WalkResult run_walk(int L, uint64_t seed, uint32_t walk, uint32_t round, int wal
       res.stuck = 1;
       break;
     }
-    const int p = best_j, q = L - 1 - best_j;
+    const int p = best_j, q = sp.mirror(best_j);
     s[p] = (int8_t)-s[p];
     if (q != p) s[q] = (int8_t)-s[q];
     for (int k = 1; k < L; ++k) C[k] += best_dC[k];
@@ -268,13 +283,12 @@ void oracle_start_free_values(uint64_t seed, uint32_t walk, uint32_t round, int3
 // each step), energy_out: walk_len + 1 int64 (E of P_1 .. P_{walk_len+1}),
 // best_seq_out: L int8.  Returns 0, or 1 if check mode found a mismatch, or
 // -1 on bad arguments.  Any of the output pointers may be null.
-int32_t oracle_walk_trace(int32_t L, uint64_t seed, uint32_t walk, uint32_t round, int32_t walk_len,
-                          int32_t check, int32_t *flips_out, int64_t *energy_out, int8_t *best_seq_out,
-                          int64_t *best_E_out, int32_t *moves_out, int32_t *stuck_out, int32_t *best_step_out) {
-  if (L < 5 || (L % 2) == 0 || walk_len < 0) return -1;
+static int32_t walk_trace_impl(const Space &sp, uint64_t seed, uint32_t walk, uint32_t round, int32_t walk_len,
+                               int32_t check, int32_t *flips_out, int64_t *energy_out, int8_t *best_seq_out,
+                               int64_t *best_E_out, int32_t *moves_out, int32_t *stuck_out, int32_t *best_step_out) {
   int failed = 0;
-  WalkResult r = run_walk(L, seed, walk, round, walk_len, check != 0, flips_out, energy_out, &failed);
-  if (best_seq_out) std::memcpy(best_seq_out, r.best_seq.data(), (size_t)L);
+  WalkResult r = run_walk(sp, seed, walk, round, walk_len, check != 0, flips_out, energy_out, &failed);
+  if (best_seq_out) std::memcpy(best_seq_out, r.best_seq.data(), (size_t)sp.L);
   if (best_E_out) *best_E_out = r.best_E;
   if (moves_out) *moves_out = r.moves;
   if (stuck_out) *stuck_out = r.stuck;
@@ -282,20 +296,37 @@ int32_t oracle_walk_trace(int32_t L, uint64_t seed, uint32_t walk, uint32_t roun
   return failed ? 1 : 0;
 }
 
+int32_t oracle_walk_trace(int32_t L, uint64_t seed, uint32_t walk, uint32_t round, int32_t walk_len,
+                          int32_t check, int32_t *flips_out, int64_t *energy_out, int8_t *best_seq_out,
+                          int64_t *best_E_out, int32_t *moves_out, int32_t *stuck_out, int32_t *best_step_out) {
+  if (L < 5 || (L % 2) == 0 || walk_len < 0) return -1;
+  return walk_trace_impl(Space{false, L}, seed, walk, round, walk_len, check, flips_out, energy_out, best_seq_out,
+                         best_E_out, moves_out, stuck_out, best_step_out);
+}
+
+// The same walk over the full search space (any L >= 2).
+int32_t oracle_full_walk_trace(int32_t L, uint64_t seed, uint32_t walk, uint32_t round, int32_t walk_len,
+                               int32_t check, int32_t *flips_out, int64_t *energy_out, int8_t *best_seq_out,
+                               int64_t *best_E_out, int32_t *moves_out, int32_t *stuck_out, int32_t *best_step_out) {
+  if (L < 2 || walk_len < 0) return -1;
+  return walk_trace_impl(Space{true, L}, seed, walk, round, walk_len, check, flips_out, energy_out, best_seq_out,
+                         best_E_out, moves_out, stuck_out, best_step_out);
+}
+
 // A batch of walks [walk_begin, walk_begin + n_walks) of one round, run on
 // `threads` host threads.  Per walk: best E, best sequence (L int8), moves,
 // stuck flag, neighbour evaluations.
-int32_t oracle_walk_batch(int32_t L, uint64_t seed, uint32_t round, uint32_t walk_begin, int32_t n_walks,
-                          int32_t walk_len, int32_t threads, int64_t *best_E, int8_t *best_seq,
-                          int32_t *moves, int32_t *stuck, int64_t *evals) {
-  if (L < 5 || (L % 2) == 0 || walk_len < 0 || n_walks < 0) return -1;
+static int32_t walk_batch_impl(const Space &sp, uint64_t seed, uint32_t round, uint32_t walk_begin,
+                               int32_t n_walks, int32_t walk_len, int32_t threads, int64_t *best_E,
+                               int8_t *best_seq, int32_t *moves, int32_t *stuck, int64_t *evals) {
+  const int L = sp.L;
   if (threads < 1) threads = 1;
   std::vector<std::thread> pool;
   for (int t = 0; t < threads; ++t) {
     pool.emplace_back([=]() {
       for (int w = t; w < n_walks; w += threads) {
         int failed = 0;
-        WalkResult r = run_walk(L, seed, walk_begin + (uint32_t)w, round, walk_len, false, nullptr, nullptr, &failed);
+        WalkResult r = run_walk(sp, seed, walk_begin + (uint32_t)w, round, walk_len, false, nullptr, nullptr, &failed);
         if (best_E) best_E[w] = r.best_E;
         if (best_seq) std::memcpy(best_seq + (size_t)w * L, r.best_seq.data(), (size_t)L);
         if (moves) moves[w] = r.moves;
@@ -308,16 +339,32 @@ int32_t oracle_walk_batch(int32_t L, uint64_t seed, uint32_t round, uint32_t wal
   return 0;
 }
 
+int32_t oracle_walk_batch(int32_t L, uint64_t seed, uint32_t round, uint32_t walk_begin, int32_t n_walks,
+                          int32_t walk_len, int32_t threads, int64_t *best_E, int8_t *best_seq,
+                          int32_t *moves, int32_t *stuck, int64_t *evals) {
+  if (L < 5 || (L % 2) == 0 || walk_len < 0 || n_walks < 0) return -1;
+  return walk_batch_impl(Space{false, L}, seed, round, walk_begin, n_walks, walk_len, threads, best_E, best_seq,
+                         moves, stuck, evals);
+}
+
+int32_t oracle_full_walk_batch(int32_t L, uint64_t seed, uint32_t round, uint32_t walk_begin, int32_t n_walks,
+                               int32_t walk_len, int32_t threads, int64_t *best_E, int8_t *best_seq,
+                               int32_t *moves, int32_t *stuck, int64_t *evals) {
+  if (L < 2 || walk_len < 0 || n_walks < 0) return -1;
+  return walk_batch_impl(Space{true, L}, seed, round, walk_begin, n_walks, walk_len, threads, best_E, best_seq,
+                         moves, stuck, evals);
+}
+
 // The whole solve of Algorithm 1 for each of n_seeds independent problems:
 // rounds r = 0, 1, ... each run `walks` contiguous SAWs; after each round the
 // problem's best is the minimum over walks by (E, round, walk); rounds go on
 // while the neighbour evaluations done are below step_budget and (when
 // target_E >= 0) the best E is above target_E.  Outputs per seed: best_E,
 // best_seq (L int8), evals done, rounds run.
-int32_t oracle_solve(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks, int32_t walk_len,
-                     uint64_t step_budget, int64_t target_E, int32_t threads, int64_t *best_E,
-                     int8_t *best_seq, uint64_t *evals_out, int32_t *rounds_out) {
-  if (L < 5 || (L % 2) == 0 || walks < 1 || walk_len < 0 || step_budget == 0 || !seeds) return -1;
+static int32_t solve_impl(const Space &sp, const uint64_t *seeds, int32_t n_seeds, int32_t walks, int32_t walk_len,
+                          uint64_t step_budget, int64_t target_E, int32_t threads, int64_t *best_E,
+                          int8_t *best_seq, uint64_t *evals_out, int32_t *rounds_out) {
+  const int L = sp.L;
   std::vector<int64_t> bE(walks), ev(walks);
   std::vector<int8_t> bS((size_t)walks * L);
   for (int si = 0; si < n_seeds; ++si) {
@@ -326,8 +373,8 @@ int32_t oracle_solve(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t 
     std::vector<int8_t> cur_seq(L);
     uint32_t round = 0;
     for (;;) {
-      oracle_walk_batch(L, seeds[si], round, 0, walks, walk_len, threads, bE.data(), bS.data(), nullptr,
-                        nullptr, ev.data());
+      walk_batch_impl(sp, seeds[si], round, 0, walks, walk_len, threads, bE.data(), bS.data(), nullptr, nullptr,
+                      ev.data());
       for (int w = 0; w < walks; ++w) {
         done += (uint64_t)ev[w];
         if (cur < 0 || bE[w] < cur) {
@@ -345,6 +392,22 @@ int32_t oracle_solve(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t 
     if (rounds_out) rounds_out[si] = (int32_t)round;
   }
   return 0;
+}
+
+int32_t oracle_solve(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks, int32_t walk_len,
+                     uint64_t step_budget, int64_t target_E, int32_t threads, int64_t *best_E,
+                     int8_t *best_seq, uint64_t *evals_out, int32_t *rounds_out) {
+  if (L < 5 || (L % 2) == 0 || walks < 1 || walk_len < 0 || step_budget == 0 || !seeds) return -1;
+  return solve_impl(Space{false, L}, seeds, n_seeds, walks, walk_len, step_budget, target_E, threads, best_E,
+                    best_seq, evals_out, rounds_out);
+}
+
+int32_t oracle_full_solve(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks, int32_t walk_len,
+                          uint64_t step_budget, int64_t target_E, int32_t threads, int64_t *best_E,
+                          int8_t *best_seq, uint64_t *evals_out, int32_t *rounds_out) {
+  if (L < 2 || walks < 1 || walk_len < 0 || step_budget == 0 || !seeds) return -1;
+  return solve_impl(Space{true, L}, seeds, n_seeds, walks, walk_len, step_budget, target_E, threads, best_E,
+                    best_seq, evals_out, rounds_out);
 }
 
 }  // extern "C"

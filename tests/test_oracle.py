@@ -334,3 +334,73 @@ def test_model_counts_d_minus_1_per_step(oracle_mod):
     L, walks, steps = 121, 1000, 8192
     D = (L + 1) // 2
     assert oracle_mod.model_nses_of_evals(L, walks * steps * D) == walks * steps * (D - 1)
+
+
+# ------------------------------------------- full search space (Section 5, future work)
+def brute_table_full(L):
+    """Energy of every length-L sequence, indexed by its code (bit p <-> s_{p+1} = -1)."""
+    codes = np.arange(1 << L, dtype=np.int64)
+    seqs = (1 - 2 * ((codes[:, None] >> np.arange(L)[None, :]) & 1)).astype(np.int64)
+    E = np.zeros(codes.size, dtype=np.int64)
+    for k in range(1, L):
+        Ck = np.sum(seqs[:, :L - k] * seqs[:, k:], axis=1)
+        E += Ck * Ck
+    return E
+
+
+def replay_full(oracle_mod, L, seed, walk, rnd, walk_len, table):
+    """Re-derive a full-space walk from the brute-force table: L single-position
+    flips, every step to the lowest-energy unvisited neighbour (lowest flip on
+    ties), the first pivot from the same Philox stream with L values."""
+    tr = oracle_mod.walk_trace(L, seed, walk, rnd, walk_len, check=True, full=True)
+    assert not tr["check_failed"]
+    cur = code_of(oracle_mod.start_free_values(seed, walk, rnd, L))
+    visited = {cur}
+    energies = [int(table[cur])]
+    flips = []
+    stuck = 0
+    for _ in range(walk_len):
+        cands = [(int(table[cur ^ (1 << j)]), j) for j in range(L) if (cur ^ (1 << j)) not in visited]
+        if not cands:
+            stuck = 1
+            break
+        e, j = min(cands)
+        cur ^= 1 << j
+        visited.add(cur)
+        flips.append(j)
+        energies.append(e)
+    assert tr["moves"] == len(flips) and tr["stuck"] == stuck
+    assert list(tr["flips"]) == flips and list(tr["energies"]) == energies
+    best = min(energies)
+    assert tr["best_E"] == best and tr["best_step"] == energies.index(best)
+    assert int(table[code_of(tr["best_seq"])]) == best
+    return tr, stuck
+
+
+@pytest.mark.parametrize("L,walk_len", [(2, 5), (3, 10), (4, 20), (5, 40), (6, 70), (8, 300), (10, 1100),
+                                        (12, 400), (13, 600)])
+def test_full_space_walks_vs_bruteforce(oracle_mod, L, walk_len):
+    table = brute_table_full(L)
+    stuck_seen = 0
+    for w in range(6):
+        tr, stuck = replay_full(oracle_mod, L, 5, w, 2, walk_len, table)
+        stuck_seen += stuck
+    if walk_len >= (1 << L):
+        assert stuck_seen == 6
+
+
+def test_full_space_reaches_the_brute_force_optimum(oracle_mod):
+    # small spaces: some walk of a few rounds reaches the global optimum of Eq. 1
+    for L in (7, 11, 13):
+        table = brute_table_full(L)
+        r = oracle_mod.solve(L, [9], 64, 8 * L, 64 * 8 * L * L * 3, full=True)
+        assert int(r["best_E"][0]) == int(table.min())
+        assert int(table[code_of(r["best_seq"][0])]) == int(r["best_E"][0])
+
+
+@pytest.mark.parametrize("L", [20, 33, 64])
+def test_full_space_incremental_matches_eq1(oracle_mod, L):
+    # every neighbour and pivot energy of a longer walk recomputed from Eq. 1
+    tr = oracle_mod.walk_trace(L, 11, 1, 0, 300, check=True, full=True)
+    assert not tr["check_failed"] and tr["moves"] == 300
+    assert oracle_mod.energy(tr["best_seq"]) == tr["best_E"]
