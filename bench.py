@@ -66,11 +66,12 @@ def digits_for(L):
     return T
 
 
-def core_alu_ops_per_eval(L, planes):
+def core_alu_ops_per_eval(L, planes, full=False):
     """ALU-pipe lane-ops of the bit-sliced Delta core per neighbour evaluation:
     per 32 lags and digit plane, two masked XORs and a carry-save full adder
-    (4 LOP3), for the number of digit planes the scan used."""
-    m = (L - 1) // 2
+    (4 LOP3), for the number of digit planes the scan used; the lags are the
+    (L-1)/2 even ones of a skew sequence or all L-1 in the full space."""
+    m = (L - 1) if full else (L - 1) // 2
     return 4.0 * planes * m / 32.0
 
 
@@ -154,13 +155,13 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS):
+def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS, full=False):
     """The oracle on a bounded sample of the benchmark's walks, all host cores."""
     import oracle
     cores = os.cpu_count() or 1
     n = n_walks or 8 * cores
     t0 = time.perf_counter()
-    r = oracle.walk_batch(L, seed, 0, 0, n, walk_len, threads=cores)
+    r = oracle.walk_batch(L, seed, 0, 0, n, walk_len, threads=cores, full=full)
     dt = time.perf_counter() - t0
     ev = int(r["evals"].sum())
     return {"value": ev / dt, "unit": "neighbour_evals/s", "cores": cores, "kind": "oracle",
@@ -521,6 +522,8 @@ def main():
     ap.add_argument("--table1-seconds", type=float, default=300.0)
     ap.add_argument("--table1-seed", type=int, default=SEED, help="seed of rank 0 (rank r uses seed + r)")
     ap.add_argument("--kernel", type=int, default=0, help="0 library choice, 1 full scan, 2 incremental")
+    ap.add_argument("--space", default="skew", choices=["skew", "full"],
+                    help="plain workload over the skew-symmetric sequences or all length-L sequences")
     ap.add_argument("--large-rounds", type=int, default=3)
     ap.add_argument("--walks-large", type=int, default=65536)
     ap.add_argument("--walk-len-large", type=int, default=16384)
@@ -568,7 +571,9 @@ def main():
     seed = rank_seed(rank)
     L = args.L
     walks, wl, budget = args.walks, args.walk_len, args.budget
-    ws_bytes = pkg.labs_walks_workspace_size(L, 1, walks, wl)
+    full = args.space == "full"
+    flips = L if full else (L + 1) // 2  # neighbour evaluations per walk step
+    ws_bytes = pkg.labs_walks_workspace_size(L, 1, walks, wl, space=args.space)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     seeds_d = torch.tensor([seed], dtype=torch.int64, device="cuda")
     best_seq_d = torch.zeros((1, L), dtype=torch.int8, device="cuda")
@@ -576,7 +581,7 @@ def main():
 
     def device_step():
         return pkg.labs_walks_device(L, seeds_d, walks, wl, budget, best_seq_d, best_E_d, stream=stream,
-                                     workspace=ws, kernel=args.kernel)
+                                     workspace=ws, kernel=args.kernel, space=args.space)
 
     def barrier():
         if dist is not None:
@@ -617,11 +622,11 @@ def main():
     e2e_evals = 0
     t0 = t1 = 0.0
     if not args.device_only:
-        pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel)  # first call maps the allocator pool
+        pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel, space=args.space)  # maps the pool
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            r = pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel)
+            r = pkg.labs_walks(L, [seed], walks, wl, budget, kernel=args.kernel, space=args.space)
             e2e_evals += int(r["evals"].sum())
         t1 = time.perf_counter()
         barrier()
@@ -636,9 +641,8 @@ def main():
         value = tot_evals / dev_s
         per_launch_ms = walk_ms / max(walk_launches, 1)
         evals_per_launch = total_evals / max(walk_launches, 1)
-        D = (L + 1) // 2
-        avg_planes = planes / max(total_evals / D, 1.0)
-        ops_per_eval = core_alu_ops_per_eval(L, avg_planes)
+        avg_planes = planes / max(total_evals / flips, 1.0)
+        ops_per_eval = core_alu_ops_per_eval(L, avg_planes, full)
         achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3) / 1e12
         peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
         line = {
@@ -646,19 +650,23 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (Philox-drawn uniform +-1 starts, seed %d per rank)" % SEED,
-            "config": {"workload": ("plain_L121_131072x8192_budget1e11" if (L, walks, wl, budget) == (121, WALKS, WALK_LEN, BUDGET)
-                                    else "plain_L%d_%dx%d_budget%d" % (L, walks, wl, budget)),
+            "config": {"workload": ("plain_L121_131072x8192_budget1e11"
+                                    if (L, walks, wl, budget, full) == (121, WALKS, WALK_LEN, BUDGET, False)
+                                    else "plain_%sL%d_%dx%d_budget%d" % ("full_" if full else "", L, walks, wl,
+                                                                          budget)),
+                       "space": args.space,
                        "L": L, "walks": walks, "walk_len": wl,
                        "budget": budget, "rounds_per_step": int(round(total_evals / args.steps /
-                                                                     (walks * wl * ((L + 1) // 2)))),
+                                                                     (walks * wl * flips))),
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GiB of visited tables per round" % (ws_bytes / 2 ** 30)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
                          "frac": achieved / peak,
                          "traffic": (TRAFFIC["bytes_per_launch"]
                                      if (walk_sources_hash() == TRAFFIC["sources_sha256_prefix"]
-                                         and (L, walks, wl) == (DEFAULT_L, WALKS, WALK_LEN)) else None),
-                         "kernel": "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32),
+                                         and (L, walks, wl, full) == (DEFAULT_L, WALKS, WALK_LEN, False)) else None),
+                         "kernel": ("full_walk_kernel<W=%d,K=4>" % ((L - 1 + 31) // 32) if full
+                                    else "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32)),
                          "kernel_ms_per_launch": per_launch_ms,
                          "ops_per_eval": ops_per_eval, "avg_digit_planes": avg_planes,
                          "peak_basis": "152 SMs x 64 lanes/clk (measured LOP3 rate) x 2070 MHz max clock"},
@@ -668,7 +676,7 @@ def main():
             "clocks": clocks,
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks)
+            line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks, full=full)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

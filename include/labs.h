@@ -63,6 +63,9 @@ typedef int32_t labs_status;
 
 #define LABS_L_MIN 5
 #define LABS_L_MAX 511
+/* lengths accepted by the full-search-space functions (labs_walks_full, ...) */
+#define LABS_FULL_L_MIN 3
+#define LABS_FULL_L_MAX 256
 
 /* Options of labs_walks.  Zero-initialise (or call labs_opts_init), then set
  * what you need. */
@@ -310,6 +313,30 @@ labs_status labs_serve_destroy(labs_server *s);
 labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
                                    int64_t *walk_best_E, int8_t *walk_best_seq, int32_t *walk_moves,
                                    int32_t *walk_stuck, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * The full search space: all 2^L binary sequences of length L, any parity,
+ * LABS_FULL_L_MIN <= L <= LABS_FULL_L_MAX.  The paper restricts its solver to
+ * the skew-symmetric sequences and leaves the full space to future work
+ * (Section 5); these functions run the same contiguous self-avoiding walks
+ * (Eq. 3, Algorithm 2) and round loop (Algorithm 1) over it: a flip negates
+ * one position, every step evaluates all L flips (so one step is L neighbour
+ * evaluations), the visited sets hold whole sequences, and the first pivot
+ * takes its L values from the Philox stream layout of the skew functions.
+ * Arguments, outputs, ownership and status codes are those of the skew
+ * functions above (labs_opts.kernel: 0 or 1; the incremental variant is
+ * skew-only).  LABS_EINVAL for an L outside the range.
+ * ------------------------------------------------------------------------- */
+labs_status labs_walks_full(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
+                            int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
+                            const labs_opts *opts, labs_stats *stats);
+size_t labs_walks_full_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len);
+labs_status labs_saw_round_full(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
+                                int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
+                                int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
+                                int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
+                                int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
+                                int32_t *visited_count);
 
 /* ---------------------------------------------------------------------------
  * Predictive model of the paper (Section 4.1, Eq. 6, Eq. 7): the evaluations

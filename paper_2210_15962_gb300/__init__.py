@@ -177,6 +177,16 @@ _EXPORTS = {
                                          ctypes.POINTER(labs_result), ctypes.c_void_p]),
     "labs_serve_get_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_serve_stats)]),
     "labs_serve_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
+    "labs_walks_full": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(labs_opts), ctypes.POINTER(labs_stats)]),
+    "labs_walks_full_workspace_size": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.c_int32]),
+    "labs_saw_round_full": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                             ctypes.c_int32, ctypes.c_void_p]),
     "labs_model_lambda": (ctypes.c_double, [ctypes.c_int32]),
     "labs_model_nses_limit": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
     "labs_model_p_optimal": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double]),
@@ -290,17 +300,30 @@ def make_opts(stream=None, device_buffers=False, recheck_every=0, target_E=-1, m
     return o
 
 
-def labs_walks_workspace_size(L: int, n_seeds: int, walks_per_seed: int, walk_len: int) -> int:
-    return int(load().labs_walks_workspace_size(L, n_seeds, walks_per_seed, walk_len))
+SPACES = ("skew", "full")  # the skew-symmetric sequences of odd L, or all 2^L sequences
+
+
+def _space(space: str) -> bool:
+    if space not in SPACES:
+        raise ValueError("space must be 'skew' or 'full'")
+    return space == "full"
+
+
+def labs_walks_workspace_size(L: int, n_seeds: int, walks_per_seed: int, walk_len: int, space: str = "skew") -> int:
+    fn = load().labs_walks_full_workspace_size if _space(space) else load().labs_walks_workspace_size
+    return int(fn(L, n_seeds, walks_per_seed, walk_len))
 
 
 def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, *, target_E: int = -1,
-               max_rounds: int = 0, recheck_every: int = 0, stream=None, workspace=None, kernel: int = 0) -> dict:
-    """Algorithm 1 around Algorithm 2 for every seed; host buffers in and out.
+               max_rounds: int = 0, recheck_every: int = 0, stream=None, workspace=None, kernel: int = 0,
+               space: str = "skew") -> dict:
+    """Algorithm 1 around Algorithm 2 for every seed; host buffers in and out
+    (space="full": labs_walks_full over all 2^L sequences).
 
     Returns dict(best_seq=(n, L) int8, best_E=(n,) int64, evals=(n,) uint64,
     rounds=(n,) int32, stats=dict).
     """
+    full = _space(space)
     sd = np.ascontiguousarray(np.atleast_1d(np.asarray(seeds, dtype=np.uint64)))
     n = sd.size
     best_seq = np.zeros((n, L), dtype=np.int8)
@@ -310,30 +333,37 @@ def labs_walks(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: i
     o = make_opts(stream=stream, recheck_every=recheck_every, target_E=target_E, max_rounds=max_rounds,
                   workspace=workspace, evals_per_seed=evals, rounds_per_seed=rounds, kernel=kernel)
     stats = labs_stats()
-    _check(load().labs_walks(L, _ptr(sd), n, walks_per_seed, walk_len, step_budget, _ptr(best_seq), _ptr(best_E),
-                             ctypes.byref(o), ctypes.byref(stats)), "labs_walks")
+    fn = load().labs_walks_full if full else load().labs_walks
+    _check(fn(L, _ptr(sd), n, walks_per_seed, walk_len, step_budget, _ptr(best_seq), _ptr(best_E), ctypes.byref(o),
+              ctypes.byref(stats)), "labs_walks_full" if full else "labs_walks")
     return {"best_seq": best_seq, "best_E": best_E, "evals": evals, "rounds": rounds, "stats": stats.as_dict()}
 
 
 def labs_walks_device(L: int, seeds, walks_per_seed: int, walk_len: int, step_budget: int, best_seq, best_E, *,
                       target_E: int = -1, max_rounds: int = 0, recheck_every: int = 0, stream=None,
-                      workspace=None, evals_per_seed=None, rounds_per_seed=None, kernel: int = 0) -> dict:
+                      workspace=None, evals_per_seed=None, rounds_per_seed=None, kernel: int = 0,
+                      space: str = "skew") -> dict:
     """labs_walks on device-resident buffers (torch CUDA tensors): seeds int64/uint64 (n,),
     best_seq int8 (n, L), best_E int64 (n,).  Stream-ordered; returns the call's stats."""
+    full = _space(space)
     o = make_opts(stream=stream, device_buffers=True, recheck_every=recheck_every, target_E=target_E,
                   max_rounds=max_rounds, workspace=workspace, evals_per_seed=evals_per_seed,
                   rounds_per_seed=rounds_per_seed, kernel=kernel)
     stats = labs_stats()
-    _check(load().labs_walks(L, ctypes.c_void_p(seeds.data_ptr()), seeds.numel(), walks_per_seed, walk_len,
-                             step_budget, ctypes.c_void_p(best_seq.data_ptr()), ctypes.c_void_p(best_E.data_ptr()),
-                             ctypes.byref(o), ctypes.byref(stats)), "labs_walks")
+    fn = load().labs_walks_full if full else load().labs_walks
+    _check(fn(L, ctypes.c_void_p(seeds.data_ptr()), seeds.numel(), walks_per_seed, walk_len, step_budget,
+              ctypes.c_void_p(best_seq.data_ptr()), ctypes.c_void_p(best_E.data_ptr()), ctypes.byref(o),
+              ctypes.byref(stats)), "labs_walks_full" if full else "labs_walks")
     return stats.as_dict()
 
 
 def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, *, recheck_every: int = 0,
-                   trace_begin: int = 0, trace_count: int = 0, visited_walk: int = -1, kernel: int = 0) -> dict:
-    """One round of walks 0..n_walks-1 with per-walk results (and optional traces / visited keys)."""
-    D = (L + 1) // 2
+                   trace_begin: int = 0, trace_count: int = 0, visited_walk: int = -1, kernel: int = 0,
+                   space: str = "skew") -> dict:
+    """One round of walks 0..n_walks-1 with per-walk results (and optional traces / visited keys);
+    space="full" walks all 2^L sequences (labs_saw_round_full)."""
+    full = _space(space)
+    D = L if full else (L + 1) // 2
     best_E = np.zeros(n_walks, dtype=np.int64)
     best_seq = np.zeros((n_walks, L), dtype=np.int8)
     moves = np.zeros(n_walks, dtype=np.int32)
@@ -344,11 +374,16 @@ def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, 
     vcap = walk_len + 1
     visited = np.zeros((vcap, kout), dtype=np.uint64) if visited_walk >= 0 else None
     vcount = np.zeros(1, dtype=np.int32)
-    _check(load().labs_saw_round(L, seed, round_, n_walks, walk_len, recheck_every, _ptr(best_E), _ptr(best_seq),
-                                 _ptr(moves), _ptr(stuck), _ptr(best_step), _ptr(trace) if trace is not None else None,
-                                 trace_begin, trace_count, visited_walk,
-                                 _ptr(visited) if visited is not None else None, vcap,
-                                 _ptr(vcount) if visited is not None else None, kernel), "labs_saw_round")
+    args = (L, seed, round_, n_walks, walk_len, recheck_every, _ptr(best_E), _ptr(best_seq), _ptr(moves),
+            _ptr(stuck), _ptr(best_step), _ptr(trace) if trace is not None else None, trace_begin, trace_count,
+            visited_walk, _ptr(visited) if visited is not None else None, vcap,
+            _ptr(vcount) if visited is not None else None)
+    if full:
+        if kernel not in (0, 1):
+            raise LabsError(LABS_EINVAL, "labs_saw_round_full")
+        _check(load().labs_saw_round_full(*args), "labs_saw_round_full")
+    else:
+        _check(load().labs_saw_round(*args, kernel), "labs_saw_round")
     out = {"best_E": best_E, "best_seq": best_seq, "moves": moves, "stuck": stuck, "best_step": best_step}
     if trace is not None:
         out["trace"] = trace

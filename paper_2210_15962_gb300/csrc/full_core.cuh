@@ -1,0 +1,305 @@
+// Bit-sliced core of a contiguous self-avoiding walk over the full search
+// space of length-L binary sequences (all 2^L of them, any L): the solver the
+// paper (arXiv 2210.15962) leaves to future work in Section 5, built from the
+// same Eq. 1, Eq. 3 and Algorithm 2.  One CUDA thread owns one walk.
+//
+// Notation (0-based positions p = 0..L-1; bit b(p) = 1 <-> s_p = -1):
+//   flip j (0 <= j < L) negates s_j alone; lags k = 1..L-1 (all parities).
+//   A flip changes C_k by -2 u_k, u_k = s_j (s_{j-k} [k <= j] + s_{j+k} [k <= L-1-j]),
+//   so Delta_j = sum_k ((C_k - 2 u_k)^2 - C_k^2) = 4 sum u_k^2 - 4 sum u_k C_k.
+//   C_k is a sum of L-k terms +-1, so it is odd for L-k odd and even for L-k
+//   even.  The signed-digit planes hold the odd numbers C'_k = C_k + [L-k even]
+//   (e = (C' + 2^T - 1) / 2, as in walk_core.cuh), and the scan subtracts the
+//   offset back: sum u C = sum u C' - sum_{k: L-k even} u_k.
+//   The lag windows of flip j are shifts of the one bit array of the sequence:
+//   x side b(j-k) (k <= j), y side b(j+k) (k <= L-1-j); they advance one
+//   position per flip.
+#pragma once
+#include "walk_core.cuh"
+
+namespace psaw {
+
+constexpr int kFullLMin = 3;
+constexpr int kFullLMax = 256;  // flip index in the low 8 bits of a packed key
+
+// Digit planes per lag-word class W (lags 1..L-1, L <= 32 W + 1):
+// |C'_k| <= L <= 2^T - 1.
+template <int W>
+struct FullPlanesFor {
+  static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
+};
+
+template <int W, int T>
+struct FullState {
+  static constexpr int NS = W + 1;  // words of the sequence (L <= 32 W + 1 bits)
+  uint32_t bits[NS];                // bit p = b(p); also the walk's visited-table key
+  uint32_t ep[T][W];                // digit planes of C'_k, lag k at bit k-1
+  int32_t E;
+};
+
+// lags k with L-k even (C_k even) as a word pattern: bit i = lag i + 1
+LABS_HD uint32_t full_even_lag_mask(int L) { return (L & 1) ? 0x55555555u : 0xAAAAAAAAu; }
+
+// Lag k of the correlations: sh holds the bit array shifted by k - 1 on entry
+// and by k on return; C_k = (L - k) - 2 popc(bits ^ sh) over the L - k pairs.
+template <int W>
+LABS_HD int full_next_correlation(const uint32_t (&bits)[W + 1], uint32_t (&sh)[W + 1], int L, int k) {
+  constexpr int NS = W + 1;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) sh[w] = fshr(sh[w], (w + 1 < NS) ? sh[w + 1] : 0u, 1u);
+  const int pairs = L - k;
+  int dis = 0;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) dis += (int)popc32((bits[w] ^ sh[w]) & low_mask_word(pairs, w));
+  return pairs - 2 * dis;
+}
+
+// P_1 of Eq. 3: L values from the Philox stream (the layout of walk_core.cuh's
+// init_walk with L in place of D), then C, E and the digit planes.
+template <int W, int T>
+LABS_HD void init_full(FullState<W, T> &st, int L, uint64_t seed, uint32_t walk, uint32_t round) {
+  constexpr int NS = W + 1;
+  uint32_t blk[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int w = 0; w < NS; ++w) {
+    if ((w & 3) == 0) {
+      blk[0] = walk;
+      blk[1] = round;
+      blk[2] = (uint32_t)(w >> 2);
+      blk[3] = 0;
+      philox4x32_10(blk, (uint32_t)seed, (uint32_t)(seed >> 32));
+    }
+    st.bits[w] = blk[w & 3] & low_mask_word(L, w);
+  }
+#pragma unroll
+  for (int t = 0; t < T; ++t)
+#pragma unroll
+    for (int w = 0; w < W; ++w) st.ep[t][w] = 0;
+  int32_t E = 0;
+  uint32_t sh[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) sh[w] = st.bits[w];
+  for (int k = 1; k < L; ++k) {
+    const int C = full_next_correlation<W>(st.bits, sh, L, k);
+    E += C * C;
+    const int Cp = C + (((L - k) & 1) ? 0 : 1);
+    const uint32_t e = (uint32_t)((Cp + (1 << T) - 1) >> 1);
+#pragma unroll
+    for (int t = 0; t < T; ++t) xor_bit(st.ep[t], k - 1, (e >> t) & 1u);
+  }
+  st.E = E;
+}
+
+// Debug recheck: C from XOR + popc against the planes, E against Eq. 1.
+template <int W, int T>
+LABS_HD bool recheck_full(const FullState<W, T> &st, int L) {
+  constexpr int NS = W + 1;
+  bool ok = true;
+  int32_t E = 0;
+  uint32_t sh[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) sh[w] = st.bits[w];
+  for (int k = 1; k < L; ++k) {
+    const int C = full_next_correlation<W>(st.bits, sh, L, k);
+    E += C * C;
+    uint32_t e = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) e |= get_bit(st.ep[t], k - 1) << t;
+    const int Cp = C + (((L - k) & 1) ? 0 : 1);
+    ok = ok && ((int)(2 * e) - ((1 << T) - 1) == Cp);
+  }
+  return ok && (E == st.E);
+}
+
+// Smallest TP (T-3 <= TP <= T) whose TP-digit form (planes 0..TP-2 and T-1)
+// holds every C'_k (the rule of walk_core.cuh's planes_needed over L-1 lags).
+template <int W, int T>
+LABS_HD int full_planes_needed(const FullState<W, T> &st, int L) {
+  uint32_t M[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) M[w] = 0xFFFFFFFFu;
+  int tp = T;
+#pragma unroll
+  for (int u = T - 2; u >= T - 4 && u >= 1; --u) {
+    bool all = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      M[w] &= st.ep[u][w] ^ st.ep[T - 1][w];
+      const uint32_t valid = low_mask_word(L - 1, w);
+      all = all && ((M[w] & valid) == valid);
+    }
+    if (!all) break;
+    tp = u + 1;
+  }
+  return tp;
+}
+
+// Valid-lag masks of every flip: row j at j * kRowWords holds Vx[0..W-1]
+// (lags 1..j) then Vy[0..W-1] (lags 1..L-1-j), padded to 16 bytes.
+template <int W>
+struct FullMaskTable {
+  static constexpr int kRowWords = (2 * W + 3) / 4 * 4;
+  static constexpr int kRows = 32 * W + 1;  // >= L
+  static constexpr int kWords = kRows * kRowWords;
+};
+
+template <int W>
+LABS_HD void fill_full_mask_rows(int L, uint32_t *tab, int first, int step) {
+  using MT = FullMaskTable<W>;
+  for (int r = first; r < MT::kRows; r += step) {
+    uint32_t *row = tab + (size_t)r * MT::kRowWords;
+    for (int k = 0; k < MT::kRowWords; ++k) row[k] = 0u;
+    if (r >= L) continue;
+    for (int w = 0; w < W; ++w) {
+      row[w] = low_mask_word(r, w);
+      row[W + w] = low_mask_word(L - 1 - r, w);
+    }
+  }
+}
+
+// One flip: the packed key ((Delta + bias) << 8) | j.  B, F: x / y windows
+// of the flip, ba = b(j).  With the bits XORed by [s_j = -1] (products
+// s_j s_{j-+k}) and the lags split into V1 (one side valid) and V2 (both), as
+// in walk_core.cuh's flip_key: S = sum_t 2^t popc(Z_t), M = |M2| (both sides
+// equal), Qev = sum over even-C lags of the products' sum,
+//   Delta = -8 S + (16 + 8 K1) M + 4 Qev + (4 + 4 K1) n - (8 + 8 K1) n2,
+// n = L-1 valid (lag, side) pairs, n2 = |V2| = min(j, L-1-j), K1 = 2^TP - 1.
+template <int W, int T, int TP>
+LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const uint32_t (&B)[W],
+                               const uint32_t (&F)[W], const uint32_t (&Vx)[W], const uint32_t (&Vy)[W],
+                               uint32_t ba, int j, int L, uint32_t evm) {
+  uint32_t acc = 0, mcnt = 0;
+  int qev = 0;
+  const uint32_t bm = 0u - ba;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    constexpr bool kSkip = W <= kSkipMaxWords;
+    const bool xa = kSkip ? (j > 32 * w) : true;
+    const bool ya = kSkip ? (L - 1 - j > 32 * w) : true;
+    const uint32_t vx = Vx[w];
+    uint32_t v = 0;
+    if (xa && ya) {
+      const uint32_t vy = Vy[w];
+      const uint32_t v1 = vx ^ vy;
+      const uint32_t gb = ((vx & B[w]) | (~vx & F[w])) ^ bm;
+      const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
+      const uint32_t mall = v1 | m2;
+      v = popc32(m2 & (gb ^ st.ep[T - 1][w]));
+#pragma unroll
+      for (int tt = TP - 1; tt >= 1; --tt) {
+        const uint32_t e1 = st.ep[tt < TP - 1 ? tt : T - 1][w];
+        const uint32_t e0 = st.ep[tt - 1][w];
+        const uint32_t et = (v1 & e1) | (~v1 & e0);
+        v = imad(v, mu.two, popc32(mall & (gb ^ et)));
+      }
+      v = imad(v, mu.two, popc32(v1 & (gb ^ st.ep[0][w])));
+      mcnt = imad(popc32(m2), mu.one, mcnt);
+      const uint32_t v1e = v1 & evm, m2e = m2 & evm;
+      qev += (int)popc32(v1e) - 2 * (int)popc32(v1e & gb) + 2 * (int)popc32(m2e) - 4 * (int)popc32(m2e & gb);
+    } else if (xa || ya) {
+      const uint32_t m = xa ? vx : Vy[w];
+      const uint32_t g = (xa ? B[w] : F[w]) ^ bm;
+      v = popc32(m & (g ^ st.ep[T - 1][w]));
+#pragma unroll
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(m & (g ^ st.ep[tt][w])));
+      const uint32_t me = m & evm;
+      qev += (int)popc32(me) - 2 * (int)popc32(me & g);
+    }
+    acc = imad(acc, mu.one, v);
+  }
+  constexpr int K1 = (1 << TP) - 1;
+  const int n = L - 1;
+  const int n2 = j < L - 1 - j ? j : L - 1 - j;
+  const int rest = 4 * qev + (4 + 4 * K1) * n - (8 + 8 * K1) * n2 + kDeltaBias;
+  const uint32_t delta = imad(acc, (uint32_t)-8, imad(mcnt, (uint32_t)(16 + 8 * K1), (uint32_t)rest));
+  return imad(delta, 256u, (uint32_t)j);
+}
+
+// Delta_j of all L flips with TP planes; the K smallest packed keys (>= floor
+// when RESCAN), skipping j == jprev.
+template <int W, int T, int TP, int K, bool RESCAN>
+LABS_HD void full_eval_tp(const FullState<W, T> &st, int L, const Muls &mu, const uint32_t *mt, int jprev,
+                          uint32_t floor, uint32_t (&top)[K]) {
+  using MT = FullMaskTable<W>;
+#pragma unroll
+  for (int r = 0; r < K; ++r) top[r] = kNone;
+  uint32_t F[W], B[W], Vx[W], Vy[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    F[w] = fshr(st.bits[w], st.bits[w + 1], 1u);
+    B[w] = 0;
+  }
+  uint32_t ba = st.bits[0] & 1u;
+  const uint32_t evm = full_even_lag_mask(L);
+  const uint32_t *row = mt;
+  for (int j = 0; j < L; ++j, row += MT::kRowWords) {
+    load_mask_row<W>(row, Vx, Vy);
+    uint32_t x = full_flip_key<W, T, TP>(st, mu, B, F, Vx, Vy, ba, j, L, evm);
+    x = (j == jprev || (RESCAN && x < floor)) ? kNone : x;
+    top_insert(top, x);
+    const uint32_t ba_next = F[0] & 1u;
+#pragma unroll
+    for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
+    B[0] = imad(B[0], mu.two, ba);
+#pragma unroll
+    for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
+    ba = ba_next;
+  }
+}
+
+template <int W, int T, int K>
+LABS_HD void full_eval(const FullState<W, T> &st, int L, const Muls &mu, const uint32_t *mt, int tp, int jprev,
+                       uint32_t floor, uint32_t (&top)[K]) {
+  constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
+  if (floor == 0) {
+    if (tp >= T) full_eval_tp<W, T, T, K, false>(st, L, mu, mt, jprev, 0u, top);
+    else if (tp == T - 1) full_eval_tp<W, T, T - 1, K, false>(st, L, mu, mt, jprev, 0u, top);
+    else if (tp == T - 2) full_eval_tp<W, T, T - 2, K, false>(st, L, mu, mt, jprev, 0u, top);
+    else full_eval_tp<W, T, T3, K, false>(st, L, mu, mt, jprev, 0u, top);
+  } else {
+    full_eval_tp<W, T, T, K, true>(st, L, mu, mt, jprev, floor, top);
+  }
+}
+
+// Move to the neighbour of flip j: C_k -= 2 u_k on the planes (e += -u_k by a
+// bit-sliced add), E += delta, and flip b(j).
+template <int W, int T>
+LABS_HD void apply_full(FullState<W, T> &st, int L, int j, int delta) {
+  constexpr int NS = W + 1;
+  const uint32_t ba = get_bit(st.bits, j);
+  const uint32_t bm = 0u - ba;
+  // Y window: bits j+1 ..; X window: bits j-1, j-2, .. via a full bit reversal
+  uint32_t F[W], R[NS], X[W];
+  shr_dyn(F, st.bits, j + 1);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) R[w] = brev32(st.bits[NS - 1 - w]);
+  shr_dyn(X, R, 32 * NS - j);
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t vx = low_mask_word(j, w);
+    const uint32_t vy = low_mask_word(L - 1 - j, w);
+    const uint32_t Xw = X[w] ^ bm, Yw = F[w] ^ bm;  // product bits (1 <-> s_j s_{j-+k} = -1)
+    // g = -product in {-1, 0, 1} (0 where the side is not valid): bit 0 = valid, sign = valid & ~product
+    const uint32_t x0 = vx, xs = vx & ~Xw;
+    const uint32_t y0 = vy, ys = vy & ~Yw;
+    // d = g_x + g_y = -u in [-2, 2], three-bit two's complement
+    const uint32_t d0 = x0 ^ y0;
+    const uint32_t c1 = x0 & y0;
+    const uint32_t d1 = xs ^ ys ^ c1;
+    const uint32_t c2 = (xs & ys) | (c1 & (xs ^ ys));
+    const uint32_t d2 = xs ^ ys ^ c2;
+    // e += d over T planes (addend planes d0, d1, d2, d2, ...)
+    uint32_t carry = 0;
+#pragma unroll
+    for (int tt = 0; tt < T; ++tt) {
+      const uint32_t add = tt == 0 ? d0 : (tt == 1 ? d1 : d2);
+      const uint32_t e = st.ep[tt][w];
+      st.ep[tt][w] = e ^ add ^ carry;
+      carry = (e & add) | (carry & (e ^ add));
+    }
+  }
+  st.E += delta;
+  xor_bit(st.bits, j, 1u);
+}
+
+}  // namespace psaw

@@ -20,6 +20,12 @@ constexpr uint64_t kRoundBatch = 16;  // rounds enqueued between host checks of 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool valid_L(int32_t L) { return L >= LABS_L_MIN && L <= LABS_L_MAX && (L & 1); }
+bool valid_full_L(int32_t L) { return L >= LABS_FULL_L_MIN && L <= LABS_FULL_L_MAX; }
+bool valid_space_L(int32_t space, int32_t L) { return space == kSpaceFull ? valid_full_L(L) : valid_L(L); }
+
+// flips per step = bits of a key: D free values of a skew sequence, L of any sequence
+int key_bits(int32_t space, int32_t L) { return space == kSpaceFull ? L : (L + 1) / 2; }
+int space_lag_words(int32_t space, int32_t L) { return space == kSpaceFull ? full_lag_words(L) : lag_words(L); }
 
 // visited-table slots: a power of two >= 1.5 x the pivots of a walk
 uint32_t table_cap(int32_t walk_len) {
@@ -137,6 +143,7 @@ struct RunConfig {
   int64_t target;
   int32_t max_rounds;
   int32_t kernel;
+  int32_t space;  // kSpaceSkew or kSpaceFull
 };
 
 // The library's choice of neighbourhood evaluation for labs_opts.kernel == 0.
@@ -220,12 +227,21 @@ done:
   return st;
 }
 
-extern "C" size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {
-  if (!valid_L(L) || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1) return 0;
+static size_t workspace_size(int32_t space, int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {
+  if (!valid_space_L(space, L) || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1) return 0;
   const size_t n_walks = (size_t)n_seeds * (size_t)walks_per_seed;
-  const size_t tb = (size_t)table_cap(walk_len) * key_words64((L + 1) / 2) * 8;
+  const size_t tb = (size_t)table_cap(walk_len) * key_words64(key_bits(space, L)) * 8;
   Buffers b;
   return carve(b, nullptr, L, n_seeds, n_walks, n_walks, tb);
+}
+
+extern "C" size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {
+  return workspace_size(kSpaceSkew, L, n_seeds, walks_per_seed, walk_len);
+}
+
+extern "C" size_t labs_walks_full_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed,
+                                                 int32_t walk_len) {
+  return workspace_size(kSpaceFull, L, n_seeds, walks_per_seed, walk_len);
 }
 
 namespace psaw {
@@ -247,10 +263,9 @@ struct Run {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> walk_ev;
 
   labs_status setup(void *user_ws, size_t user_bytes) {
-    const int D = (cfg.L + 1) / 2;
-    W = lag_words(cfg.L);
+    W = space_lag_words(cfg.space, cfg.L);
     cap = table_cap(cfg.walk_len);
-    kw64 = key_words64(D);
+    kw64 = key_words64(key_bits(cfg.space, cfg.L));
     table_bytes = (size_t)cap * kw64 * 8;
     n_walks = (size_t)cfg.n_seeds * (size_t)cfg.walks;
     const size_t fixed = carve(b, nullptr, cfg.L, cfg.n_seeds, n_walks, 0, table_bytes);
@@ -300,6 +315,7 @@ struct Run {
     p.err = b.err;
     p.plane_steps = b.plane_steps;
     p.variant = resolve_variant(cfg.kernel);
+    p.space = cfg.space;
     set_muls(p);
     return p;
   }
@@ -376,25 +392,27 @@ struct Run {
 }  // namespace
 }  // namespace psaw
 
-extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
-                                  int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
-                                  const labs_opts *opts_in, labs_stats *stats) {
+static labs_status walks_impl(int32_t space, int32_t L, const uint64_t *seeds, int32_t n_seeds,
+                              int32_t walks_per_seed, int32_t walk_len, uint64_t step_budget, int8_t *best_seq,
+                              int64_t *best_E, const labs_opts *opts_in, labs_stats *stats) {
   labs_opts opts;
   if (opts_in) opts = *opts_in;
   else labs_opts_init(&opts);
-  if (!valid_L(L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1 ||
-      walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0 ||
-      opts.kernel < 0 || opts.kernel > 2)
+  // the full search space has the full-scan kernel only
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantIncremental;
+  if (!valid_space_L(space, L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 ||
+      walk_len < 1 || walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0 ||
+      opts.kernel < 0 || opts.kernel > max_kernel)
     return LABS_EINVAL;
   if ((uint64_t)n_seeds * (uint64_t)walks_per_seed > (1ull << 31)) return LABS_EINVAL;
   labs_status st = LABS_OK;
   Run run;
   run.cfg = RunConfig{L, n_seeds, walks_per_seed, walk_len, opts.recheck_every, step_budget, opts.target_E,
-                      opts.max_rounds, opts.kernel};
+                      opts.max_rounds, opts.kernel, space};
   run.s = (cudaStream_t)opts.stream;
   const cudaMemcpyKind in_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind out_kind = opts.device_buffers ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const uint64_t full_round = (uint64_t)walks_per_seed * (uint64_t)walk_len * (uint64_t)((L + 1) / 2);
+  const uint64_t full_round = (uint64_t)walks_per_seed * (uint64_t)walk_len * (uint64_t)key_bits(space, L);
   uint64_t est = (step_budget + full_round - 1) / full_round;
   if (opts.max_rounds > 0) est = std::min<uint64_t>(est, (uint64_t)opts.max_rounds);
   uint32_t round = 0;
@@ -418,7 +436,7 @@ extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_se
     if (round >= est) est = round + 1;
   }
   ++run.launches;
-  LABS_CU(launch_expand(n_seeds, L, run.b.p_key, kKeyWords, run.b.best_seq, run.s));
+  LABS_CU(launch_expand(n_seeds, L, run.b.p_key, kKeyWords, run.b.best_seq, run.s, space == kSpaceFull));
   t1 = run.timer.rec(run.s);
   LABS_CU(cudaMemcpyAsync(best_seq, run.b.best_seq, (size_t)n_seeds * L, out_kind, run.s));
   LABS_CU(cudaMemcpyAsync(best_E, run.b.p_bestE, sizeof(int64_t) * n_seeds, out_kind, run.s));
@@ -456,22 +474,37 @@ done:
   return st;
 }
 
-extern "C" labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
-                                      int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
-                                      int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
-                                      int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
-                                      int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
-                                      int32_t *visited_count, int32_t kernel) {
-  if (!valid_L(L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 || kernel < 0 ||
-      kernel > 2)
+extern "C" labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
+                                  int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
+                                  const labs_opts *opts, labs_stats *stats) {
+  return walks_impl(kSpaceSkew, L, seeds, n_seeds, walks_per_seed, walk_len, step_budget, best_seq, best_E, opts,
+                    stats);
+}
+
+extern "C" labs_status labs_walks_full(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_t walks_per_seed,
+                                       int32_t walk_len, uint64_t step_budget, int8_t *best_seq, int64_t *best_E,
+                                       const labs_opts *opts, labs_stats *stats) {
+  return walks_impl(kSpaceFull, L, seeds, n_seeds, walks_per_seed, walk_len, step_budget, best_seq, best_E, opts,
+                    stats);
+}
+
+static labs_status saw_round_impl(int32_t space, int32_t L, uint64_t seed, uint32_t round, int32_t n_walks,
+                                  int32_t walk_len, int32_t recheck_every, int64_t *walk_best_E,
+                                  int8_t *walk_best_seq, int32_t *walk_moves, int32_t *walk_stuck,
+                                  int32_t *walk_best_step, int32_t *trace_flips, int32_t trace_begin,
+                                  int32_t trace_count, int32_t visited_walk, uint64_t *visited_keys,
+                                  int32_t visited_cap, int32_t *visited_count, int32_t kernel) {
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantIncremental;
+  if (!valid_space_L(space, L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 ||
+      kernel < 0 || kernel > max_kernel)
     return LABS_EINVAL;
   if (trace_flips && (trace_begin < 0 || trace_count < 0 || trace_begin + trace_count > n_walks)) return LABS_EINVAL;
   if (visited_keys && (visited_walk < 0 || visited_walk >= n_walks || visited_cap < 0 || !visited_count))
     return LABS_EINVAL;
-  const int D = (L + 1) / 2;
+  const int D = key_bits(space, L);
   labs_status st = LABS_OK;
   Run run;
-  run.cfg = RunConfig{L, 1, n_walks, walk_len, recheck_every, ~0ull, -1, 1, kernel};
+  run.cfg = RunConfig{L, 1, n_walks, walk_len, recheck_every, ~0ull, -1, 1, kernel, space};
   run.s = 0;
   int32_t *d_trace = nullptr;
   int8_t *d_seqs = nullptr;
@@ -499,7 +532,7 @@ extern "C" labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, 
     LABS_CU(cudaMemcpy(walk_best_step, run.b.w_best_step, sizeof(int32_t) * n_walks, cudaMemcpyDeviceToHost));
   if (walk_best_seq) {
     LABS_CU(cudaMalloc(&d_seqs, (size_t)n_walks * L));
-    LABS_CU(launch_expand(n_walks, L, run.b.w_key, kKeyWords, d_seqs, 0));
+    LABS_CU(launch_expand(n_walks, L, run.b.w_key, kKeyWords, d_seqs, 0, space == kSpaceFull));
     LABS_CU(cudaMemcpy(walk_best_seq, d_seqs, (size_t)n_walks * L, cudaMemcpyDeviceToHost));
   }
   if (trace_n) LABS_CU(cudaMemcpy(trace_flips, d_trace, trace_n * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -534,4 +567,26 @@ done:
     if (e != cudaSuccess) st = cuda_status(e);
   }
   return st;
+}
+
+extern "C" labs_status labs_saw_round(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
+                                      int32_t recheck_every, int64_t *walk_best_E, int8_t *walk_best_seq,
+                                      int32_t *walk_moves, int32_t *walk_stuck, int32_t *walk_best_step,
+                                      int32_t *trace_flips, int32_t trace_begin, int32_t trace_count,
+                                      int32_t visited_walk, uint64_t *visited_keys, int32_t visited_cap,
+                                      int32_t *visited_count, int32_t kernel) {
+  return saw_round_impl(kSpaceSkew, L, seed, round, n_walks, walk_len, recheck_every, walk_best_E, walk_best_seq,
+                        walk_moves, walk_stuck, walk_best_step, trace_flips, trace_begin, trace_count, visited_walk,
+                        visited_keys, visited_cap, visited_count, kernel);
+}
+
+extern "C" labs_status labs_saw_round_full(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks,
+                                           int32_t walk_len, int32_t recheck_every, int64_t *walk_best_E,
+                                           int8_t *walk_best_seq, int32_t *walk_moves, int32_t *walk_stuck,
+                                           int32_t *walk_best_step, int32_t *trace_flips, int32_t trace_begin,
+                                           int32_t trace_count, int32_t visited_walk, uint64_t *visited_keys,
+                                           int32_t visited_cap, int32_t *visited_count) {
+  return saw_round_impl(kSpaceFull, L, seed, round, n_walks, walk_len, recheck_every, walk_best_E, walk_best_seq,
+                        walk_moves, walk_stuck, walk_best_step, trace_flips, trace_begin, trace_count, visited_walk,
+                        visited_keys, visited_cap, visited_count, 0);
 }

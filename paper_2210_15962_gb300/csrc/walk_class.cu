@@ -1,5 +1,6 @@
 // The walk kernels of one lag-word class W (Eq. 4 and Algorithm 2 of arXiv
-// 2210.15962): the full-scan kernel and the incremental variant.  This file is
+// 2210.15962): the full-scan kernel, the incremental variant and the kernel
+// of the full search space (all length-L sequences).  This file is
 // compiled once per class with -DPSAW_W=W (1..8), so that the classes' large,
 // pattern-specialised kernels build in parallel.
 #include "walk_device.cuh"
@@ -127,8 +128,53 @@ static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The full search space (full_core.cuh): same contract as walk_kernel with L
+// flips per step and the whole sequence as key (kKeyWords >= W + 1 words).
+template <int W, int T, int K, int MINB>
+__global__ void __launch_bounds__(kWalkBlock, MINB) full_walk_kernel(const WalkParams p) {
+  constexpr int NS = W + 1;
+  const uint32_t lid = blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
+  const uint32_t gw = p.g_begin + lid;
+  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
+  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
+  const bool live = lid < p.g_count && !(p.done && p.done[prob]);
+  uint64_t *table = p.tables + (size_t)lid * table_words;
+  __shared__ __align__(16) uint32_t mask_rows[FullMaskTable<W>::kWords];
+  fill_full_mask_rows<W>(p.L, mask_rows, threadIdx.x, blockDim.x);
+  __syncthreads();
+  clear_tables_warp(table, table_words, live);
+  if (!live) return;
+
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  int32_t *trace = nullptr;
+  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
+    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
+  WalkOut<NS> o;
+  run_walk_full<W, T, K>(p.L, mu, mask_rows, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64,
+                         p.recheck_every, trace, p.err, o);
+  p.w_bestE[gw] = o.bestE;
+  p.w_moves[gw] = o.moves;
+  p.w_stuck[gw] = o.stuck;
+  p.w_best_step[gw] = o.best_step;
+#pragma unroll
+  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
+  atomicAdd(&p.p_evals[prob], (unsigned long long)p.L * (unsigned long long)(o.moves + o.stuck));
+  if (p.plane_steps) atomicAdd(p.plane_steps, o.planes);
+  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
+}
+
+template <int W>
+static cudaError_t launch_full(const WalkParams &p, cudaStream_t s) {
+  constexpr int T = FullPlanesFor<W>::value;
+  const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
+  full_walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int W>
 cudaError_t launch_walk_class(const WalkParams &p, cudaStream_t s) {
+  if (p.space == kSpaceFull) return launch_full<W>(p, s);
   return p.variant == kVariantIncremental ? launch_w_incr<W>(p, s) : launch_w<W>(p, s);
 }
 

@@ -3,6 +3,7 @@
 // kernel, plus small warp helpers.
 #pragma once
 #include <type_traits>
+#include "full_core.cuh"
 #include "walk_incr.cuh"
 #include "walk_kernels.cuh"
 
@@ -154,6 +155,92 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
 #pragma unroll
     for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
   }
+  out.planes = plane_sum;
+}
+
+// One walk over the full search space (full_core.cuh): the same step loop as
+// run_walk with L flips per step and the whole sequence as key; `mt` is the
+// full-space mask table of L (FullMaskTable<W>).
+template <int W, int T, int K>
+__device__ __forceinline__ void run_walk_full(int L, const Muls &mu, const uint32_t *mt, uint64_t seed, uint32_t walk,
+                                              uint32_t round, int walk_len, uint64_t *table, uint32_t cap, int kw64,
+                                              int recheck_every, int32_t *trace, int32_t *err, WalkOut<W + 1> &out) {
+  constexpr int NS = W + 1;
+  FullState<W, T> st;
+  init_full(st, L, seed, walk, round);
+  {
+    uint32_t slot;
+    table_find(table, cap, kw64, st.bits, L, &slot);
+    table_store(table, slot, kw64, st.bits, L);
+  }
+  int32_t bestE = st.E, best_step = 0, moves = 0, stuck = 0;
+  uint32_t best_key[NS];
+#pragma unroll
+  for (int w = 0; w < NS; ++w) best_key[w] = st.bits[w];
+  int jprev = -1;
+  uint32_t plane_sum = 0;
+  for (int step = 1; step <= walk_len; ++step) {
+    uint32_t floor = 0;
+    int chosen = -1, cdelta = 0;
+    uint32_t cslot = 0;
+    bool need = true;
+    int tp = full_planes_needed(st, L);
+    tp = __reduce_max_sync(__activemask(), (unsigned)tp);  // one plane count per warp (any larger is exact)
+    tp = tp < T - 3 ? T - 3 : tp;
+    plane_sum += (uint32_t)tp;
+    while (need) {
+      uint32_t top[K];
+      full_eval<W, T, K>(st, L, mu, mt, tp, jprev, floor, top);
+#pragma unroll
+      for (int r = 0; r < K; ++r) {
+        if (need) {
+          if (top[r] == kNone) {
+            need = false;  // every neighbour not below `floor` is visited: stuck
+          } else {
+            const int a = key_flip(top[r]);
+            uint32_t nk[NS];
+#pragma unroll
+            for (int w = 0; w < NS; ++w) nk[w] = st.bits[w];
+            xor_bit(nk, a, 1u);
+            uint32_t s;
+            if (!table_find(table, cap, kw64, nk, L, &s)) {
+              need = false;
+              if (s == kNone) {
+                atomicOr(err, kErrOverflow);
+              } else {
+                chosen = a;
+                cdelta = key_delta(top[r]);
+                cslot = s;
+              }
+            }
+          }
+        }
+      }
+      if (need) floor = top[K - 1] + 1u;
+    }
+    if (chosen < 0) {
+      stuck = 1;
+      break;
+    }
+    apply_full(st, L, chosen, cdelta);
+    table_store(table, cslot, kw64, st.bits, L);
+    jprev = chosen;
+    moves = step;
+    if (trace) trace[step - 1] = chosen;
+    if (st.E < bestE) {
+      bestE = st.E;
+      best_step = step;
+#pragma unroll
+      for (int w = 0; w < NS; ++w) best_key[w] = st.bits[w];
+    }
+    if (recheck_every > 0 && (step % recheck_every) == 0 && !recheck_full(st, L)) atomicOr(err, kErrRecheck);
+  }
+  out.bestE = bestE;
+  out.best_step = best_step;
+  out.moves = moves;
+  out.stuck = stuck;
+#pragma unroll
+  for (int w = 0; w < NS; ++w) out.best_key[w] = best_key[w];
   out.planes = plane_sum;
 }
 

@@ -76,7 +76,7 @@ cudaError_t launch_init_problems(int n, int64_t *p_bestE, unsigned long long *p_
 }
 
 // Eq. 2: sequence s_0..s_{L-1} (+1/-1) from the D key bits (bit 1 <-> -1).
-__global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out) {
+__global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, int full) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * (size_t)L) return;
   const int p = (int)(idx / (size_t)L);
@@ -84,7 +84,7 @@ __global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_str
   const int c = (L - 1) / 2;
   const uint32_t *k = keys + (size_t)p * key_stride;
   uint32_t b;
-  if (a <= c) {
+  if (full || a <= c) {
     b = (k[a >> 5] >> (a & 31)) & 1u;
   } else {
     const int i = a - c, src = c - i;
@@ -93,10 +93,11 @@ __global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_str
   seq_out[(size_t)p * L + a] = b ? (int8_t)-1 : (int8_t)1;
 }
 
-cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s) {
+cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s,
+                          int full) {
   if (n <= 0) return cudaSuccess;
   const size_t total = (size_t)n * (size_t)L;
-  expand_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, keys, key_stride, seq_out);
+  expand_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, L, keys, key_stride, seq_out, full);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,10 @@ enum ErrorBits : int32_t {
   kErrOverflow = 2,  // a visited table ran out of slots
 };
 
+// search spaces: the skew-symmetric sequences of odd L, or all sequences
+constexpr int32_t kSpaceSkew = 0;
+constexpr int32_t kSpaceFull = 1;
+
 // One launch = walks [g_begin, g_begin + g_count) of one round of one or more
 // problems of the same L; global walk id gw = problem * walks_per_problem + walk.
 struct WalkParams {
@@ -56,6 +60,7 @@ struct WalkParams {
   // sum over walk steps of the digit planes used (for the work accounting)
   unsigned long long *plane_steps;
   int32_t variant;  // kVariantFullScan or kVariantIncremental
+  int32_t space;    // kSpaceSkew or kSpaceFull
 };
 
 inline void set_muls(WalkParams &p) {
@@ -101,9 +106,14 @@ cudaError_t launch_finalize(const FinalizeParams &f, cudaStream_t s);
 cudaError_t launch_init_problems(int n, int64_t *p_bestE, unsigned long long *p_evals,
                                  unsigned long long *p_round_best, int32_t *done, int32_t *p_rounds,
                                  int32_t *p_best_round, int32_t *p_best_walk, uint32_t *p_key, cudaStream_t s);
-cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s);
+// keys -> +-1 sequences: a skew key holds the D free values (Eq. 2 gives the
+// rest), a full-space key the whole sequence (full = 1)
+cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride, int8_t *seq_out, cudaStream_t s,
+                          int full = 0);
 cudaError_t launch_energy(const int8_t *seqs, int n, int L, int64_t *E_out, int32_t *err, cudaStream_t s);
 
 inline int lag_words(int L) { return ((L - 1) / 2 + 31) / 32; }
+// 32-bit words of the L - 1 lags of the full search space
+inline int full_lag_words(int L) { return (L - 1 + 31) / 32; }
 
 }  // namespace psaw

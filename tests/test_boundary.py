@@ -184,3 +184,24 @@ def test_serve_rejects_bad_config(lib):
     assert lib.labs_serve_submit(None, None, None) == m.LABS_EINVAL
     assert lib.labs_serve_poll(None, 1, None, None) == m.LABS_EINVAL
     assert lib.labs_serve_destroy(None) == m.LABS_EINVAL
+
+
+def test_full_space_rejects_bad_args(lib):
+    import paper_2210_15962_gb300 as m
+    seeds = np.array([1], dtype=np.uint64)
+    seq = np.zeros(300, dtype=np.int8)
+    E = np.zeros(1, dtype=np.int64)
+    p = m._ptr
+    for L in [2, 1, 0, 257, 511]:
+        assert lib.labs_walks_full(L, p(seeds), 1, 4, 8, 100, p(seq), p(E), None, None) == m.LABS_EINVAL
+        assert lib.labs_walks_full_workspace_size(L, 1, 4, 8) == 0
+    o = m.labs_opts()
+    lib.labs_opts_init(ctypes.byref(o))
+    o.kernel = 2  # the incremental variant is skew-only
+    assert lib.labs_walks_full(64, p(seeds), 1, 4, 8, 100, p(seq), p(E), ctypes.byref(o), None) == m.LABS_EINVAL
+    assert lib.labs_saw_round_full(257, 1, 0, 4, 8, 0, None, None, None, None, None, None, 0, 0, -1, None, 0,
+                                   None) == m.LABS_EINVAL
+    # even lengths are fine in the full space and sized like any other
+    assert lib.labs_walks_full_workspace_size(64, 1, 4, 8) > 0
+    assert lib.labs_walks_workspace_size(64, 1, 4, 8) == 0
+
