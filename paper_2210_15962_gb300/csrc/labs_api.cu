@@ -1,6 +1,6 @@
 // Host side of the C ABI declared in include/labs.h: argument checks,
 // workspace layout, the round loop of Algorithm 1 and result copies.  All
-// arithmetic of the method runs in the kernels of walk_kernels.cu.
+// arithmetic of the method runs in the kernels of walk_class.cu and walk_kernels.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
