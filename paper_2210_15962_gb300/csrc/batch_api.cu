@@ -290,7 +290,8 @@ labs_status plan_launch(labs_batch *b, const std::vector<int32_t> &next_round, c
         for (uint32_t ch = 0; ch < chunks; ++ch)
           tk.push_back({cost, BatchTask{(uint32_t)i, slot_round[first[i] + k], ch, first[i] + k}});
     }
-    std::stable_sort(tk.begin(), tk.end(), [](const std::pair<double, BatchTask> &x, const std::pair<double, BatchTask> &y) {
+    using Costed = std::pair<double, BatchTask>;
+    std::stable_sort(tk.begin(), tk.end(), [](const Costed &x, const Costed &y) {
       if (x.first != y.first) return x.first > y.first;
       return std::tie(x.second.round, x.second.problem, x.second.chunk) <
              std::tie(y.second.round, y.second.problem, y.second.chunk);

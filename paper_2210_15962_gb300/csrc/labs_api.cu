@@ -357,8 +357,9 @@ struct Run {
     std::vector<uint64_t> bud(cfg.n_seeds, cfg.budget);
     std::vector<int64_t> tgt(cfg.n_seeds, cfg.target);
     cudaError_t e = cudaMemcpyAsync(b.seeds, seeds_src, sizeof(uint64_t) * cfg.n_seeds, kind, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b.budget, bud.data(), sizeof(uint64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b.target, tgt.data(), sizeof(int64_t) * cfg.n_seeds, cudaMemcpyHostToDevice, s);
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.budget, bud.data(), sizeof(uint64_t) * cfg.n_seeds, h2d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.target, tgt.data(), sizeof(int64_t) * cfg.n_seeds, h2d, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.plane_steps, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) {

@@ -205,7 +205,8 @@ labs_status labs_server::step(std::vector<int> &active) {
   for (size_t ci = 0; ci < pools.size(); ++ci) {
     ClassPool &c = pools[ci];
     auto &v = tk[ci];
-    std::stable_sort(v.begin(), v.end(), [](const std::pair<double, BatchTask> &x, const std::pair<double, BatchTask> &y) {
+    using Costed = std::pair<double, BatchTask>;
+    std::stable_sort(v.begin(), v.end(), [](const Costed &x, const Costed &y) {
       return x.first > y.first;
     });
     c.n_tasks = (uint32_t)v.size();
@@ -294,7 +295,8 @@ labs_status labs_server::step(std::vector<int> &active) {
   if (cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(rounds.data(), d_rounds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(bestE.data(), d_bestE, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(evals.data(), d_evals, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(evals.data(), d_evals, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
       cudaMemcpyAsync(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return LABS_ECUDA;

@@ -44,7 +44,7 @@ MIX = [
     (121, 128, 300, 5, 128 * 300 * 61 * 2),            # W=2
     (131, 33, 150, 6, 33 * 150 * 66 * 3),              # W=3
     (199, 40, 120, 7, 1, -1),                          # W=4
-    (223, 64, 100, 8, 10 ** 12, 4600),                 # W=4 with a target (reached in round 0; later rounds speculative)
+    (223, 64, 100, 8, 10 ** 12, 4600),                 # W=4, target reached in round 0 (later rounds speculative)
     (301, 32, 80, 9, 32 * 80 * 151 * 2),               # W=5
 ]
 
