@@ -226,7 +226,7 @@ typedef struct labs_serve_cfg {
   int32_t max_L;             /* largest L accepted (sizes the table pools), default 301 */
   int32_t max_walks;         /* largest walks per round accepted, default 2048 */
   int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
-  int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 4 */
+  int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 8 */
   int32_t block_threads;     /* walks per CTA of the batch kernels, default 128 */
 } labs_serve_cfg;
 
@@ -258,7 +258,7 @@ typedef struct labs_serve_stats {
 typedef struct labs_server labs_server; /* opaque */
 
 /* Defaults: mem_bytes 8 GiB, max_active 64, max_L 301, max_walks 2048,
- * max_walk_len 8 * (max_L + 1) / 2, rounds_per_launch 4, block_threads 128. */
+ * max_walk_len 8 * (max_L + 1) / 2, rounds_per_launch 8, block_threads 128. */
 void labs_serve_cfg_init(labs_serve_cfg *cfg);
 /* Allocate the server (visited-table pools for every lag-word class up to
  * max_L) and start its scheduler thread on the current device. */

@@ -451,7 +451,7 @@ extern "C" void labs_serve_cfg_init(labs_serve_cfg *c) {
   c->max_L = 301;
   c->max_walks = 2048;
   c->max_walk_len = 0;
-  c->rounds_per_launch = 4;
+  c->rounds_per_launch = 8;  // measured: 8 beat 1, 2, 4 and 16 on throughput and median latency
   c->block_threads = 128;
 }
 
