@@ -11,6 +11,9 @@
 
 namespace psaw {
 
+// Longest L of the four-word class that runs with 3 resident blocks per SM.
+constexpr int kW4FewerBlocksMaxL = 233;
+
 // Widest lag-word class whose scan runs through loops specialised for the
 // pattern of active word sides.  Wider classes measured 1.3-2.4x slower with
 // specialised runs (by both sides' word counts, or by the non-empty words
@@ -124,6 +127,15 @@ template <int W>
 static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
   constexpr int T = PlanesFor<W>::value;
   const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
+  if constexpr (W == 4) {
+    // four-word classes: the shorter lengths run faster with 3 blocks per SM
+    // (170 registers), the longer with 4 (measured over two full waves each:
+    // L=199 +7%, 223 +5% with 3; L=245 +2%, 257 +14% with 4)
+    if (p.L <= kW4FewerBlocksMaxL) {
+      walk_kernel<W, T, kTopK, 3><<<blocks, kWalkBlock, 0, s>>>(p);
+      return cudaGetLastError();
+    }
+  }
   walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
