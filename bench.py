@@ -503,6 +503,65 @@ def run_table1(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_walklen(args, world, rank, local):
+    """The walk-length rule (the paper's n = 8 D against D .. 32 D) as time to a
+    target energy: L (--L, default 121), --walks walks per round, target = the
+    best E of a calibration solve (walk length 8 D, seed 99, --walklen-cal-budget
+    evaluations); for each walk length, --walklen-seeds solves (seeds 1..) with
+    that target, each capped at about --walklen-seconds of rounds; the median
+    time to target per length."""
+    import numpy as np
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    L, walks = args.L, args.walks
+    D = (L + 1) // 2
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    cal, t_cal = timed(lambda: pkg.labs_walks(L, [99], walks, 8 * D, args.walklen_cal_budget, stream=stream))
+    target = int(cal["best_E"][0])
+    speed = int(cal["evals"][0]) / t_cal
+    sampler = ClockSampler(local)
+    sampler.start()
+    rows = {}
+    for mult in (1, 2, 4, 8, 16, 32):
+        wl = mult * D
+        per_round = walks * wl * D
+        max_rounds = max(1, int(args.walklen_seconds * speed / per_round))
+        times, reached, evals = [], 0, []
+        for sd in range(1, args.walklen_seeds + 1):
+            r, t = timed(lambda: pkg.labs_walks(L, [sd], walks, wl, 1 << 62, target_E=target, max_rounds=max_rounds,
+                                                stream=stream))
+            ok = int(r["best_E"][0]) <= target
+            reached += ok
+            times.append(t if ok else float("inf"))
+            evals.append(int(r["evals"][0]))
+        rows["%dD" % mult] = {"walk_len": wl, "median_s": float(np.median(times)), "reached": reached,
+                              "times_s": [None if x == float("inf") else x for x in times],
+                              "median_evals": float(np.median(evals))}
+    clocks = sampler.stop()
+    best = min(rows, key=lambda k: rows[k]["median_s"])
+    line = {
+        "metric": "time_to_target_s", "value": rows["8D"]["median_s"], "unit": "s", "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic (Philox starts, seeds 1..%d)" % args.walklen_seeds,
+        "config": {"workload": "walklen_L%d_%dwalks" % (L, walks), "L": L, "walks": walks, "target_E": target,
+                   "calibration": {"walk_len": 8 * D, "seed": 99, "budget": args.walklen_cal_budget,
+                                   "evals_per_s": speed}},
+        "by_walk_length": rows, "fastest": best, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -516,7 +575,11 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "large", "table1"])
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batched", "serving", "large", "table1", "walklen"])
+    ap.add_argument("--walklen-cal-budget", type=int, default=10 ** 12)
+    ap.add_argument("--walklen-seeds", type=int, default=4)
+    ap.add_argument("--walklen-seconds", type=float, default=20.0)
     ap.add_argument("--table1-L", type=int, default=171)
     ap.add_argument("--table1-walks", type=int, default=233472)  # 3 full waves of the 3-word kernel
     ap.add_argument("--table1-seconds", type=float, default=300.0)
@@ -551,6 +614,9 @@ def main():
         return
     if args.workload == "table1" and args.impl != "reference":
         run_table1(args, world, rank, local)
+        return
+    if args.workload == "walklen" and args.impl != "reference":
+        run_walklen(args, world, rank, local)
         return
 
     if args.impl == "reference":
