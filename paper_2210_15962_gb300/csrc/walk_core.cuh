@@ -383,6 +383,25 @@ LABS_HD uint32_t imadhi(uint32_t a, uint32_t b, uint32_t c) {
 #endif
 }
 
+// Three-input bit function by its lookup table (the PTX lop3 encoding: LUT =
+// f(0xF0, 0xCC, 0xAA) for f of (a, b, c)), one LOP3 on the device.
+template <uint32_t LUT>
+LABS_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+#else
+  uint32_t r = 0;
+  for (int i = 0; i < 8; ++i)
+    if ((LUT >> i) & 1u) r |= ((i & 4) ? a : ~a) & ((i & 2) ? b : ~b) & ((i & 1) ? c : ~c);
+  return r;
+#endif
+}
+constexpr uint32_t kLutAndXor = 0x60;     // a & (b ^ c)
+constexpr uint32_t kLutSelect = 0xCA;     // a ? b : c, bitwise
+constexpr uint32_t kLutAndXnor = 0x90;    // a & ~(b ^ c)
+
 // Smallest number of digit planes TP (T-3 <= TP <= T) that represents every
 // current C_{2i}: |C| <= 2^TP - 1 holds iff the digit bits TP-1 .. T-2 of
 // every e_i differ from its top bit T-1.  The TP-digit form of C then uses
@@ -464,25 +483,25 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     if (xa && ya) {
       const uint32_t vy = Vye[w];
       const uint32_t v1 = vx ^ vy;
-      const uint32_t gb = ((vx & B[w]) | (~vx & F[w])) ^ bm;
-      const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
+      const uint32_t gb = lop3<kLutSelect>(vx, B[w], F[w]) ^ bm;
+      const uint32_t m2 = lop3<kLutAndXnor>(vx & vy, B[w], F[w]);
       const uint32_t mall = v1 | m2;
-      v = popc32(m2 & (gb ^ st.ep[T - 1][w]));
+      v = popc32(lop3<kLutAndXor>(m2, gb, st.ep[T - 1][w]));
 #pragma unroll
       for (int tt = TP - 1; tt >= 1; --tt) {
         const uint32_t e1 = st.ep[tt < TP - 1 ? tt : T - 1][w];
         const uint32_t e0 = st.ep[tt - 1][w];
-        const uint32_t et = (v1 & e1) | (~v1 & e0);
-        v = imad(v, mu.two, popc32(mall & (gb ^ et)));
+        const uint32_t et = lop3<kLutSelect>(v1, e1, e0);
+        v = imad(v, mu.two, popc32(lop3<kLutAndXor>(mall, gb, et)));
       }
-      v = imad(v, mu.two, popc32(v1 & (gb ^ st.ep[0][w])));
+      v = imad(v, mu.two, popc32(lop3<kLutAndXor>(v1, gb, st.ep[0][w])));
       mcnt = imad(popc32(m2), mu.one, mcnt);
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : Vye[w];
       const uint32_t g = (xa ? B[w] : F[w]) ^ bm;
-      v = popc32(m & (g ^ st.ep[T - 1][w]));
+      v = popc32(lop3<kLutAndXor>(m, g, st.ep[T - 1][w]));
 #pragma unroll
-      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(m & (g ^ st.ep[tt][w])));
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(lop3<kLutAndXor>(m, g, st.ep[tt][w])));
     }
     acc = imad(acc, mu.one, v);
   }
