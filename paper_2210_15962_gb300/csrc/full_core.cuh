@@ -181,29 +181,29 @@ LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const 
     if (xa && ya) {
       const uint32_t vy = Vy[w];
       const uint32_t v1 = vx ^ vy;
-      const uint32_t gb = ((vx & B[w]) | (~vx & F[w])) ^ bm;
-      const uint32_t m2 = vx & vy & ~(B[w] ^ F[w]);
+      const uint32_t gb = lop3<kLutSelect>(vx, B[w], F[w]) ^ bm;
+      const uint32_t m2 = lop3<kLutAndXnor>(vx & vy, B[w], F[w]);
       const uint32_t mall = v1 | m2;
-      v = popc32(m2 & (gb ^ st.ep[T - 1][w]));
+      v = popc32(lop3<kLutAndXor>(m2, gb, st.ep[T - 1][w]));
 #pragma unroll
       for (int tt = TP - 1; tt >= 1; --tt) {
         const uint32_t e1 = st.ep[tt < TP - 1 ? tt : T - 1][w];
         const uint32_t e0 = st.ep[tt - 1][w];
-        const uint32_t et = (v1 & e1) | (~v1 & e0);
-        v = imad(v, mu.two, popc32(mall & (gb ^ et)));
+        const uint32_t et = lop3<kLutSelect>(v1, e1, e0);
+        v = imad(v, mu.two, popc32(lop3<kLutAndXor>(mall, gb, et)));
       }
-      v = imad(v, mu.two, popc32(v1 & (gb ^ st.ep[0][w])));
+      v = imad(v, mu.two, popc32(lop3<kLutAndXor>(v1, gb, st.ep[0][w])));
       mcnt = imad(popc32(m2), mu.one, mcnt);
       const uint32_t v1e = v1 & evm, m2e = m2 & evm;
-      qev += (int)popc32(v1e) - 2 * (int)popc32(v1e & gb) + 2 * (int)popc32(m2e) - 4 * (int)popc32(m2e & gb);
+      qev += (int)popc32(v1e) - 2 * (int)popc32(lop3<kLutAnd3>(v1, evm, gb)) + 2 * (int)popc32(m2e) -
+             4 * (int)popc32(lop3<kLutAnd3>(m2, evm, gb));
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : Vy[w];
       const uint32_t g = (xa ? B[w] : F[w]) ^ bm;
-      v = popc32(m & (g ^ st.ep[T - 1][w]));
+      v = popc32(lop3<kLutAndXor>(m, g, st.ep[T - 1][w]));
 #pragma unroll
-      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(m & (g ^ st.ep[tt][w])));
-      const uint32_t me = m & evm;
-      qev += (int)popc32(me) - 2 * (int)popc32(me & g);
+      for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(lop3<kLutAndXor>(m, g, st.ep[tt][w])));
+      qev += (int)popc32(m & evm) - 2 * (int)popc32(lop3<kLutAnd3>(m, evm, g));
     }
     acc = imad(acc, mu.one, v);
   }
@@ -294,8 +294,8 @@ LABS_HD void apply_full(FullState<W, T> &st, int L, int j, int delta) {
     for (int tt = 0; tt < T; ++tt) {
       const uint32_t add = tt == 0 ? d0 : (tt == 1 ? d1 : d2);
       const uint32_t e = st.ep[tt][w];
-      st.ep[tt][w] = e ^ add ^ carry;
-      carry = (e & add) | (carry & (e ^ add));
+      st.ep[tt][w] = lop3<kLutXor3>(e, add, carry);
+      carry = lop3<kLutMajority>(e, add, carry);
     }
   }
   st.E += delta;

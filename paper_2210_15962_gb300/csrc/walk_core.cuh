@@ -401,6 +401,9 @@ LABS_HD uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
 constexpr uint32_t kLutAndXor = 0x60;     // a & (b ^ c)
 constexpr uint32_t kLutSelect = 0xCA;     // a ? b : c, bitwise
 constexpr uint32_t kLutAndXnor = 0x90;    // a & ~(b ^ c)
+constexpr uint32_t kLutXor3 = 0x96;       // a ^ b ^ c
+constexpr uint32_t kLutMajority = 0xE8;   // at least two of a, b, c
+constexpr uint32_t kLutAnd3 = 0x80;       // a & b & c
 
 // Smallest number of digit planes TP (T-3 <= TP <= T) that represents every
 // current C_{2i}: |C| <= 2^TP - 1 holds iff the digit bits TP-1 .. T-2 of
@@ -702,8 +705,8 @@ LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta
     for (int tt = 1; tt < T; ++tt) {
       const uint32_t add = tt == 1 ? d0 : (tt == 2 ? d1 : d2);
       const uint32_t e = st.ep[tt][w];
-      st.ep[tt][w] = e ^ add ^ carry;
-      carry = (e & add) | (carry & (e ^ add));
+      st.ep[tt][w] = lop3<kLutXor3>(e, add, carry);
+      carry = lop3<kLutMajority>(e, add, carry);
     }
   }
   st.E += delta;
