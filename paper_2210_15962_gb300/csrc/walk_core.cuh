@@ -461,13 +461,41 @@ struct FoldSign {
   static constexpr bool value = W <= 3 || W == 5;
 };
 
+// Words of a class that can hold x lags: a scanned flip has t <= (D-1)/2 = m/2
+// <= 16 W, so its x lags i <= t lie in the first ceil(W/2) words.
+template <int W>
+constexpr int x_words() {
+  return (W + 1) / 2;
+}
+
+// The part of a flip's key that the bit counts do not enter.  The key is
+// 256 (Delta + bias) + a; with Delta as below and n = |Vx| + |Vye|,
+// nxy = |Vx & Vye| it is
+//   key = -4096 S + 4096 (K1 + 4) M + kbase                          (s_a folded into the bits)
+//   key = 256 sig S + 256 mul M + kbase + [s_a = -1] kdiff           (coefficients selected by s_a)
+//   kbase = 256 (bias + (16 + 8 K1) n - (32 + 16 K1) nxy) + a,  kdiff = 256 (32 K1 nxy - 16 K1 n),
+// all modulo 2^32 like the key.  Along a run of flips n is fixed and a, nxy
+// grow by 2 and 1 per flip (while the pair lag stays on one side of t), so
+// both advance by a constant step.
+template <int TP>
+LABS_HD uint32_t key_base(int a, int n, int nxy) {
+  constexpr uint32_t K1 = (1u << TP) - 1u;
+  return 256u * ((uint32_t)kDeltaBias + (16u + 8u * K1) * (uint32_t)n - (32u + 16u * K1) * (uint32_t)nxy) +
+         (uint32_t)a;
+}
+template <int TP>
+LABS_HD uint32_t key_diff(int n, int nxy) {
+  constexpr uint32_t K1 = (1u << TP) - 1u;
+  return 256u * (32u * K1 * (uint32_t)nxy - 16u * K1 * (uint32_t)n);
+}
+
 // NX, NY >= 0 fix at compile time how many leading words have valid x / y
 // lags (the caller guarantees NX = ceil(t/32), NY = ceil((Nq-1-t)/32));
-// -1 decides per flip.
+// -1 decides per flip.  kbase, kdiff: the flip's key_base / key_diff.
 template <int W, int T, int TP, bool CENTRE, int NX = -1, int NY = -1>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
-                          const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, int a, int n, int nxy, int t,
-                          int Nq) {
+                          const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, uint32_t kbase,
+                          uint32_t kdiff, int t, int Nq) {
   constexpr bool kFold = FoldSign<W>::value;
   uint32_t acc = 0, mcnt = 0;
   const uint32_t bm = kFold ? 0u - ba : 0u;  // all ones where s_a = -1 (folded form)
@@ -478,7 +506,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     // two-sided path: with few resident warps they rely on the compiler
     // interleaving the words' independent chains.
     constexpr bool kSkip = W <= kSkipMaxWords;
-    const bool xa = NX >= 0 ? (w < NX) : (kSkip ? (t > 32 * w) : true);
+    const bool xa = w < x_words<W>() && (NX >= 0 ? (w < NX) : (kSkip ? (t > 32 * w) : true));
     const bool ya = CENTRE ? false : (NY >= 0 ? (w < NY) : (kSkip ? (Nq - 1 - t > 32 * w) : true));
     const uint32_t vx = Vx[w];
     uint32_t v = 0;
@@ -508,48 +536,52 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     }
     acc = imad(acc, mu.one, v);
   }
-  constexpr int K1 = (1 << TP) - 1;
+  constexpr uint32_t K1 = (1u << TP) - 1u;
   if constexpr (kFold) {
-    const uint32_t kap = (uint32_t)((16 + 8 * K1) * n - (32 + 16 * K1) * nxy + kDeltaBias);
-    const uint32_t delta = imad(acc, (uint32_t)-16, imad(mcnt, (uint32_t)(16 * (K1 + 4)), kap));
-    return imad(delta, 256u, (uint32_t)a);
+    return imad(acc, (uint32_t)-4096, imad(mcnt, 4096u * (K1 + 4u), kbase));
   } else {
     // bits not folded: S and M are taken over the window bits themselves, and
     //   s_a = +1: Delta = -16 S + 16 (K1 + 4) M + 8 K1 n + 16 n + 32 nxy - 16 (K1 + 4) nxy
     //   s_a = -1: Delta = +16 S - 16 (K1 - 4) M - 8 K1 n + 16 n - 32 nxy + 16 K1 nxy
-    const int kap0 = 8 * K1 * n + 16 * n + 32 * nxy - 16 * (K1 + 4) * nxy + kDeltaBias;
-    const int kap1 = -8 * K1 * n + 16 * n - 32 * nxy + 16 * K1 * nxy + kDeltaBias;
-    const uint32_t sig = imad(ba, 32u, (uint32_t)-16);
-    const uint32_t mul = imad(ba, (uint32_t)(-32 * K1), (uint32_t)(16 * (K1 + 4)));
-    const uint32_t kap = imad(ba, (uint32_t)(kap1 - kap0), (uint32_t)kap0);
-    const uint32_t delta = imad(acc, sig, imad(mcnt, mul, kap));
-    return imad(delta, 256u, (uint32_t)a);
+    // (the s_a = +1 constant is kbase's, the difference kdiff's)
+    const uint32_t sig = imad(ba, 8192u, (uint32_t)-4096);
+    const uint32_t mul = imad(ba, 0u - 8192u * K1, 4096u * (K1 + 4u));
+    const uint32_t kap = imad(ba, kdiff, kbase);
+    return imad(acc, sig, imad(mcnt, mul, kap));
   }
 }
 
-// Flips t0 .. t1-1 of class q (none of them the centre): packed keys into
-// top, windows B, F and the bit ba of position a advanced one lag per flip.
+// Flips t0 .. t1-1 of class q (none of them the centre, and the pair lag
+// c - a on one side of t throughout: t >= tpair for all of them or for none):
+// packed keys into top, skipping t == tprev; windows B, F and the bit ba of
+// position a advanced one lag per flip.
 template <int W, int T, int TP, int K, bool RESCAN, int NX, int NY>
 LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
-                        int t0, int t1, int jprev, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W], uint32_t &ba,
-                        uint32_t (&top)[K]) {
+                        int t0, int t1, int tprev, int tpair, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W],
+                        uint32_t &ba, uint32_t (&top)[K]) {
   using MT = MaskTable<W>;
+  constexpr uint32_t K1 = (1u << TP) - 1u;
   const int Nq = g.D - q;  // N_q without indexing g.N
   const int n = Nq - 2;    // |Vx| + |Vye| for every non-centre flip
+  // |Vx & Vye| = min(t, Nq-1-t) = t in the scan (t <= (Nq-1)/2), less the
+  // pair lag c - a if it is <= t, i.e. if t >= tpair
+  const int nxy0 = t0 - (t0 >= tpair ? 1 : 0);
+  uint32_t kbase = key_base<TP>(2 * t0 + q, n, nxy0);
+  uint32_t kdiff = key_diff<TP>(n, nxy0);
   const uint32_t *row = rows + (size_t)t0 * MT::kRowWords;
   for (int t = t0; t < t1; ++t, row += MT::kRowWords) {
-    const int a = 2 * t + q;
-    // |Vx & Vye|: min(t, Nq-1-t) = t in the scan (t <= (Nq-1)/2), less the pair lag c - a if it is <= t
-    const int nxy = t - ((g.c - a) <= t ? 1 : 0);
     uint32_t Vx[W], Vye[W];
     load_mask_row<W>(row, Vx, Vye);
-    uint32_t x = flip_key<W, T, TP, false, NX, NY>(st, mu, B, F, Vx, Vye, ba, a, n, nxy, t, Nq);
-    x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
+    uint32_t x = flip_key<W, T, TP, false, NX, NY>(st, mu, B, F, Vx, Vye, ba, kbase, kdiff, t, Nq);
+    x = (t == tprev || (RESCAN && x < floor)) ? kNone : x;
     top_insert(top, x);
-    // advance the windows by one lag (shifts as IMAD on the FMA pipe)
+    kbase += 2u - 256u * (32u + 16u * K1);  // a += 2, nxy += 1
+    kdiff += 256u * 32u * K1;
+    // advance the windows by one lag (shifts as IMAD on the FMA pipe); the x
+    // window only over the words that can hold x lags
     const uint32_t ba_next = F[0] & 1u;
 #pragma unroll
-    for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
+    for (int w = x_words<W>() - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
     B[0] = imad(B[0], mu.two, ba);
 #pragma unroll
     for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
@@ -569,18 +601,19 @@ constexpr int kPatternMinWords = 2;
 // pattern decides per flip.
 template <int W, int T, int TP, int K, bool RESCAN, int NX = 0, int NY = (W / 2 > 1 ? W / 2 : 1)>
 LABS_HD void scan_run(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
-                      int nx, int ny, int t0, int t1, int jprev, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W],
-                      uint32_t &ba, uint32_t (&top)[K]) {
+                      int nx, int ny, int t0, int t1, int tprev, int tpair, uint32_t floor, uint32_t (&B)[W],
+                      uint32_t (&F)[W], uint32_t &ba, uint32_t (&top)[K]) {
   if constexpr (NX > (W + 1) / 2) {
-    scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t0, t1, jprev, floor, B, F, ba, top);
+    scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
   } else if constexpr (NY > W) {
-    scan_run<W, T, TP, K, RESCAN, NX + 1, (W / 2 > 1 ? W / 2 : 1)>(st, g, mu, rows, q, nx, ny, t0, t1, jprev, floor,
-                                                                   B, F, ba, top);
+    scan_run<W, T, TP, K, RESCAN, NX + 1, (W / 2 > 1 ? W / 2 : 1)>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair,
+                                                                   floor, B, F, ba, top);
   } else {
     if (nx == NX && ny == NY)
-      scan_flips<W, T, TP, K, RESCAN, NX, NY>(st, g, mu, rows, q, t0, t1, jprev, floor, B, F, ba, top);
+      scan_flips<W, T, TP, K, RESCAN, NX, NY>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
     else
-      scan_run<W, T, TP, K, RESCAN, NX, NY + 1>(st, g, mu, rows, q, nx, ny, t0, t1, jprev, floor, B, F, ba, top);
+      scan_run<W, T, TP, K, RESCAN, NX, NY + 1>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair, floor, B, F, ba,
+                                                top);
   }
 }
 
@@ -616,6 +649,10 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
     uint32_t ba = ((st.cls[1][0] & mq) | (st.cls[0][0] & ~mq)) & 1u;
     const bool has_centre = (g.c & 1) == q;
     const int nloop = (q ? g.D / 2 : (g.D + 1) / 2) - (has_centre ? 1 : 0);
+    // the previous pivot's flip index in this class (-1: none), and the first
+    // t whose pair lag c - a = c - 2t - q is <= t
+    const int tprev = (jprev >= 0 && (jprev & 1) == q) ? (jprev >> 1) : -1;
+    const int tpair = (g.c - q + 2) / 3;
     if (W >= kPatternMinWords && W <= PMAX && !RESCAN) {
       for (int t = 0; t < nloop;) {
         const int nx = (t + 31) >> 5;
@@ -623,18 +660,25 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
         const int ny = ly > 0 ? (ly + 31) >> 5 : 0;
         int t1 = 32 * nx + 1;                                             // next change of nx
         if (ny > 0 && Nq - 1 - 32 * (ny - 1) < t1) t1 = Nq - 1 - 32 * (ny - 1);  // ... or of ny
+        if (t < tpair && tpair < t1) t1 = tpair;                          // ... or of the pair lag's side
         if (t1 > nloop) t1 = nloop;
-        scan_run<W, T, TP, K, RESCAN>(st, g, mu, rows, q, nx, ny, t, t1, jprev, floor, B, F, ba, top);
+        scan_run<W, T, TP, K, RESCAN>(st, g, mu, rows, q, nx, ny, t, t1, tprev, tpair, floor, B, F, ba, top);
         t = t1;
       }
     } else {
-      scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, 0, nloop, jprev, floor, B, F, ba, top);
+      for (int t = 0; t < nloop;) {  // at most two runs, split where the pair lag changes side
+        const int t1 = (t < tpair && tpair < nloop) ? tpair : nloop;
+        scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t, t1, tprev, tpair, floor, B, F, ba, top);
+        t = t1;
+      }
     }
     if (has_centre) {
       const int t = nloop, a = g.c;
       uint32_t Vx[W], Vye[W];
       load_mask_row<W>(rows + (size_t)t * MT::kRowWords, Vx, Vye);
-      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vye, ba, a, t, 0, t, Nq);
+      // the centre has n = |Vx| = t and no y side (nxy = 0)
+      uint32_t x = flip_key<W, T, TP, true>(st, mu, B, F, Vx, Vye, ba, key_base<TP>(a, t, 0), key_diff<TP>(t, 0), t,
+                                            Nq);
       x = (a == jprev || (RESCAN && x < floor)) ? kNone : x;
       top_insert(top, x);
     }
