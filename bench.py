@@ -46,7 +46,7 @@ SM_MAX_MHZ = 2070.0
 # capture summarised in profiles/walk_kernel_L121_107008x1024_ncu_full.md
 # (18.68 GB for 107008 walks x 1024 steps, scaled by walk-steps to 131072 x 8192),
 # valid only for the kernel sources it was captured from.
-TRAFFIC = {"sources_sha256_prefix": "6b4c542dd935c71a", "bytes_per_launch": 18.68e9 * (131072 * 8192) / (107008 * 1024)}
+TRAFFIC = {"sources_sha256_prefix": "6dd5a5d1b544e5e9", "bytes_per_launch": 18.69e9 * (131072 * 8192) / (107008 * 1024)}
 WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_incr.cuh", "walk_class.cu", "walk_kernels.cuh"]
 
 

@@ -65,17 +65,22 @@ def test_requests_same_alone_and_mixed(m):
 
 
 def test_requests_arriving_while_others_run(m):
-    with m.Server(max_walks=256, rounds_per_launch=1) as sv:
-        tickets = []
-        seen_active = 0
+    # the first request runs six rounds at L=301 (a few hundred ms on its own),
+    # so the others, submitted 10 ms apart, arrive while it is on the GPU
+    first = (301, 256, 1208, 12, 256 * 1208 * 151 * 6)
+    reqs = [first] + REQS
+    with m.Server(max_walks=512, rounds_per_launch=1) as sv:
+        tickets = [sv.submit(*first)]
         for p in REQS:
+            time.sleep(0.01)
             tickets.append(sv.submit(*p))
-            time.sleep(0.05)
-            seen_active = max(seen_active, sv.stats()["active"])
         results = [sv.wait(t) for t in tickets]
-        for p, r in zip(REQS, results):
-            check(m, p, r)
-        assert seen_active >= 2  # later requests joined while earlier ones were on the GPU
+    for p, r in zip(reqs, results):
+        check(m, p, r)
+    assert results[0]["rounds"] == 6
+    # later requests were admitted, and finished, while the first one was running
+    assert any(r["t_admit_ns"] < results[0]["t_done_ns"] for r in results[1:])
+    assert any(r["t_done_ns"] < results[0]["t_done_ns"] for r in results[1:])
 
 
 def test_memory_admission_serialises_and_rejects(m):
