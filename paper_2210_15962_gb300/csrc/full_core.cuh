@@ -135,10 +135,12 @@ LABS_HD int full_planes_needed(const FullState<W, T> &st, int L) {
 }
 
 // Valid-lag masks of every flip: row j at j * kRowWords holds Vx[0..W-1]
-// (lags 1..j) then Vy[0..W-1] (lags 1..L-1-j), padded to 16 bytes.
+// (lags 1..j), Vy[0..W-1] (lags 1..L-1-j) and the number of lags with L-k
+// even that only one side has (|(Vx ^ Vy) & evm|, a term of Qev that depends
+// on the flip alone), padded to 16 bytes.
 template <int W>
 struct FullMaskTable {
-  static constexpr int kRowWords = (2 * W + 3) / 4 * 4;
+  static constexpr int kRowWords = (2 * W + 1 + 3) / 4 * 4;
   static constexpr int kRows = 32 * W + 1;  // >= L
   static constexpr int kWords = kRows * kRowWords;
 };
@@ -146,15 +148,43 @@ struct FullMaskTable {
 template <int W>
 LABS_HD void fill_full_mask_rows(int L, uint32_t *tab, int first, int step) {
   using MT = FullMaskTable<W>;
+  const uint32_t evm = full_even_lag_mask(L);
   for (int r = first; r < MT::kRows; r += step) {
     uint32_t *row = tab + (size_t)r * MT::kRowWords;
     for (int k = 0; k < MT::kRowWords; ++k) row[k] = 0u;
     if (r >= L) continue;
+    uint32_t c1 = 0;
     for (int w = 0; w < W; ++w) {
       row[w] = low_mask_word(r, w);
       row[W + w] = low_mask_word(L - 1 - r, w);
+      c1 += popc32((row[w] ^ row[W + w]) & evm);
     }
+    row[2 * W] = c1;
   }
+}
+
+template <int W>
+LABS_HD void load_full_row(const uint32_t *row, uint32_t (&Vx)[W], uint32_t (&Vy)[W], uint32_t &c1) {
+  using MT = FullMaskTable<W>;
+  uint32_t r[MT::kRowWords];
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+  for (int k = 0; k < MT::kRowWords / 4; ++k) {
+    const uint4 v = reinterpret_cast<const uint4 *>(row)[k];
+    r[4 * k] = v.x;
+    r[4 * k + 1] = v.y;
+    r[4 * k + 2] = v.z;
+    r[4 * k + 3] = v.w;
+  }
+#else
+  for (int k = 0; k < MT::kRowWords; ++k) r[k] = row[k];
+#endif
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Vx[w] = r[w];
+    Vy[w] = r[W + w];
+  }
+  c1 = r[2 * W];
 }
 
 // One flip: the packed key ((Delta + bias) << 8) | j.  B, F: x / y windows
@@ -164,10 +194,23 @@ LABS_HD void fill_full_mask_rows(int L, uint32_t *tab, int first, int step) {
 // equal), Qev = sum over even-C lags of the products' sum,
 //   Delta = -8 S + (16 + 8 K1) M + 4 Qev + (4 + 4 K1) n - (8 + 8 K1) n2,
 // n = L-1 valid (lag, side) pairs, n2 = |V2| = min(j, L-1-j), K1 = 2^TP - 1.
+// Qev = c1 + 2 |M2e| - 2 |V1e & G| - 4 |M2e & G| over the lags with L-k even
+// (suffix e), G the product bits, c1 = |V1e| from the mask row.  The key is
+// then -2048 S + 256 (16 + 8 K1) M + 1024 (Qev - c1) + kbase + 1024 c1 with
+//   kbase = 256 ((4 + 4 K1) n - (8 + 8 K1) n2 + bias) + j   (modulo 2^32),
+// which moves by a constant per flip on each side of j = L/2; kc = kbase + 1024 c1.
+template <int TP>
+LABS_HD uint32_t full_key_base(int j, int L) {
+  constexpr uint32_t K1 = (1u << TP) - 1u;
+  const int n2 = j < L - 1 - j ? j : L - 1 - j;
+  return 256u * ((4u + 4u * K1) * (uint32_t)(L - 1) - (8u + 8u * K1) * (uint32_t)n2 + (uint32_t)kDeltaBias) +
+         (uint32_t)j;
+}
+
 template <int W, int T, int TP>
 LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const uint32_t (&B)[W],
                                const uint32_t (&F)[W], const uint32_t (&Vx)[W], const uint32_t (&Vy)[W],
-                               uint32_t ba, int j, int L, uint32_t evm) {
+                               uint32_t ba, int j, int L, uint32_t evm, uint32_t kc) {
   uint32_t acc = 0, mcnt = 0;
   int qev = 0;
   const uint32_t bm = 0u - ba;
@@ -194,8 +237,8 @@ LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const 
       }
       v = imad(v, mu.two, popc32(lop3<kLutAndXor>(v1, gb, st.ep[0][w])));
       mcnt = imad(popc32(m2), mu.one, mcnt);
-      const uint32_t v1e = v1 & evm, m2e = m2 & evm;
-      qev += (int)popc32(v1e) - 2 * (int)popc32(lop3<kLutAnd3>(v1, evm, gb)) + 2 * (int)popc32(m2e) -
+      const uint32_t m2e = m2 & evm;
+      qev += 2 * (int)popc32(m2e) - 2 * (int)popc32(lop3<kLutAnd3>(v1, evm, gb)) -
              4 * (int)popc32(lop3<kLutAnd3>(m2, evm, gb));
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : Vy[w];
@@ -203,16 +246,12 @@ LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const 
       v = popc32(lop3<kLutAndXor>(m, g, st.ep[T - 1][w]));
 #pragma unroll
       for (int tt = TP - 2; tt >= 0; --tt) v = imad(v, mu.two, popc32(lop3<kLutAndXor>(m, g, st.ep[tt][w])));
-      qev += (int)popc32(m & evm) - 2 * (int)popc32(lop3<kLutAnd3>(m, evm, g));
+      qev -= 2 * (int)popc32(lop3<kLutAnd3>(m, evm, g));
     }
     acc = imad(acc, mu.one, v);
   }
-  constexpr int K1 = (1 << TP) - 1;
-  const int n = L - 1;
-  const int n2 = j < L - 1 - j ? j : L - 1 - j;
-  const int rest = 4 * qev + (4 + 4 * K1) * n - (8 + 8 * K1) * n2 + kDeltaBias;
-  const uint32_t delta = imad(acc, (uint32_t)-8, imad(mcnt, (uint32_t)(16 + 8 * K1), (uint32_t)rest));
-  return imad(delta, 256u, (uint32_t)j);
+  constexpr uint32_t K1 = (1u << TP) - 1u;
+  return imad(acc, (uint32_t)-2048, imad(mcnt, 256u * (16u + 8u * K1), imad((uint32_t)qev, 1024u, kc)));
 }
 
 // Delta_j of all L flips with TP planes; the K smallest packed keys (>= floor
@@ -223,7 +262,7 @@ LABS_HD void full_eval_tp(const FullState<W, T> &st, int L, const Muls &mu, cons
   using MT = FullMaskTable<W>;
 #pragma unroll
   for (int r = 0; r < K; ++r) top[r] = kNone;
-  uint32_t F[W], B[W], Vx[W], Vy[W];
+  uint32_t F[W], B[W], Vx[W], Vy[W], c1;
 #pragma unroll
   for (int w = 0; w < W; ++w) {
     F[w] = fshr(st.bits[w], st.bits[w + 1], 1u);
@@ -231,19 +270,27 @@ LABS_HD void full_eval_tp(const FullState<W, T> &st, int L, const Muls &mu, cons
   }
   uint32_t ba = st.bits[0] & 1u;
   const uint32_t evm = full_even_lag_mask(L);
+  constexpr uint32_t K1 = (1u << TP) - 1u;
   const uint32_t *row = mt;
-  for (int j = 0; j < L; ++j, row += MT::kRowWords) {
-    load_mask_row<W>(row, Vx, Vy);
-    uint32_t x = full_flip_key<W, T, TP>(st, mu, B, F, Vx, Vy, ba, j, L, evm);
-    x = (j == jprev || (RESCAN && x < floor)) ? kNone : x;
-    top_insert(top, x);
-    const uint32_t ba_next = F[0] & 1u;
+  // two runs, n2 = j below L/2 and L-1-j from there, the key base stepped along each
+#pragma unroll 1
+  for (int part = 0; part < 2; ++part) {
+    const int j0 = part ? L / 2 : 0, j1 = part ? L : L / 2;
+    const uint32_t step = part ? 1u + 256u * (8u + 8u * K1) : 1u - 256u * (8u + 8u * K1);
+    uint32_t kbase = full_key_base<TP>(j0, L);
+    for (int j = j0; j < j1; ++j, row += MT::kRowWords, kbase += step) {
+      load_full_row<W>(row, Vx, Vy, c1);
+      uint32_t x = full_flip_key<W, T, TP>(st, mu, B, F, Vx, Vy, ba, j, L, evm, imad(c1, 1024u, kbase));
+      x = (j == jprev || (RESCAN && x < floor)) ? kNone : x;
+      top_insert(top, x);
+      const uint32_t ba_next = F[0] & 1u;
 #pragma unroll
-    for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
-    B[0] = imad(B[0], mu.two, ba);
+      for (int w = W - 1; w >= 1; --w) B[w] = imadhi(B[w - 1], mu.two, imad(B[w], mu.two, 0u));
+      B[0] = imad(B[0], mu.two, ba);
 #pragma unroll
-    for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
-    ba = ba_next;
+      for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
+      ba = ba_next;
+    }
   }
 }
 
