@@ -195,10 +195,21 @@ LABS_HD void load_full_row(const uint32_t *row, uint32_t (&Vx)[W], uint32_t (&Vy
 //   Delta = -8 S + (16 + 8 K1) M + 4 Qev + (4 + 4 K1) n - (8 + 8 K1) n2,
 // n = L-1 valid (lag, side) pairs, n2 = |V2| = min(j, L-1-j), K1 = 2^TP - 1.
 // Qev = c1 + 2 |M2e| - 2 |V1e & G| - 4 |M2e & G| over the lags with L-k even
-// (suffix e), G the product bits, c1 = |V1e| from the mask row.  The key is
-// then -2048 S + 256 (16 + 8 K1) M + 1024 (Qev - c1) + kbase + 1024 c1 with
+// (suffix e), G the product bits, c1 = |V1e| from the mask row.  The two
+// G-dependent terms carry S's coefficient; in a two-sided word they join the
+// plane sums by one carry-save step, |Z_0| + |A| = |Z_0 ^ A| + 2 |Z_0 & A| with
+// A = V1e & G, where Z_0 & A (in V1) and M2e & G (in M2) are disjoint, so
+//   S + |A| + 2 |M2e & G| = sum_{t>=1} 2^t |Z_t| + 2 |(Z_0 & A) | (M2e & G)| + |Z_0 ^ A|,
+//   Z_0 ^ A = V1 & ((G & ~evm) ^ e_0),  (Z_0 & A) | (M2e & G) = evm & G & ((V1 & ~e_0) | M2),
+// one popcount fewer.  The key is then
+//   -2048 S' + 256 (16 + 8 K1) M + 1024 Q' + kbase + 1024 c1
+// (S' the plane sums with these terms; Q' = 2 |M2e| of the two-sided words
+// less 2 |V1e & G| of the one-sided words, where V1 is the valid side) with
 //   kbase = 256 ((4 + 4 K1) n - (8 + 8 K1) n2 + bias) + j   (modulo 2^32),
 // which moves by a constant per flip on each side of j = L/2; kc = kbase + 1024 c1.
+constexpr uint32_t kLutAndNotXor = 0x9A;  // (a & ~b) ^ c
+constexpr uint32_t kLutAndNotOr = 0xBA;   // (a & ~b) | c
+
 template <int TP>
 LABS_HD uint32_t full_key_base(int j, int L) {
   constexpr uint32_t K1 = (1u << TP) - 1u;
@@ -235,11 +246,12 @@ LABS_HD uint32_t full_flip_key(const FullState<W, T> &st, const Muls &mu, const 
         const uint32_t et = lop3<kLutSelect>(v1, e1, e0);
         v = imad(v, mu.two, popc32(lop3<kLutAndXor>(mall, gb, et)));
       }
-      v = imad(v, mu.two, popc32(lop3<kLutAndXor>(v1, gb, st.ep[0][w])));
+      // the even-lag terms by the carry-save step above: weight 2 and weight 1
+      const uint32_t e0 = st.ep[0][w];
+      v = imad(popc32(lop3<kLutAnd3>(evm, gb, lop3<kLutAndNotOr>(v1, e0, m2))), mu.one, v);
+      v = imad(v, mu.two, popc32(v1 & lop3<kLutAndNotXor>(gb, evm, e0)));
       mcnt = imad(popc32(m2), mu.one, mcnt);
-      const uint32_t m2e = m2 & evm;
-      qev += 2 * (int)popc32(m2e) - 2 * (int)popc32(lop3<kLutAnd3>(v1, evm, gb)) -
-             4 * (int)popc32(lop3<kLutAnd3>(m2, evm, gb));
+      qev += 2 * (int)popc32(m2 & evm);
     } else if (xa || ya) {
       const uint32_t m = xa ? vx : Vy[w];
       const uint32_t g = (xa ? B[w] : F[w]) ^ bm;
