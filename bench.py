@@ -155,11 +155,30 @@ def dist_setup():
     return world, rank, local
 
 
+CPU_SAMPLE_LAG_UPDATES = 1.5e10  # about 13 s of oracle work on 16 host cores
+
+
+CPU_STEP_OVERHEAD = 256  # the oracle's per-step set lookups and move, in (flip, lag) updates
+
+
+def cpu_sample_walks(L, walk_len, cores, full=False, total_walks=None, lag_updates=CPU_SAMPLE_LAG_UPDATES):
+    """Walks in the oracle's timed sample: a whole number of walks per core,
+    enough for about `lag_updates` (flip, lag) updates (the oracle's cost per
+    evaluation grows with the lag count), at least one walk per core and at
+    most the workload's walks."""
+    flips = L if full else (L + 1) // 2
+    lags = max(1, L - 1 if full else (L - 1) // 2)
+    per_walk = float(walk_len) * (flips * lags + CPU_STEP_OVERHEAD)
+    per_core = max(1, -(-int(lag_updates) // max(1, int(per_walk * cores))))
+    n = per_core * cores
+    return min(n, total_walks) if total_walks else n
+
+
 def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS, full=False):
     """The oracle on a bounded sample of the benchmark's walks, all host cores."""
     import oracle
     cores = os.cpu_count() or 1
-    n = n_walks or 8 * cores
+    n = n_walks or cpu_sample_walks(L, walk_len, cores, full, total_walks)
     t0 = time.perf_counter()
     r = oracle.walk_batch(L, seed, 0, 0, n, walk_len, threads=cores, full=full)
     dt = time.perf_counter() - t0
@@ -174,7 +193,7 @@ def run_reference(args, world, rank):
         return
     steps = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(n_walks=args.ref_walks)
+        cb = cpu_baseline(n_walks=args.ref_walks or 8 * (os.cpu_count() or 1))
         if i >= args.warmup:
             steps.append(cb)
     val = statistics.mean(s["value"] for s in steps)

@@ -1,6 +1,6 @@
 """CPU checks of bench.py's helpers: the Table 1 fixture reader, the symmetry
-images used to compare a found sequence with Table 1's, and the work unit of
-the roofline accounting."""
+images used to compare a found sequence with Table 1's, the work unit of the
+roofline accounting and the size of the oracle's timed sample."""
 import os
 import sys
 
@@ -35,3 +35,21 @@ def test_roofline_unit_counts_the_lags_of_each_space():
     # 4 LOP3 per 32 lags and digit plane: (L-1)/2 even lags of a skew sequence, L-1 lags in the full space
     assert bench.core_alu_ops_per_eval(121, 5.0) == 4.0 * 5.0 * 60 / 32
     assert bench.core_alu_ops_per_eval(121, 5.0, full=True) == 4.0 * 5.0 * 120 / 32
+
+
+def test_cpu_sample_is_bounded_and_whole_per_core():
+    def work(n, L, wl, full=False):
+        flips = L if full else (L + 1) // 2
+        lags = L - 1 if full else (L - 1) // 2
+        return n * wl * (flips * lags + bench.CPU_STEP_OVERHEAD)
+    target = bench.CPU_SAMPLE_LAG_UPDATES
+    for L, wl, cores, full in [(121, 8192, 16, False), (27, 4096, 16, False), (449, 16384, 16, False),
+                               (128, 2048, 8, True), (64, 4096, 12, True)]:
+        n = bench.cpu_sample_walks(L, wl, cores, full)
+        assert n % cores == 0 and n >= cores
+        # just enough whole walks per core to reach the target work
+        assert work(n, L, wl, full) >= target or n == cores
+        assert work(n - cores, L, wl, full) < target
+    assert 16 * 16 <= bench.cpu_sample_walks(121, 8192, 16) <= 64 * 16  # ~13 s of oracle work
+    assert bench.cpu_sample_walks(449, 10 ** 7, 16) == 16               # one walk per core at least
+    assert bench.cpu_sample_walks(27, 4096, 16, total_walks=64) == 64   # never more than the workload
