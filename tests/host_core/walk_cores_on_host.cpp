@@ -1,9 +1,10 @@
-// Runs the CUDA path's walk cores on the host: walk_core.cuh and full_core.cuh
-// hold the arithmetic of the walk kernels as host+device functions, and this
-// program compiles them with the host compiler.  It reads cases from stdin,
-// one per line:
+// Runs the CUDA path's walk cores on the host: walk_core.cuh, full_core.cuh
+// and walk_incr.cuh hold the arithmetic of the walk kernels as host+device
+// functions, and this program compiles them with the host compiler.  It reads
+// cases from stdin, one per line:
 //   skew L seed round walk walk_len force_tp pmax
 //   full L seed round walk walk_len force_tp
+//   incr L seed round walk walk_len            (the incremental neighbourhood)
 // and prints, per case, one line
 //   moves stuck best_E recheck_ok | flip_1 .. flip_moves | E_0 E_1 .. E_moves
 // A CPU test compares these with the oracle walk by walk.  The step loop here
@@ -18,10 +19,12 @@
 #include <iostream>
 #include <sstream>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "walk_core.cuh"
 #include "full_core.cuh"
+#include "walk_incr.cuh"
 
 using namespace psaw;
 
@@ -159,6 +162,81 @@ Walk run_full(int L, uint64_t seed, uint32_t walk, uint32_t round, int walk_len,
   return out;
 }
 
+// the incremental variant's storage per class, as its kernel stores it:
+// C_{2i} as int8 up to two lag words, Delta / 8 as int16 up to three
+template <int W>
+struct IncrStorage {
+  using CT = typename std::conditional<W <= 2, int8_t, int16_t>::type;
+  using DT = typename std::conditional<W <= 3, int16_t, int32_t>::type;
+};
+
+template <int W>
+Walk run_incr(int L, uint64_t seed, uint32_t walk, uint32_t round, int walk_len) {
+  using CT = typename IncrStorage<W>::CT;
+  using DT = typename IncrStorage<W>::DT;
+  constexpr int NS = W + 1;
+  const Geometry g = make_geometry(L, skew_planes<W>());
+  std::vector<CT> Cs(g.m + 1);
+  std::vector<DT> Ds(g.D + 1);
+  const IncrView<CT, DT> v{Cs.data(), Ds.data(), 1};
+  IncrState<W> st;
+  init_incr(st, g, v, seed, walk, round);
+  Walk out;
+  out.recheck_ok = recheck_incr(st, g, v);
+  const uint32_t cap = table_cap(walk_len);
+  const int kw = key_words64(g.D);
+  std::vector<uint64_t> table((size_t)cap * kw, 0);
+  uint32_t slot;
+  table_find(table.data(), cap, kw, st.key, g.D, &slot);
+  table_store(table.data(), slot, kw, st.key, g.D);
+  out.best_E = st.E;
+  out.energies.push_back(st.E);
+  const Muls mu{1u, 2u, 4u, 0x80000000u, 0x40000000u};
+  int jprev = -1;
+  // the stored deltas are scanned once at the start; each move updates them
+  // and hands over the next step's 4 smallest keys; rescans read them again
+  uint32_t next[kTop];
+  scan_stored<W, CT, DT, kTop>(g, v, -1, 0u, next);
+  for (int step = 1; step <= walk_len; ++step) {
+    auto eval = [&](uint32_t floor, uint32_t (&top)[kTop]) {
+      if (floor == 0) {
+        for (int r = 0; r < kTop; ++r) top[r] = next[r];
+      } else {
+        scan_stored<W, CT, DT, kTop>(g, v, jprev, floor, top);
+      }
+    };
+    int flip, delta;
+    const bool found = choose<NS>(eval, st.key, g.D, table, cap, kw, &flip, &delta, &slot);
+    if (!found) {
+      out.stuck = 1;
+      break;
+    }
+    MoveData<W> md;
+    apply_move_incr(st, g, v, flip, md);
+    table_store(table.data(), slot, kw, st.key, g.D);
+    jprev = flip;
+    out.flips.push_back(flip);
+    out.energies.push_back(st.E);
+    if (st.E < out.best_E) out.best_E = st.E;
+    update_neighbours_fast<W, CT, DT, kTop>(st, g, v, md, mu, next);
+    out.recheck_ok = out.recheck_ok && recheck_incr(st, g, v);
+  }
+  return out;
+}
+
+Walk incr_by_class(int L, uint64_t seed, uint32_t round, uint32_t walk, int walk_len) {
+  switch (((L - 1) / 2 + 31) / 32) {
+    case 1: return run_incr<1>(L, seed, walk, round, walk_len);
+    case 2: return run_incr<2>(L, seed, walk, round, walk_len);
+    case 3: return run_incr<3>(L, seed, walk, round, walk_len);
+    case 4: return run_incr<4>(L, seed, walk, round, walk_len);
+    case 5: return run_incr<5>(L, seed, walk, round, walk_len);
+    case 6: return run_incr<6>(L, seed, walk, round, walk_len);
+    case 7: return run_incr<7>(L, seed, walk, round, walk_len);
+    default: return run_incr<8>(L, seed, walk, round, walk_len);
+  }
+}
+
 template <int PMAX>
 Walk skew_by_class(int L, uint64_t seed, uint32_t round, uint32_t walk, int walk_len, bool force_tp) {
   switch (((L - 1) / 2 + 31) / 32) {
@@ -197,13 +275,17 @@ int main() {
     int L = 0, walk_len = 0, force_tp = 0, pmax = 4;
     unsigned long long seed = 0;
     unsigned round = 0, walk = 0;
-    if (!(in >> space >> L >> seed >> round >> walk >> walk_len >> force_tp)) continue;
+    if (!(in >> space >> L >> seed >> round >> walk >> walk_len)) continue;
+    if (space != "incr" && !(in >> force_tp)) return 2;
     Walk r;
     if (space == "skew") {
       in >> pmax;
       if (L < kLMin || L > kLMax || (L % 2) == 0) return 2;
       r = pmax == 2 ? skew_by_class<2>(L, seed, round, walk, walk_len, force_tp != 0)
                     : skew_by_class<4>(L, seed, round, walk, walk_len, force_tp != 0);
+    } else if (space == "incr") {
+      if (L < kLMin || L > kLMax || (L % 2) == 0) return 2;
+      r = incr_by_class(L, seed, round, walk, walk_len);
     } else if (space == "full") {
       if (L < kFullLMin || L > kFullLMax) return 2;
       r = full_by_class(L, seed, round, walk, walk_len, force_tp != 0);

@@ -1,10 +1,11 @@
 """The CUDA path's walk cores, compiled for the host, against the oracle.
 
-`walk_core.cuh` and `full_core.cuh` hold the walk kernels' arithmetic as
-host+device functions: the start (Philox draw, Eq. 2 expansion, Eq. 1
-correlations into digit planes), the bit-sliced neighbourhood scan of
-Algorithm 2 with its pattern runs, sign fold, stepped key and plane-count
-choice, the move's bit-sliced update and the visited table.
+`walk_core.cuh`, `full_core.cuh` and `walk_incr.cuh` hold the walk kernels'
+arithmetic as host+device functions: the start (Philox draw, Eq. 2
+expansion, Eq. 1 correlations into digit planes), the bit-sliced
+neighbourhood scan of Algorithm 2 with its pattern runs, sign fold, stepped
+key and plane-count choice, the move's bit-sliced update, the incremental
+variant's stored correlations and deltas, and the visited table.
 `host_core/walk_cores_on_host.cpp` compiles them with g++ and walks with them;
 every walk's flips, energies, best E and stuck flag must equal the oracle's,
 and the digit planes must pass the full recheck after every move.  This runs
@@ -86,6 +87,15 @@ def test_skew_cores_long_walks_with_rescans(cores, oracle_mod):
     for case, got in zip(cases, res):
         compare(oracle_mod, case, got, full=False)
     assert any(r["stuck"] for r in res)
+
+
+def test_incremental_cores_match_the_oracle(cores, oracle_mod):
+    # the incremental neighbourhood (stored C and Delta, updated by each move), every class, with the
+    # kernel's storage widths; short walks at small L revisit and rescan
+    cases = [("incr", L, 11, 2, walk, walk_len_for(L)) for L in SKEW_L for walk in range(2)]
+    cases += [("incr", L, 5, 0, walk, wl) for L, wl in [(7, 80), (13, 4000)] for walk in range(2)]
+    for case, got in zip(cases, run_cases(cores, cases)):
+        compare(oracle_mod, case, got, full=False)
 
 
 def test_full_cores_match_the_oracle(cores, oracle_mod):
