@@ -21,7 +21,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 
 SOURCES = ["walk_kernels.cu", "walk_class.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu",
            "serve.cu", "model.cu"]
-HEADERS = ["walk_core.cuh", "walk_kernels.cuh", "walk_device.cuh", "walk_incr.cuh", "batch.cuh"]
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))  # every header of the sources
 LAG_WORD_CLASSES = range(1, 9)  # walk_class.cu is compiled once per class W (m <= 32 W lags)
 
 
