@@ -1,7 +1,10 @@
 """CPU checks of bench.py's helpers: the Table 1 fixture reader, the symmetry
 images used to compare a found sequence with Table 1's, the work unit of the
-roofline accounting and the size of the oracle's timed sample."""
+roofline accounting, the size of the oracle's timed sample and the JSON line
+of the reference arm (the oracle, which needs no GPU)."""
+import json
 import os
+import subprocess
 import sys
 
 import numpy as np
@@ -53,3 +56,21 @@ def test_cpu_sample_is_bounded_and_whole_per_core():
     assert 16 * 16 <= bench.cpu_sample_walks(121, 8192, 16) <= 64 * 16  # ~13 s of oracle work
     assert bench.cpu_sample_walks(449, 10 ** 7, 16) == 16               # one walk per core at least
     assert bench.cpu_sample_walks(27, 4096, 16, total_walks=64) == 64   # never more than the workload
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--ref-walks", "4"], capture_output=True, text=True, check=True,
+                         cwd=ROOT, timeout=600).stdout
+    lines = [x for x in out.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "neighbour_evals_per_s" and d["unit"] == "neighbour_evals/s"
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1 and d["vs_baseline"] is None
+    assert d["config"]["workload"] == "plain_L121_131072x8192_budget1e11"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "4 of the 131072" in cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
