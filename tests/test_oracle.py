@@ -139,6 +139,26 @@ def test_exhaustive_vs_numpy_and_invariants(oracle_mod, L):
         assert best == (L - 1) // 2  # Barker sequences are optimal where they exist
 
 
+# ------------------------------------------ random sequences up to L=511
+@pytest.mark.parametrize("L", [2, 3, 64, 121, 128, 255, 256, 449, 511])
+def test_random_sequences_vs_numpy(oracle_mod, L):
+    # Eq. 1 against numpy's correlation at the lengths the solvers take (full space up to 256, skew up to 511),
+    # and for odd L the skew expansion of Eq. 2 against its definition
+    rng = np.random.default_rng(20221028 + L)
+    for _ in range(8):
+        s = rng.choice(np.array([-1, 1], dtype=np.int8), size=L)
+        assert oracle_mod.energy(s) == np_energy(s)
+        C = oracle_mod.autocorrelations(s)
+        want = [int(np.dot(s[:L - k].astype(np.int64), s[k:].astype(np.int64))) for k in range(1, L)]
+        assert list(C[1:L]) == want
+        if L % 2 == 1 and L >= 5:
+            D = (L + 1) // 2
+            x = oracle_mod.skew_expand(s[:D].copy(), L)
+            # s_{D+i} = (-1)^i s_{D-i} in the paper's 1-based indices
+            assert all(x[D - 1 + i] == (-1) ** i * x[D - 1 - i] for i in range(1, D))
+            assert np.array_equal(x[:D], s[:D])
+
+
 # --------------------------------------------------------------- Philox
 @pytest.mark.parametrize("row", read_rows("philox4x32_10_kat.txt"))
 def test_philox_known_answers(oracle_mod, row):
