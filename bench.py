@@ -174,8 +174,10 @@ def cpu_sample_walks(L, walk_len, cores, full=False, total_walks=None, lag_updat
     return min(n, total_walks) if total_walks else n
 
 
-def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS, full=False):
-    """The oracle on a bounded sample of the benchmark's walks, all host cores."""
+def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WALKS, full=False, one_core=False):
+    """The oracle on a bounded sample of the benchmark's walks, all host cores
+    (with one_core, also the rate of one core on an eighth of one core's share
+    of the sample, at least one walk: about 2 s)."""
     import oracle
     cores = os.cpu_count() or 1
     n = n_walks or cpu_sample_walks(L, walk_len, cores, full, total_walks)
@@ -183,9 +185,17 @@ def cpu_baseline(n_walks=None, walk_len=WALK_LEN, seed=SEED, L=L, total_walks=WA
     r = oracle.walk_batch(L, seed, 0, 0, n, walk_len, threads=cores, full=full)
     dt = time.perf_counter() - t0
     ev = int(r["evals"].sum())
-    return {"value": ev / dt, "unit": "neighbour_evals/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of the %d walks of round 0 (L=%d, %d steps each), %d evaluations in %.1f s"
-                      % (n, total_walks, L, walk_len, ev, dt)}
+    out = {"value": ev / dt, "unit": "neighbour_evals/s", "cores": cores, "kind": "oracle",
+           "sample": "%d of the %d walks of round 0 (L=%d, %d steps each), %d evaluations in %.1f s"
+                     % (n, total_walks, L, walk_len, ev, dt)}
+    if one_core:
+        n1 = max(1, (n // cores) // 8)
+        t0 = time.perf_counter()
+        r1 = oracle.walk_batch(L, seed, 0, 0, n1, walk_len, threads=1, full=full)
+        dt1 = time.perf_counter() - t0
+        ev1 = int(r1["evals"].sum())
+        out["one_core"] = {"value": ev1 / dt1, "sample": "%d walks, %d evaluations in %.1f s" % (n1, ev1, dt1)}
+    return out
 
 
 def run_reference(args, world, rank):
@@ -763,7 +773,7 @@ def main():
             "clocks": clocks,
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks, full=full)
+            line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks, full=full, one_core=True)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

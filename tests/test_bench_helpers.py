@@ -74,3 +74,11 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    cores = os.cpu_count() or 1
+    cb = bench.cpu_baseline(n_walks=8 * cores, walk_len=256, L=27, total_walks=64 * cores, one_core=True)
+    assert cb["kind"] == "oracle" and cb["unit"] == "neighbour_evals/s" and cb["cores"] == cores
+    assert cb["value"] > 0 and ("%d of the %d walks" % (8 * cores, 64 * cores)) in cb["sample"]
+    assert cb["one_core"]["value"] > 0 and cb["one_core"]["sample"].startswith("1 walks")
