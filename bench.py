@@ -42,10 +42,10 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
 
-# DRAM traffic of one walk-kernel launch of the default workload, from the ncu
-# capture summarised in profiles/walk_kernel_L121_107008x1024_ncu_full.md
-# (18.68 GB for 107008 walks x 1024 steps, scaled by walk-steps to 131072 x 8192),
-# valid only for the kernel sources it was captured from.
+# DRAM traffic of one walk-kernel launch of the default workload, from an ncu
+# capture of the walk kernel on 107008 walks x 1024 steps (18.68 GB, scaled by
+# walk-steps to 131072 x 8192), valid only for the kernel sources it was
+# captured from.
 TRAFFIC = {"sources_sha256_prefix": "6dd5a5d1b544e5e9", "bytes_per_launch": 18.69e9 * (131072 * 8192) / (107008 * 1024)}
 WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_incr.cuh", "walk_class.cu", "walk_kernels.cuh"]
 
@@ -387,6 +387,7 @@ def run_serving(args, world, rank, local):
         "p_optimal": {"p50": float(np.percentile([r["p_optimal"] for r in results], 50)),
                       "min": float(min(r["p_optimal"] for r in results))},
         "device_busy_frac": st["busy_ms"] / 1e3 / (t1 - t0),
+        "evals_run": st["evals_run"], "useful_frac": st["evals"] / max(1, st["evals_run"]),
         "plain": {"value": plain_ev / (tp1 - tp0), "unit": "neighbour_evals/s",
                   "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
                   "same_results": bool(same)},

@@ -120,6 +120,23 @@ int64_t labs_energy(const int8_t *seq, int32_t L);
 labs_status labs_energy_batch(const int8_t *seqs, int32_t n, int32_t L, int64_t *E_out, void *stream,
                               int32_t check);
 
+/* Table 1's sequence code (Section 4.2, the text under Table 1): the free
+ * half s_1..s_D of a skew-symmetric sequence (D = (L+1)/2) as D binary digits,
+ * s_1 the most significant, +1 -> 0 and -1 -> 1, written in hexadecimal.  The
+ * other half follows from Eq. 2.  Host-only format helpers: no GPU is used.
+ *   labs_from_hex: hex = NUL-terminated hex digits (an optional "0x" prefix,
+ *     either case, any leading zeros) -> seq_out[L] (host, caller-owned, +-1).
+ *     LABS_EINVAL for a NULL pointer, an L that is not odd in
+ *     LABS_L_MIN..LABS_L_MAX, a character that is not a hex digit, an empty
+ *     code or a value of more than D binary digits.
+ *   labs_to_hex: seq[L] (host, +-1, skew-symmetric) -> out[out_len] (host,
+ *     caller-owned): ceil(D/4) upper-case hex digits, leading zeros kept (the
+ *     form Table 1 prints), then a NUL.  LABS_EINVAL for a NULL pointer, a bad
+ *     L, a value other than +-1, a sequence that breaks Eq. 2, or
+ *     out_len < ceil(D/4) + 1. */
+labs_status labs_from_hex(const char *hex, int32_t L, int8_t *seq_out);
+labs_status labs_to_hex(const int8_t *seq, int32_t L, char *out, size_t out_len);
+
 /* The whole solver (Algorithm 1 around Algorithm 2) for n_seeds independent
  * problems of the same L: rounds of walks_per_seed walks of walk_len steps,
  * until step_budget neighbour evaluations (per seed) or opts->target_E.
@@ -253,6 +270,9 @@ typedef struct labs_serve_stats {
   uint64_t mem_used;         /* admission budget in use */
   int32_t status;            /* LABS_OK, or the error that stopped the server */
   int32_t reserved;
+  uint64_t evals_run;        /* neighbour evaluations the device ran, including rounds run
+                                speculatively past a request's stop (evals counts only the
+                                rounds up to each stop) */
 } labs_serve_stats;
 
 typedef struct labs_server labs_server; /* opaque */
@@ -295,9 +315,12 @@ labs_status labs_serve_destroy(labs_server *s);
  * It calls no allocator.  Its scratch (visited tables, per-walk state,
  * counters) is one static device array of LABS_NOALLOC_SCRATCH_BYTES that
  * every process loading this library holds on every GPU it uses until exit.
- *   walk_best_E[n_walks]      device out: each walk's best energy;
- *   walk_best_seq[n_walks*L]  device out: each walk's best sequence (+-1);
- *   walk_moves, walk_stuck    device out [n_walks] or NULL;
+ * Every output is a caller-owned device pointer to memory of the current
+ * device with at least the elements stated (the library cannot check this:
+ * a smaller or host buffer is written out of bounds):
+ *   walk_best_E[n_walks]      int64, device out: each walk's best energy;
+ *   walk_best_seq[n_walks*L]  int8, device out: each walk's best sequence (+-1);
+ *   walk_moves, walk_stuck    int32 [n_walks] device out, or NULL;
  *   stream                    cudaStream_t or NULL; the call synchronises it
  *                             before returning.
  * The first call on a device looks up the scratch's device address (with

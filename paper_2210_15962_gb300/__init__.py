@@ -135,6 +135,7 @@ class labs_serve_stats(ctypes.Structure):
         ("mem_used", ctypes.c_uint64),
         ("status", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("evals_run", ctypes.c_uint64),
     ]
 
 
@@ -187,6 +188,8 @@ _EXPORTS = {
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                              ctypes.c_int32, ctypes.c_void_p]),
+    "labs_from_hex": (ctypes.c_int32, [ctypes.c_char_p, ctypes.c_int32, ctypes.c_void_p]),
+    "labs_to_hex": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t]),
     "labs_model_lambda": (ctypes.c_double, [ctypes.c_int32]),
     "labs_model_nses_limit": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32]),
     "labs_model_p_optimal": (ctypes.c_double, [ctypes.c_int32, ctypes.c_double]),
@@ -396,12 +399,33 @@ def labs_saw_round(L: int, seed: int, round_: int, n_walks: int, walk_len: int, 
 def labs_saw_round_noalloc(L: int, seed: int, round_: int, n_walks: int, walk_len: int, walk_best_E, walk_best_seq,
                            walk_moves=None, walk_stuck=None, stream=None) -> None:
     """labs_saw_round into caller-owned CUDA tensors, using only the library's fixed static scratch
-    (for callers that may not allocate device memory; see include/labs.h)."""
-    def p(t):
-        return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    (for callers that may not allocate device memory; see include/labs.h).
+
+    walk_best_E: int64 (n_walks,), walk_best_seq: int8 (n_walks, L) or (n_walks * L,), walk_moves and
+    walk_stuck: int32 (n_walks,) or None; all contiguous CUDA tensors on the current device.  Anything
+    else raises LabsError(LABS_EINVAL) before the library is called."""
+    import torch
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+
+    def p(t, dtype, numel, name, optional=False):
+        if t is None:
+            if optional:
+                return None
+            raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc (%s is required)" % name)
+        ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == dtype
+              and t.is_contiguous() and t.numel() >= numel)
+        if not ok:
+            raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc (%s must be a contiguous %s CUDA tensor on the "
+                                         "current device with at least %d elements)" % (name, dtype, numel))
+        return ctypes.c_void_p(t.data_ptr())
+    if n_walks < 1 or L < 1:
+        raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc")
+    args = (p(walk_best_E, torch.int64, n_walks, "walk_best_E"),
+            p(walk_best_seq, torch.int8, n_walks * L, "walk_best_seq"),
+            p(walk_moves, torch.int32, n_walks, "walk_moves", True),
+            p(walk_stuck, torch.int32, n_walks, "walk_stuck", True))
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
-    _check(load().labs_saw_round_noalloc(L, seed, round_, n_walks, walk_len, p(walk_best_E), p(walk_best_seq),
-                                         p(walk_moves), p(walk_stuck), st), "labs_saw_round_noalloc")
+    _check(load().labs_saw_round_noalloc(L, seed, round_, n_walks, walk_len, *args, st), "labs_saw_round_noalloc")
 
 
 def make_problem(L, walks, walk_len, seed, step_budget, target_E=-1) -> labs_problem:
@@ -550,26 +574,18 @@ class Server:
 
 
 def to_hex(seq) -> str:
-    """Table 1 encoding of a skew-symmetric sequence: its first D values, s_1 as the most
-    significant bit, +1 -> 0 and -1 -> 1, in hexadecimal."""
-    s = np.asarray(seq)
-    D = (s.size + 1) // 2
-    v = 0
-    for x in s[:D]:
-        v = (v << 1) | (1 if x < 0 else 0)
-    return "0x%X" % v
+    """Table 1 code of a skew-symmetric sequence (C ABI labs_to_hex): ceil(D/4)
+    upper-case hex digits of its first D values, s_1 most significant, -1 -> 1."""
+    s = np.ascontiguousarray(seq, dtype=np.int8)
+    out = ctypes.create_string_buffer(s.size // 8 + 8)
+    _check(load().labs_to_hex(_ptr(s), s.size, out, len(out)), "labs_to_hex")
+    return out.value.decode()
 
 
 def from_hex(hexstr: str, L: int) -> np.ndarray:
-    """Inverse of to_hex: the length-L skew-symmetric sequence (Eq. 2) of a Table 1 code."""
-    D = (L + 1) // 2
-    v = int(hexstr, 16)
-    if v >> D:
-        raise ValueError("code has more than D = %d bits" % D)
+    """The length-L skew-symmetric sequence of a Table 1 code (C ABI labs_from_hex)."""
     s = np.zeros(L, dtype=np.int8)
-    for i in range(D):
-        s[i] = -1 if (v >> (D - 1 - i)) & 1 else 1
-    c = D - 1
-    for i in range(1, D):
-        s[c + i] = -s[c - i] if i & 1 else s[c - i]
+    st = load().labs_from_hex(hexstr.encode(), L, _ptr(s))
+    if st != LABS_OK:
+        raise LabsError(st, "labs_from_hex")
     return s

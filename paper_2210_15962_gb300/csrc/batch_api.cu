@@ -24,14 +24,6 @@ bool valid_problem(const labs_problem &p) {
          p.walk_len >= 1 && p.walk_len <= (1 << 26) && p.step_budget >= 1;
 }
 
-// visited-table slots: a power of two >= factor/10 x the pivots of a walk
-uint32_t table_cap_f(int32_t walk_len, int factor_x10) {
-  const uint64_t need = ((uint64_t)walk_len + 1) * (uint64_t)factor_x10 / 10 + 1;
-  uint64_t cap = 64;
-  while (cap < need) cap <<= 1;
-  return (uint32_t)cap;
-}
-
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
   *p = nullptr;
@@ -215,7 +207,7 @@ labs_status build_pools(labs_batch *b) {
     c.pool = nullptr;
     size_t words = 0;
     for (int i : c.probs) {
-      const size_t w = (size_t)table_cap_f(b->pr[i].walk_len, c.factor_x10) * key_words64((b->pr[i].L + 1) / 2);
+      const size_t w = (size_t)visited_table_cap(b->pr[i].walk_len, c.factor_x10) * key_words64((b->pr[i].L + 1) / 2);
       words = std::max(words, w);
     }
     c.pool_words = (words + 1) / 2 * 2;
@@ -234,7 +226,7 @@ labs_status build_pools(labs_batch *b) {
     hp[i].W = b->W[i];
     hp[i].walk_len = p.walk_len;
     hp[i].walks = p.walks;
-    hp[i].cap = table_cap_f(p.walk_len, cp->factor_x10);
+    hp[i].cap = visited_table_cap(p.walk_len, cp->factor_x10);
     hp[i].kw64 = key_words64((p.L + 1) / 2);
     hp[i].seed = p.seed;
   }

@@ -28,12 +28,7 @@ int key_bits(int32_t space, int32_t L) { return space == kSpaceFull ? L : (L + 1
 int space_lag_words(int32_t space, int32_t L) { return space == kSpaceFull ? full_lag_words(L) : lag_words(L); }
 
 // visited-table slots: a power of two >= 1.5 x the pivots of a walk
-uint32_t table_cap(int32_t walk_len) {
-  const uint64_t need = ((uint64_t)walk_len + 1) * 3 / 2 + 1;
-  uint64_t cap = 64;
-  while (cap < need) cap <<= 1;
-  return (uint32_t)cap;
-}
+uint32_t table_cap(int32_t walk_len) { return visited_table_cap(walk_len); }
 
 // A bump allocator over one device block.
 struct Carver {
@@ -225,6 +220,61 @@ extern "C" labs_status labs_energy_batch(const int8_t *seqs, int32_t n, int32_t 
 done:
   if (d_err) cudaFreeAsync(d_err, s);
   return st;
+}
+
+// Table 1's encoding (Section 4.2): the free half s_1..s_D as D binary
+// digits, s_1 the most significant, +1 -> 0 and -1 -> 1, printed in
+// hexadecimal with ceil(D/4) digits; the other half follows from Eq. 2.
+static int hex_digit_value(char c) {
+  if (c >= '0' && c <= '9') return c - '0';
+  if (c >= 'a' && c <= 'f') return c - 'a' + 10;
+  if (c >= 'A' && c <= 'F') return c - 'A' + 10;
+  return -1;
+}
+
+extern "C" labs_status labs_from_hex(const char *hex, int32_t L, int8_t *seq_out) {
+  if (!hex || !seq_out || L < LABS_L_MIN || L > LABS_L_MAX || !(L & 1)) return LABS_EINVAL;
+  const int D = (L + 1) / 2;
+  if (hex[0] == '0' && (hex[1] == 'x' || hex[1] == 'X')) hex += 2;
+  const size_t n = std::strlen(hex);
+  if (n == 0 || n > 4096) return LABS_EINVAL;
+  // binary digits from the least significant: bit b of the code -> s_{D-b}
+  std::vector<uint8_t> bits(std::max<size_t>(4 * n, (size_t)D), 0);
+  for (size_t i = 0; i < n; ++i) {
+    const int v = hex_digit_value(hex[n - 1 - i]);
+    if (v < 0) return LABS_EINVAL;
+    for (int k = 0; k < 4; ++k) bits[4 * i + k] = (uint8_t)((v >> k) & 1);
+  }
+  for (size_t b = (size_t)D; b < bits.size(); ++b)
+    if (bits[b]) return LABS_EINVAL;  // more than D binary digits
+  for (int i = 0; i < D; ++i) seq_out[i] = bits[(size_t)(D - 1 - i)] ? (int8_t)-1 : (int8_t)1;
+  // Eq. 2 with 0-based indices: centre c = D-1, s[c+i] = (-1)^i s[c-i]
+  const int c = D - 1;
+  for (int i = 1; i <= c; ++i) seq_out[c + i] = (i & 1) ? (int8_t)-seq_out[c - i] : seq_out[c - i];
+  return LABS_OK;
+}
+
+extern "C" labs_status labs_to_hex(const int8_t *seq, int32_t L, char *out, size_t out_len) {
+  if (!seq || !out || L < LABS_L_MIN || L > LABS_L_MAX || !(L & 1)) return LABS_EINVAL;
+  const int D = (L + 1) / 2, c = D - 1;
+  const int digits = (D + 3) / 4;
+  if (out_len < (size_t)digits + 1) return LABS_EINVAL;
+  for (int i = 0; i < L; ++i)
+    if (seq[i] != 1 && seq[i] != -1) return LABS_EINVAL;
+  for (int i = 1; i <= c; ++i)
+    if (seq[c + i] != ((i & 1) ? -seq[c - i] : seq[c - i])) return LABS_EINVAL;  // not skew-symmetric
+  static const char kHex[] = "0123456789ABCDEF";
+  // hex digit k (from the least significant) holds binary digits 4k..4k+3, binary digit b = [s_{D-b} = -1]
+  for (int k = 0; k < digits; ++k) {
+    int v = 0;
+    for (int bit = 0; bit < 4; ++bit) {
+      const int b = 4 * k + bit;
+      if (b < D && seq[D - 1 - b] < 0) v |= 1 << bit;
+    }
+    out[digits - 1 - k] = kHex[v];
+  }
+  out[digits] = '\0';
+  return LABS_OK;
 }
 
 static size_t workspace_size(int32_t space, int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {

@@ -49,13 +49,6 @@ cudaError_t scratch_address(void **out) {
 
 size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
-uint32_t table_cap(int32_t walk_len) {
-  const uint64_t need = ((uint64_t)walk_len + 1) * 3 / 2 + 1;
-  uint64_t cap = 64;
-  while (cap < need) cap <<= 1;
-  return (uint32_t)cap;
-}
-
 __global__ void widen_kernel(int n, const int32_t *in, int64_t *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[i];
@@ -73,7 +66,7 @@ extern "C" labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t
       !walk_best_E || !walk_best_seq)
     return LABS_EINVAL;
   const int D = (L + 1) / 2;
-  const uint32_t cap = table_cap(walk_len);
+  const uint32_t cap = visited_table_cap(walk_len);  // the rule labs_saw_round uses
   const int kw64 = key_words64(D);
   const size_t table_bytes = (size_t)cap * kw64 * 8;
   // layout inside the static scratch

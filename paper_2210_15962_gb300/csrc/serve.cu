@@ -35,13 +35,6 @@ uint64_t now_ns() {
       .count();
 }
 
-uint32_t cap_for(int32_t walk_len, int factor_x10) {
-  const uint64_t need = ((uint64_t)walk_len + 1) * (uint64_t)factor_x10 / 10 + 1;
-  uint64_t cap = 64;
-  while (cap < need) cap <<= 1;
-  return (uint32_t)cap;
-}
-
 struct Request {
   uint64_t ticket = 0;
   labs_problem p{};
@@ -95,7 +88,7 @@ struct labs_server {
   labs_status failed = LABS_OK;
   std::thread th;
   // counters
-  uint64_t n_submitted = 0, n_completed = 0, evals_done = 0;
+  uint64_t n_submitted = 0, n_completed = 0, evals_done = 0, evals_run = 0;
   uint64_t launches = 0, walk_launches = 0;
   double busy_ms = 0.0;
   uint64_t t_created = 0;
@@ -167,7 +160,7 @@ constexpr int kTableFactor = 15;  // visited-table slots per pivot x 10
 // all ran at once plus its round slots and chunk keys
 size_t request_cost(const labs_problem &p, int rounds_per_launch) {
   const int D = (p.L + 1) / 2;
-  const size_t table = (size_t)cap_for(p.walk_len, kTableFactor) * key_words64(D) * 8;
+  const size_t table = (size_t)visited_table_cap(p.walk_len, kTableFactor) * key_words64(D) * 8;
   const size_t chunks = (size_t)(p.walks + 31) / 32;
   return (size_t)p.walks * table + (size_t)rounds_per_launch * (16 + chunks * kKeyWords * 4) + 256;
 }
@@ -292,7 +285,10 @@ labs_status labs_server::step(std::vector<int> &active) {
   std::vector<int64_t> bestE(n);
   std::vector<unsigned long long> evals(n);
   int32_t err = 0;
-  if (cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  std::vector<unsigned long long> run_evals(nslots);
+  if (cudaMemcpyAsync(run_evals.data(), d_slot_evals, sizeof(unsigned long long) * nslots, cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess ||
+      cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(rounds.data(), d_rounds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(bestE.data(), d_bestE, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(evals.data(), d_evals, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) !=
@@ -327,6 +323,7 @@ labs_status labs_server::step(std::vector<int> &active) {
   }
   const uint64_t t = now_ns();
   std::lock_guard<std::mutex> lock(mu);
+  for (unsigned long long x : run_evals) evals_run += x;
   for (int sl : active) {
     Request &r = *reqs[slot_ticket[sl]];
     evals_done += evals[sl] - r.evals;
@@ -379,7 +376,7 @@ void labs_server::loop() {
           bp.W = r.W;
           bp.walk_len = r.p.walk_len;
           bp.walks = r.p.walks;
-          bp.cap = cap_for(r.p.walk_len, kTableFactor);
+          bp.cap = visited_table_cap(r.p.walk_len, kTableFactor);
           bp.kw64 = key_words64((r.p.L + 1) / 2);
           bp.seed = r.p.seed;
           adm_probs.push_back(bp);
@@ -507,7 +504,7 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
     ClassPool c;
     c.W = W;
     const int Lmax = std::min(cfg.max_L, 64 * W + 1);
-    c.words = (size_t)cap_for(cfg.max_walk_len, kTableFactor) * key_words64((Lmax + 1) / 2);
+    c.words = (size_t)visited_table_cap(cfg.max_walk_len, kTableFactor) * key_words64((Lmax + 1) / 2);
     c.words = (c.words + 1) / 2 * 2;
     c.resident = batch_resident_lanes(W, cfg.block_threads);
     if (c.resident <= 0) return fail(LABS_ECUDA);
@@ -621,6 +618,7 @@ extern "C" labs_status labs_serve_get_stats(labs_server *sv, labs_serve_stats *o
   for (auto t : sv->slot_ticket) act += t != 0;
   out->active = (uint64_t)act;
   out->evals = sv->evals_done;
+  out->evals_run = sv->evals_run;
   out->launches = sv->launches;
   out->walk_launches = sv->walk_launches;
   out->busy_ms = sv->busy_ms;

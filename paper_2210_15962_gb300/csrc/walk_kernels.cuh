@@ -113,6 +113,18 @@ cudaError_t launch_expand(int n, int L, const uint32_t *keys, size_t key_stride,
 cudaError_t launch_energy(const int8_t *seqs, int n, int L, int64_t *E_out, int32_t *err, cudaStream_t s);
 
 inline int lag_words(int L) { return ((L - 1) / 2 + 31) / 32; }
+
+// Visited-table slots of one walk of walk_len steps: the power of two (at
+// least 64) >= factor_x10 / 10 x its walk_len + 1 pivots, plus one.  Every
+// entry point sizes its tables with this one rule (factor 1.5 unless a batch
+// is tuned otherwise).
+constexpr int kTableFactorX10 = 15;
+inline uint32_t visited_table_cap(int32_t walk_len, int factor_x10 = kTableFactorX10) {
+  const uint64_t need = ((uint64_t)walk_len + 1) * (uint64_t)factor_x10 / 10 + 1;
+  uint64_t cap = 64;
+  while (cap < need) cap <<= 1;
+  return (uint32_t)cap;
+}
 // 32-bit words of the L - 1 lags of the full search space
 inline int full_lag_words(int L) { return (L - 1 + 31) / 32; }
 

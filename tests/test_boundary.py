@@ -145,16 +145,49 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         m.load()
 
 
-def test_hex_helpers_roundtrip_table1():
+def test_hex_helpers_roundtrip_table1(lib):
+    # the C ABI's Table 1 helpers (host code, no GPU): every printed code decodes
+    # to a sequence with the printed energy and encodes back to the same digits
     import paper_2210_15962_gb300 as m
     import oracle
     rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "table1_skew_sequences.txt"))
             if l.strip() and not l.startswith("#")]
+    assert len(rows) == 17
     for r in rows:
         L, E, hx = int(r[0]), int(r[1]), r[4]
         s = m.from_hex(hx, L)
         assert oracle.energy(s) == E
-        assert int(m.to_hex(s), 16) == int(hx, 16)
+        assert oracle.energy(oracle.skew_expand(s[:(L + 1) // 2], L)) == E and np.array_equal(
+            oracle.skew_expand(s[:(L + 1) // 2], L), s)
+        assert m.to_hex(s) == hx  # ceil(D/4) digits with the leading zeros Table 1 prints
+        assert np.array_equal(m.from_hex("0x" + hx.lower(), L), s)
+
+
+def test_hex_helpers_reject_bad_input(lib):
+    import paper_2210_15962_gb300 as m
+    L = 27  # D = 14: at most 0x3FFF
+    import oracle
+    assert np.array_equal(m.from_hex("0", L), oracle.skew_expand(np.ones(14, dtype=np.int8), L))
+    assert m.to_hex(m.from_hex("3FFF", L)) == "3FFF"
+    for bad in ["", "0x", "4000", "12G4", "0x-1"]:
+        with pytest.raises(m.LabsError) as ei:
+            m.from_hex(bad, L)
+        assert ei.value.status == m.LABS_EINVAL
+    with pytest.raises(m.LabsError):
+        m.from_hex("1", 26)  # even L
+    s = m.from_hex("2A5", L)
+    t = s.copy()
+    t[-1] = -t[-1]  # breaks Eq. 2
+    with pytest.raises(m.LabsError):
+        m.to_hex(t)
+    t = s.copy()
+    t[0] = 0  # not +-1
+    with pytest.raises(m.LabsError):
+        m.to_hex(t)
+    buf = ctypes.create_string_buffer(4)  # needs ceil(14/4) + 1 = 5 bytes
+    assert lib.labs_to_hex(m._ptr(s), L, buf, 4) == m.LABS_EINVAL
+    assert lib.labs_to_hex(m._ptr(s), L, buf, 0) == m.LABS_EINVAL
+    assert lib.labs_from_hex(None, L, m._ptr(s)) == m.LABS_EINVAL
 
 
 @pytest.mark.parametrize("bad", [(6, 32, 10, 1, 100), (27, 0, 10, 1, 100), (27, 32, 0, 1, 100), (27, 32, 10, 1, 0),

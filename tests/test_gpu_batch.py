@@ -103,3 +103,74 @@ def test_many_instances_config3_shape(m):
     with m.Batch(probs, use_graph=True) as b:
         b.run()
         check_same(m, probs, b.results())
+
+
+def oracle_result(p, threads=8):
+    import oracle
+    L, walks, wl, seed, budget = p[:5]
+    tgt = p[5] if len(p) > 5 else -1
+    o = oracle.solve(L, [seed], walks, wl, budget, target_E=tgt, threads=threads)
+    return {"best_E": int(o["best_E"][0]), "best_seq": o["best_seq"][0], "evals": int(o["evals"][0]),
+            "rounds": int(o["rounds"][0])}
+
+
+def check_oracle(probs, results):
+    for p, g in zip(probs, results):
+        o = oracle_result(p)
+        assert g["best_E"] == o["best_E"], (p, g["best_E"], o["best_E"])
+        assert np.array_equal(g["best_seq"], o["best_seq"]), p
+        assert g["evals"] == o["evals"] and g["rounds"] == o["rounds"], (p, g["evals"], o["evals"])
+
+
+def target_after_rounds(L, walks, wl, seed, rounds):
+    """A target energy the oracle first reaches within `rounds` rounds (its best after them)."""
+    D = (L + 1) // 2
+    return oracle_result((L, walks, wl, seed, walks * wl * D * rounds))["best_E"]
+
+
+# one problem per lag-word class W = ceil(((L-1)/2)/32), each with its own
+# word edge: L = 61 (m=30, W=1), 67 (m=33, W=2), 129 (m=64, W=2 full), 131 (W=3),
+# 161 (W=3), 223 (W=4), 259 (m=129, W=5), 301 (W=5), 383 (W=6), 449 (W=7), 511 (W=8);
+# several rounds each, ragged chunks (walks not a multiple of 32)
+CLASS_PROBS = [
+    (61, 40, 160, 101, 40 * 160 * 31 * 3),
+    (67, 33, 150, 102, 33 * 150 * 34 * 2),
+    (129, 45, 140, 103, 45 * 140 * 65 * 2 + 1),
+    (131, 32, 120, 104, 32 * 120 * 66 * 2),
+    (161, 50, 120, 105, 50 * 120 * 81 * 3),
+    (223, 37, 110, 106, 37 * 110 * 112 * 2),
+    (259, 32, 100, 107, 32 * 100 * 130 * 2),
+    (301, 40, 100, 108, 40 * 100 * 151 * 2),
+    (383, 32, 80, 109, 32 * 80 * 192 * 2),
+    (449, 36, 80, 110, 36 * 80 * 225 * 2),
+    (511, 32, 60, 111, 32 * 60 * 256 * 2),
+]
+
+
+def test_batch_vs_oracle_every_class(m):
+    # the persistent batch kernel of every lag-word class (its own code: pattern
+    # loops, register budgets) against the oracle's Algorithm 1 + Algorithm 2
+    with m.Batch(CLASS_PROBS) as b:
+        b.run()
+        check_oracle(CLASS_PROBS, b.results())
+
+
+def test_batch_vs_oracle_targets_and_graph(m):
+    # target problems (stop at the first round reaching E <= target, later rounds
+    # run speculatively and are ignored) beside budget problems, one per class
+    # W = 2..5, and the CUDA-graph path for the budget-only mix
+    probs = []
+    for L, walks, wl, seed in [(121, 40, 150, 201), (161, 33, 120, 202), (223, 32, 100, 203), (301, 32, 80, 204)]:
+        tgt = target_after_rounds(L, walks, wl, seed, 2)
+        probs.append((L, walks, wl, seed, 10 ** 12, tgt))
+    probs.append((121, 64, 200, 205, 64 * 200 * 61 * 3))
+    with m.Batch(probs, rounds_per_launch=2) as b:
+        b.run()
+        res = b.results()
+        check_oracle(probs, res)
+        assert all(r["rounds"] <= 2 for r in res[:4])
+    budget_only = [p for p in CLASS_PROBS[:6]]
+    with m.Batch(budget_only, use_graph=True, autotune=True) as b:
+        for _ in range(2):
+            b.run()
+            check_oracle(budget_only, b.results())

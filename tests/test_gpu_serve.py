@@ -150,3 +150,33 @@ def test_probability_target_sets_the_budget(m):
                                            rel=1e-9, abs=1.0)
             assert r["evals"] >= budget and r["p_optimal"] >= P
             check(m, (L, w, wl, seed, budget), r)
+
+
+def test_served_results_match_oracle_every_class(m):
+    # a mixed submission across the lag-word classes W = 1..5 (L = 61, 121, 161,
+    # 223, 301), with budgets over several rounds and one target request; every
+    # result is compared with the oracle's Algorithm 1 + Algorithm 2 directly
+    import oracle
+    D = lambda L: (L + 1) // 2
+    reqs = [
+        (61, 40, 160, 301, 40 * 160 * 31 * 3),
+        (121, 50, 150, 302, 50 * 150 * 61 * 2),
+        (161, 33, 120, 303, 33 * 120 * 81 * 3),
+        (223, 40, 110, 304, 40 * 110 * 112 * 2),
+        (301, 32, 100, 305, 32 * 100 * 151 * 2),
+    ]
+    o = oracle.solve(161, [306], 32, 120, 32 * 120 * 81 * 2, threads=8)
+    reqs.append((161, 32, 120, 306, 10 ** 12, int(o["best_E"][0])))  # stops within two rounds
+    with m.Server(max_walks=64, rounds_per_launch=2) as sv:
+        tickets = [sv.submit(*p) for p in reqs]
+        results = [sv.wait(t) for t in tickets]
+    for p, r in zip(reqs, results):
+        L, walks, wl, seed, budget = p[:5]
+        tgt = p[5] if len(p) > 5 else -1
+        w = oracle.solve(L, [seed], walks, wl, budget, target_E=tgt, threads=8)
+        assert r["status"] == m.LABS_OK
+        assert r["best_E"] == int(w["best_E"][0]), (p, r["best_E"], int(w["best_E"][0]))
+        assert np.array_equal(r["best_seq"], w["best_seq"][0]), p
+        assert r["evals"] == int(w["evals"][0]) and r["rounds"] == int(w["rounds"][0]), p
+        if tgt >= 0:
+            assert r["reached_target"] == 1 and r["rounds"] <= 2

@@ -34,7 +34,9 @@ def run_noalloc(m, L, seed, rnd, n, wl):
 
 
 def test_noalloc_round_matches_allocating_round_on_consecutive_calls(m):
-    cases = [(27, 1, 0, 64, 4096), (121, 7, 3, 100, 1500), (27, 1, 0, 64, 4096)]
+    # lag-word classes 1, 2 and 7 (L = 27, 121, 449); the third and last calls
+    # reuse a scratch that an earlier, different round left filled
+    cases = [(27, 1, 0, 64, 4096), (121, 7, 3, 100, 1500), (449, 5, 2, 40, 600), (27, 1, 0, 64, 4096)]
     for L, seed, rnd, n, wl in cases:
         E, S, mv, sk = run_noalloc(m, L, seed, rnd, n, wl)
         ref = m.labs_saw_round(L, seed, rnd, n, wl)
@@ -55,3 +57,25 @@ def test_noalloc_rejects_rounds_larger_than_its_scratch(m):
     E2, S2, _, _ = run_noalloc(m, 27, 2, 0, 8, 300)
     ref = m.labs_saw_round(27, 2, 0, 8, 300)
     assert np.array_equal(E2, ref["best_E"]) and np.array_equal(S2, ref["best_seq"])
+
+
+def test_noalloc_binding_rejects_bad_buffers(m):
+    # the binding refuses buffers the library would write out of bounds
+    import torch
+    n, L = 8, 27
+    good_E = torch.zeros(n, dtype=torch.int64, device="cuda")
+    good_S = torch.zeros((n, L), dtype=torch.int8, device="cuda")
+    bad = [
+        (torch.zeros(n, dtype=torch.int32, device="cuda"), good_S),   # wrong dtype
+        (torch.zeros(n - 1, dtype=torch.int64, device="cuda"), good_S),  # too short
+        (torch.zeros(n, dtype=torch.int64), good_S),                   # host tensor
+        (good_E, torch.zeros((L, n), dtype=torch.int8, device="cuda").t()),  # not contiguous
+        (good_E, None),
+    ]
+    for E, S in bad:
+        with pytest.raises(m.LabsError) as ei:
+            m.labs_saw_round_noalloc(L, 1, 0, n, 100, E, S)
+        assert ei.value.status == m.LABS_EINVAL
+    E, S, mv, sk = run_noalloc(m, L, 3, 0, n, 100)
+    ref = m.labs_saw_round(L, 3, 0, n, 100)
+    assert np.array_equal(E, ref["best_E"]) and np.array_equal(S, ref["best_seq"])
