@@ -628,7 +628,7 @@ def main():
     ap.add_argument("--target-budget", type=int, default=2 * 10 ** 9)
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--mem-gib", type=int, default=16)
-    ap.add_argument("--rounds-per-launch", type=int, default=8)
+    ap.add_argument("--rounds-per-launch", type=int, default=4)
     ap.add_argument("--plain-requests", type=int, default=10)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)

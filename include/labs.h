@@ -221,6 +221,9 @@ labs_status labs_batch_run(labs_batch *b, labs_stats *stats);
  * best_seq[L], best_E, evaluations, rounds.  LABS_PENDING before a run. */
 labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t *best_seq, int64_t *best_E, uint64_t *evals,
                               int32_t *rounds);
+/* Work accounting of problem i of the last run: the digit planes its
+ * neighbourhood scans used, summed over the walk steps of its rounds. */
+labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, uint64_t *plane_steps);
 /* Launch shape chosen for class W: walks per CTA, table factor x 10, walks resident at once. */
 labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads, int32_t *table_factor_x10,
                              int32_t *resident_walks);
@@ -229,21 +232,29 @@ labs_status labs_batch_destroy(labs_batch *b);
 /* ---------------------------------------------------------------- serving
  * A server takes solve requests (one labs_problem each) at any time and runs
  * them with continuous batching: a scheduler thread admits queued requests in
- * arrival order while a slot is free and the memory budget holds their
- * working set, runs every admitted request's next rounds together in the
- * persistent batch kernels, hands back finished requests and admits new ones
- * at the next launch boundary.  A request's result is exactly what labs_walks
- * gives for it alone.  Thread-safe: any host thread may submit, poll or wait;
- * destroy must not overlap other calls on the same server. */
+ * arrival order while a slot is free and a launch over every admitted request
+ * fits half of the device arena, and keeps two launches of the persistent
+ * batch kernels in flight (the next queued while one runs), each giving every
+ * admitted request its next rounds.  The kernels finalize each request's
+ * rounds in order as they complete and skip the rounds issued past its stop.
+ * After each launch the scheduler hands back finished requests and admits new
+ * ones.  A request's result is exactly what labs_walks gives for it alone.
+ * Thread-safe: any host thread may submit, poll or wait; destroy must not
+ * overlap other calls on the same server. */
 typedef struct labs_serve_cfg {
-  void *stream;              /* cudaStream_t for the server's work; NULL = its own stream */
-  size_t mem_bytes;          /* admission budget: sum over admitted requests of
-                                walks x visited-table bytes + round state (default 8 GiB) */
+  void *stream;              /* cudaStream_t whose queued work the server's first launch follows
+                                (NULL = the legacy default stream); the server runs on streams
+                                of its own */
+  size_t mem_bytes;          /* device arena, allocated at create, for the visited tables and
+                                task lists of the launches (two in flight, each in one half);
+                                a request is admitted only while one launch over every
+                                admitted request fits in half of it (default 8 GiB) */
   int32_t max_active;        /* requests admitted at once (slots), default 64 */
   int32_t max_L;             /* largest L accepted (sizes the table pools), default 301 */
   int32_t max_walks;         /* largest walks per round accepted, default 2048 */
   int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
-  int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 8 */
+  int32_t rounds_per_launch; /* rounds each admitted request gets per launch at most, default 4
+                                (two launches are in flight: the next is queued while one runs) */
   int32_t block_threads;     /* walks per CTA of the batch kernels, default 128 */
 } labs_serve_cfg;
 
@@ -260,6 +271,8 @@ typedef struct labs_result {
   double p_optimal;          /* Eq. 7 for the request's evaluations: the predictive
                                 model's probability that best_E is optimal
                                 (labs_model_p_optimal of labs_model_nses_of_evals) */
+  uint64_t plane_steps;      /* digit planes the neighbourhood scans used, summed over the
+                                walk steps of the request's rounds (work accounting) */
 } labs_result;
 
 typedef struct labs_serve_stats {
@@ -267,25 +280,27 @@ typedef struct labs_serve_stats {
   uint64_t evals;            /* neighbour evaluations done so far */
   uint64_t launches, walk_launches;
   double busy_ms;            /* device time of the launches (CUDA events) */
-  uint64_t mem_used;         /* admission budget in use */
+  uint64_t mem_used;         /* arena bytes a launch over the admitted requests needs */
   int32_t status;            /* LABS_OK, or the error that stopped the server */
   int32_t reserved;
   uint64_t evals_run;        /* neighbour evaluations the device ran, including rounds run
                                 speculatively past a request's stop (evals counts only the
                                 rounds up to each stop) */
+  uint64_t mem_peak;         /* largest share of the arena one launch used (<= mem_bytes / 2) */
+  uint64_t fixed_bytes;      /* device bytes of the per-slot state, outside the arena */
 } labs_serve_stats;
 
 typedef struct labs_server labs_server; /* opaque */
 
 /* Defaults: mem_bytes 8 GiB, max_active 64, max_L 301, max_walks 2048,
- * max_walk_len 8 * (max_L + 1) / 2, rounds_per_launch 8, block_threads 128. */
+ * max_walk_len 8 * (max_L + 1) / 2, rounds_per_launch 4, block_threads 128. */
 void labs_serve_cfg_init(labs_serve_cfg *cfg);
-/* Allocate the server (visited-table pools for every lag-word class up to
- * max_L) and start its scheduler thread on the current device. */
+/* Allocate the server (its per-slot state and round records, and the arena
+ * of mem_bytes) and start its scheduler thread on the current device. */
 labs_status labs_serve_create(const labs_serve_cfg *cfg, labs_server **out);
 /* Queue a request; never blocks on the GPU.  LABS_EINVAL for a bad problem,
  * LABS_ENOMEM if it can never be admitted (L, walks or walk length above the
- * server's limits, or a working set above mem_bytes), LABS_ESHUTDOWN while
+ * server's limits, or a launch over it alone would not fit half of mem_bytes), LABS_ESHUTDOWN while
  * destroying, or the error that stopped the server. */
 labs_status labs_serve_submit(labs_server *s, const labs_problem *req, uint64_t *ticket);
 /* LABS_PENDING while the request runs; otherwise fills *out (and best_seq[L]

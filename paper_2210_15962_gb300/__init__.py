@@ -119,6 +119,7 @@ class labs_result(ctypes.Structure):
         ("t_admit_ns", ctypes.c_uint64),
         ("t_done_ns", ctypes.c_uint64),
         ("p_optimal", ctypes.c_double),
+        ("plane_steps", ctypes.c_uint64),
     ]
 
 
@@ -136,6 +137,8 @@ class labs_serve_stats(ctypes.Structure):
         ("status", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("evals_run", ctypes.c_uint64),
+        ("mem_peak", ctypes.c_uint64),
+        ("fixed_bytes", ctypes.c_uint64),
     ]
 
 
@@ -165,6 +168,7 @@ _EXPORTS = {
     "labs_batch_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(labs_stats)]),
     "labs_batch_result": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "labs_batch_plane_steps": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "labs_batch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "labs_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
@@ -467,7 +471,10 @@ class Batch:
         ev = np.zeros(1, dtype=np.uint64)
         rd = np.zeros(1, dtype=np.int32)
         _check(load().labs_batch_result(self._h, i, _ptr(seq), _ptr(E), _ptr(ev), _ptr(rd)), "labs_batch_result")
-        return {"best_seq": seq, "best_E": int(E[0]), "evals": int(ev[0]), "rounds": int(rd[0])}
+        ps = np.zeros(1, dtype=np.uint64)
+        _check(load().labs_batch_plane_steps(self._h, i, _ptr(ps)), "labs_batch_plane_steps")
+        return {"best_seq": seq, "best_E": int(E[0]), "evals": int(ev[0]), "rounds": int(rd[0]),
+                "plane_steps": int(ps[0])}
 
     def results(self) -> list:
         return [self.result(i) for i in range(len(self.problems))]

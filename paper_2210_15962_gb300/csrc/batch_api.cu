@@ -1,8 +1,9 @@
 // Host side of the batched entry points (include/labs.h, labs_batch_*):
 // many independent problems of uneven L solved together by the persistent
-// batch kernel, launch after launch, with the launch sequence captured once as
-// a CUDA graph when the plan is fixed in advance, and launch shapes (walks per
-// CTA, visited-table capacity) chosen by timing candidates on a sample.
+// batch kernel, launch after launch, with the first launch sequence captured
+// once as a CUDA graph when the plan is fixed in advance, and launch shapes
+// (walks per CTA, visited-table capacity) chosen by timing candidates on a
+// sample.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +20,8 @@
 namespace psaw {
 namespace {
 
+constexpr uint32_t kMaxRingRounds = 64;  // rounds of one problem issued in one launch at most
+
 bool valid_problem(const labs_problem &p) {
   return p.L >= LABS_L_MIN && p.L <= LABS_L_MAX && (p.L & 1) && p.walks >= 1 && p.walks <= (1 << 24) &&
          p.walk_len >= 1 && p.walk_len <= (1 << 26) && p.step_budget >= 1;
@@ -34,7 +37,7 @@ cudaError_t dalloc(T **p, size_t n) {
 struct ClassPlan {
   int W = 0;
   int block = 128;
-  int factor_x10 = 15;
+  int factor_x10 = kTableFactorX10;
   std::vector<int> probs;  // problem indices of this class
   size_t pool_words = 0;
   int resident = 0;
@@ -62,6 +65,17 @@ int ilog2(uint64_t x) {
   return r;
 }
 
+uint64_t full_round_evals(const labs_problem &p) {
+  return (uint64_t)p.walks * (uint64_t)p.walk_len * (uint64_t)((p.L + 1) / 2);
+}
+
+// Rounds a problem still needs for its budget, given the evaluations done.
+uint64_t rounds_needed(const labs_problem &p, uint64_t evals_done) {
+  const uint64_t fr = full_round_evals(p);
+  const uint64_t rem = p.step_budget > evals_done ? p.step_budget - evals_done : 0;
+  return std::max<uint64_t>(1, (rem + fr - 1) / fr);
+}
+
 }  // namespace
 }  // namespace psaw
 
@@ -75,38 +89,38 @@ struct labs_batch {
   bool own_stream = false;
   bool use_graph = false;
   int rounds_per_launch = 4;
-  // device state
+  // per-problem device state, one allocation
+  void *state_block = nullptr;
   BatchProblem *d_probs = nullptr;
-  uint64_t *d_budget = nullptr;
-  int64_t *d_target = nullptr;
-  int32_t *d_done = nullptr, *d_best_round = nullptr, *d_best_walk = nullptr, *d_rounds = nullptr;
-  int64_t *d_bestE = nullptr;
-  uint32_t *d_key = nullptr;
-  unsigned long long *d_evals = nullptr;
-  int8_t *d_seq = nullptr;
-  size_t seq_total = 0;
-  std::vector<size_t> seq_off;
-  // slots of the current launch
-  size_t slots_cap = 0;
-  uint32_t max_chunks = 1;
-  unsigned long long *d_slot_best = nullptr, *d_slot_evals = nullptr;
-  uint32_t *d_slot_keys = nullptr, *d_slot_round = nullptr;
-  uint32_t *d_first_slot = nullptr, *d_n_slots = nullptr;
+  ProblemState ps{};
+  uint32_t *d_rec_base = nullptr, *d_ring = nullptr;
+  int32_t *d_all = nullptr;  // 0 .. n-1
+  std::vector<uint32_t> rec_base, ring;
+  // round records (one ring per problem, plus one record the autotuner's sample uses)
+  void *rec_block = nullptr;
+  RoundRecords rec{};
+  uint32_t n_records = 0, tune_record = 0;
+  // per launch
+  RecordInit *d_issue = nullptr;
+  size_t issue_cap = 0;
+  int n_issue = 0;
   unsigned int *d_task_next = nullptr;  // one counter per class
-  unsigned long long *d_planes = nullptr;
-  unsigned long long *d_rb_scratch = nullptr;  // per problem, for the state reset kernel
   int32_t *d_err = nullptr;
+  // read back after every launch, one block: done, rounds, best E, evals, planes, sequences
+  char *d_snap = nullptr;
+  size_t snap_bytes = 0;
+  Snapshot snap{};
+  int seq_stride = 0;  // the largest L
+  std::vector<char> h_snap;
   // host mirrors of the last run
   std::vector<int64_t> h_bestE;
-  std::vector<unsigned long long> h_evals;
+  std::vector<unsigned long long> h_evals, h_planes;
   std::vector<int32_t> h_rounds, h_done;
   std::vector<int8_t> h_seq;
   bool have_results = false;
   // graph of the first launch plan (problems without targets)
   cudaGraphExec_t graph = nullptr;
-  bool graph_plan_built = false;
   int launches_per_graph = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> graph_events;
   // one stream per class so the classes' persistent kernels overlap (each
   // class's tail runs beside the next class's work)
   std::vector<cudaStream_t> cs;
@@ -121,35 +135,16 @@ labs_batch::~labs_batch() {
   for (auto x : cs) cudaStreamDestroy(x);
   for (auto e : cs_done) cudaEventDestroy(e);
   if (fork) cudaEventDestroy(fork);
-  for (auto &pe : graph_events) {
-    cudaEventDestroy(pe.first);
-    cudaEventDestroy(pe.second);
-  }
   for (auto &c : cls) {
     cudaFree(c.pool);
     cudaFree(c.tasks);
   }
-  cudaFree(d_probs);
-  cudaFree(d_budget);
-  cudaFree(d_target);
-  cudaFree(d_done);
-  cudaFree(d_best_round);
-  cudaFree(d_best_walk);
-  cudaFree(d_rounds);
-  cudaFree(d_bestE);
-  cudaFree(d_key);
-  cudaFree(d_evals);
-  cudaFree(d_seq);
-  cudaFree(d_slot_best);
-  cudaFree(d_slot_evals);
-  cudaFree(d_slot_keys);
-  cudaFree(d_slot_round);
-  cudaFree(d_first_slot);
-  cudaFree(d_n_slots);
+  cudaFree(state_block);
+  cudaFree(rec_block);
+  cudaFree(d_issue);
   cudaFree(d_task_next);
-  cudaFree(d_planes);
-  cudaFree(d_rb_scratch);
   cudaFree(d_err);
+  cudaFree(d_snap);
   if (own_stream && s) cudaStreamDestroy(s);
 }
 
@@ -167,15 +162,10 @@ labs_status cu(cudaError_t e) {
     if (st_ != LABS_OK) return st_;       \
   } while (0)
 
-uint64_t full_round_evals(const labs_problem &p) {
-  return (uint64_t)p.walks * (uint64_t)p.walk_len * (uint64_t)((p.L + 1) / 2);
-}
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// relative cost of one task (32 walks): steps x flips x lag words
-double task_cost(const labs_problem &p) {
-  const int D = (p.L + 1) / 2;
-  return (double)p.walk_len * D * (double)lag_words(p.L);
-}
+double task_cost(const labs_problem &p) { return batch_task_cost(p.L, p.walk_len); }
 
 BatchKernelParams kernel_params(labs_batch *b, ClassPlan &c, int ci) {
   BatchKernelParams k{};
@@ -185,17 +175,13 @@ BatchKernelParams kernel_params(labs_batch *b, ClassPlan &c, int ci) {
   k.task_next = b->d_task_next + ci;
   k.pool = c.pool;
   k.pool_words = c.pool_words;
-  k.slot_best = b->d_slot_best;
-  k.slot_evals = b->d_slot_evals;
-  k.slot_keys = b->d_slot_keys;
-  k.max_chunks = b->max_chunks;
-  k.done = b->d_done;
+  k.rec = b->rec;
+  k.ps = b->ps;
   k.mul_one = 1u;
   k.mul_two = 2u;
   k.mul_four = 4u;
   k.mul_h31 = 0x80000000u;
   k.mul_h30 = 0x40000000u;
-  k.plane_steps = b->d_planes;
   k.err = b->d_err;
   return k;
 }
@@ -234,87 +220,67 @@ labs_status build_pools(labs_batch *b) {
   return LABS_OK;
 }
 
-labs_status ensure_slots(labs_batch *b, size_t n_slots) {
-  if (n_slots <= b->slots_cap) return LABS_OK;
-  cudaFree(b->d_slot_best);
-  cudaFree(b->d_slot_evals);
-  cudaFree(b->d_slot_keys);
-  cudaFree(b->d_slot_round);
-  b->slots_cap = std::max(n_slots, b->slots_cap * 2);
-  BCU(dalloc(&b->d_slot_best, b->slots_cap));
-  BCU(dalloc(&b->d_slot_evals, b->slots_cap));
-  BCU(dalloc(&b->d_slot_keys, b->slots_cap * b->max_chunks * kKeyWords));
-  BCU(dalloc(&b->d_slot_round, b->slots_cap));
-  return LABS_OK;
-}
-
-// Plan one launch: rounds per problem (all the budget still needs, or at most
-// rounds_per_launch for problems with a target), slots in round order, and
-// each class's tasks sorted by decreasing cost (longest first).
+// Plan one launch from the host's view of each problem (done, rounds
+// finalized, evaluations): the rounds each unfinished problem runs (what its
+// budget still needs, at most its ring, and at most rounds_per_launch for a
+// problem with a target), their records, and each class's tasks in launch
+// order (order_tasks).
 labs_status plan_launch(labs_batch *b, const std::vector<int32_t> &next_round, const std::vector<int32_t> &done,
-                        const std::vector<unsigned long long> &evals, size_t *n_slots_out) {
+                        const std::vector<unsigned long long> &evals) {
   const size_t n = b->pr.size();
-  std::vector<uint32_t> first(n, 0), cnt(n, 0), slot_round;
-  size_t slots = 0;
-  for (size_t i = 0; i < n; ++i) {
-    if (done[i]) continue;
-    const labs_problem &p = b->pr[i];
-    const uint64_t fr = full_round_evals(p);
-    const uint64_t rem = p.step_budget > evals[i] ? p.step_budget - evals[i] : 0;
-    uint64_t r = rem == 0 ? 1 : (rem + fr - 1) / fr;
-    if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
-    r = std::max<uint64_t>(r, 1);
-    first[i] = (uint32_t)slots;
-    cnt[i] = (uint32_t)r;
-    for (uint64_t k = 0; k < r; ++k) slot_round.push_back((uint32_t)(next_round[i] + k));
-    slots += r;
+  std::vector<RecordInit> issue;
+  std::vector<std::vector<PlannedTask>> tk(b->cls.size());
+  for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+    for (int i : b->cls[ci].probs) {
+      if (done[i]) continue;
+      const labs_problem &p = b->pr[i];
+      uint64_t r = std::min<uint64_t>(rounds_needed(p, evals[i]), b->ring[i]);
+      if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
+      const uint32_t chunks = (uint32_t)((p.walks + 31) / 32);
+      const double cost = task_cost(p);
+      for (uint32_t k = 0; k < (uint32_t)r; ++k) {
+        const uint32_t round = (uint32_t)next_round[i] + k;
+        const uint32_t rec = b->rec_base[i] + round % b->ring[i];
+        issue.push_back(RecordInit{rec, round, chunks});
+        for (uint32_t ch = 0; ch < chunks; ++ch)
+          tk[ci].push_back({p.target_E >= 0 ? k : 0u, cost, BatchTask{(uint32_t)i, round, ch, rec}});
+      }
+    }
   }
-  labs_status st = ensure_slots(b, slots);
-  if (st != LABS_OK) return st;
+  (void)n;
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
     ClassPlan &c = b->cls[ci];
-    std::vector<std::pair<double, BatchTask>> tk;
-    for (int i : c.probs) {
-      if (done[i]) continue;
-      const uint32_t chunks = (uint32_t)((b->pr[i].walks + 31) / 32);
-      const double cost = task_cost(b->pr[i]);
-      for (uint32_t k = 0; k < cnt[i]; ++k)
-        for (uint32_t ch = 0; ch < chunks; ++ch)
-          tk.push_back({cost, BatchTask{(uint32_t)i, slot_round[first[i] + k], ch, first[i] + k}});
-    }
-    using Costed = std::pair<double, BatchTask>;
-    std::stable_sort(tk.begin(), tk.end(), [](const Costed &x, const Costed &y) {
-      if (x.first != y.first) return x.first > y.first;
-      return std::tie(x.second.round, x.second.problem, x.second.chunk) <
-             std::tie(y.second.round, y.second.problem, y.second.chunk);
-    });
-    if (tk.size() > c.tasks_cap) {
+    order_tasks(tk[ci]);
+    if (tk[ci].size() > c.tasks_cap) {
       cudaFree(c.tasks);
-      c.tasks_cap = std::max(tk.size(), 2 * c.tasks_cap);
+      c.tasks_cap = std::max(tk[ci].size(), 2 * c.tasks_cap);
       BCU(dalloc(&c.tasks, c.tasks_cap));
     }
-    std::vector<BatchTask> flat(tk.size());
-    for (size_t j = 0; j < tk.size(); ++j) flat[j] = tk[j].second;
+    std::vector<BatchTask> flat(tk[ci].size());
+    for (size_t j = 0; j < flat.size(); ++j) flat[j] = tk[ci][j].t;
     c.n_tasks = (uint32_t)flat.size();
     if (!flat.empty()) BCU(cudaMemcpy(c.tasks, flat.data(), sizeof(BatchTask) * flat.size(), cudaMemcpyHostToDevice));
   }
-  if (slots) BCU(cudaMemcpy(b->d_slot_round, slot_round.data(), sizeof(uint32_t) * slots, cudaMemcpyHostToDevice));
-  BCU(cudaMemcpy(b->d_first_slot, first.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
-  BCU(cudaMemcpy(b->d_n_slots, cnt.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
-  *n_slots_out = slots;
+  if (issue.size() > b->issue_cap) {
+    cudaFree(b->d_issue);
+    b->issue_cap = std::max(issue.size(), 2 * b->issue_cap);
+    BCU(dalloc(&b->d_issue, b->issue_cap));
+  }
+  b->n_issue = (int)issue.size();
+  if (!issue.empty())
+    BCU(cudaMemcpy(b->d_issue, issue.data(), sizeof(RecordInit) * issue.size(), cudaMemcpyHostToDevice));
   return LABS_OK;
 }
 
-// Enqueue one planned launch: reset the slot accumulators and task counters,
-// the persistent kernel of each class, then the in-order finalize.
-labs_status enqueue_launch(labs_batch *b, size_t n_slots, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev,
-                           int *launches) {
-  if (n_slots) {
-    BCU(cudaMemsetAsync(b->d_slot_best, 0xFF, sizeof(unsigned long long) * n_slots, b->s));
-    BCU(cudaMemsetAsync(b->d_slot_evals, 0, sizeof(unsigned long long) * n_slots, b->s));
-  }
+// Enqueue one planned launch: the new rounds' records, the persistent kernel
+// of each class on its own stream, the finalization of anything the kernels
+// left, and the snapshot of every problem.
+labs_status enqueue_launch(labs_batch *b, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *ev, int *launches) {
+  const int n = (int)b->pr.size();
+  BCU(launch_issue_records(b->d_issue, b->n_issue, b->rec, b->s));
   BCU(cudaMemsetAsync(b->d_task_next, 0, sizeof(unsigned int) * b->cls.size(), b->s));
-  // fork: every class's kernel on its own stream after the resets, join before the finalize
+  ++*launches;
+  // fork: every class's kernel on its own stream, join before the finalize
   BCU(cudaEventRecord(b->fork, b->s));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ev) {
@@ -337,49 +303,22 @@ labs_status enqueue_launch(labs_batch *b, size_t n_slots, std::vector<std::pair<
     BCU(cudaEventRecord(e1, b->s));
     ev->push_back({e0, e1});
   }
-  BatchFinalizeParams f{};
-  f.n_problems = (int32_t)b->pr.size();
-  f.first_slot = b->d_first_slot;
-  f.n_slots = b->d_n_slots;
-  f.slot_round = b->d_slot_round;
-  f.slot_best = b->d_slot_best;
-  f.slot_evals = b->d_slot_evals;
-  f.slot_keys = b->d_slot_keys;
-  f.max_chunks = b->max_chunks;
-  f.budget = b->d_budget;
-  f.target = b->d_target;
-  f.done = b->d_done;
-  f.bestE = b->d_bestE;
-  f.key = b->d_key;
-  f.best_round = b->d_best_round;
-  f.best_walk = b->d_best_walk;
-  f.evals = b->d_evals;
-  f.rounds = b->d_rounds;
-  BCU(launch_batch_finalize(f, b->s));
-  ++*launches;
+  BCU(launch_batch_finalize(b->d_all, n, b->rec, b->ps, b->s));
+  BCU(launch_snapshot(b->d_all, n, b->d_probs, b->ps, nullptr, 0, b->rec, b->snap, b->s));
+  *launches += 2;
   return LABS_OK;
 }
 
 labs_status reset_state(labs_batch *b, int *launches) {
-  const int n = (int)b->pr.size();
-  BCU(launch_init_problems(n, b->d_bestE, b->d_evals, b->d_rb_scratch, b->d_done, b->d_rounds, b->d_best_round,
-                           b->d_best_walk, b->d_key, b->s));
+  BCU(launch_init_problems_state(b->d_all, (int)b->pr.size(), b->rec, b->ps, b->s));
   BCU(cudaMemsetAsync(b->d_err, 0, sizeof(int32_t), b->s));
-  BCU(cudaMemsetAsync(b->d_planes, 0, sizeof(unsigned long long), b->s));
   ++*launches;
   return LABS_OK;
 }
 
-labs_status expand_results(labs_batch *b, int *launches) {
-  for (size_t i = 0; i < b->pr.size(); ++i) {
-    BCU(launch_expand(1, b->pr[i].L, b->d_key + i * kKeyWords, kKeyWords, b->d_seq + b->seq_off[i], b->s));
-    ++*launches;
-  }
-  return LABS_OK;
-}
-
 // Time candidate shapes (walks per CTA x table capacity) of one class on a
-// sample of its round-0 tasks with walks shortened to at most 256 steps.
+// sample of its tasks (rounds no solve uses) with walks shortened to at most
+// 256 steps; the sample's tasks all count into one record that never completes.
 labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   int max_len = 0, max_walks = 0;
   for (int i : c.probs) {
@@ -400,40 +339,34 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   const int factors[] = {15, 30};
   float best_ms = 1e30f;
   int best_block = c.block, best_factor = c.factor_x10;
-  // sample problems: the class's problems with short walks, round 0
   std::vector<labs_problem> saved = b->pr;
   for (int i : c.probs) b->pr[i].walk_len = std::min(b->pr[i].walk_len, 256);
+  auto restore = [&](labs_status st) {
+    b->pr = saved;
+    return st;
+  };
   for (int fct : factors) {
     for (int blk : blocks) {
       c.block = blk;
       c.factor_x10 = fct;
       labs_status st = build_pools(b);
-      if (st != LABS_OK) {
-        b->pr = saved;
-        return st;
-      }
+      if (st != LABS_OK) return restore(st);
       // one wave of tasks
       std::vector<BatchTask> tk;
       const size_t want = (size_t)std::max(1, c.resident / 32);
       for (size_t k = 0; tk.size() < want && k < 4 * want; ++k) {
         const int i = c.probs[k % c.probs.size()];
         const uint32_t chunks = (uint32_t)((b->pr[i].walks + 31) / 32);
-        tk.push_back(BatchTask{(uint32_t)i, 1000u + (uint32_t)(k / c.probs.size()), (uint32_t)(k % chunks), 0u});
-      }
-      st = ensure_slots(b, 1);
-      if (st != LABS_OK) {
-        b->pr = saved;
-        return st;
+        tk.push_back(BatchTask{(uint32_t)i, 1000u + (uint32_t)(k / c.probs.size()), (uint32_t)(k % chunks),
+                               b->tune_record});
       }
       if (tk.size() > c.tasks_cap) {
         cudaFree(c.tasks);
         c.tasks_cap = tk.size();
-        if (dalloc(&c.tasks, c.tasks_cap) != cudaSuccess) {
-          b->pr = saved;
-          return LABS_ENOMEM;
-        }
+        if (dalloc(&c.tasks, c.tasks_cap) != cudaSuccess) return restore(LABS_ENOMEM);
       }
-      cudaMemcpy(c.tasks, tk.data(), sizeof(BatchTask) * tk.size(), cudaMemcpyHostToDevice);
+      if (cudaMemcpy(c.tasks, tk.data(), sizeof(BatchTask) * tk.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return restore(LABS_ECUDA);
       c.n_tasks = (uint32_t)tk.size();
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
@@ -441,7 +374,7 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
         cudaMemsetAsync(b->d_task_next + ci, 0, sizeof(unsigned int), b->s);
-        cudaMemsetAsync(b->d_slot_best, 0xFF, sizeof(unsigned long long), b->s);
+        cudaMemsetAsync(b->rec.left + b->tune_record, 0xFF, sizeof(uint32_t), b->s);
         cudaEventRecord(e0, b->s);
         launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr);
         cudaEventRecord(e1, b->s);
@@ -450,10 +383,7 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      if (cudaGetLastError() != cudaSuccess) {
-        b->pr = saved;
-        return LABS_ECUDA;
-      }
+      if (cudaGetLastError() != cudaSuccess) return restore(LABS_ECUDA);
       if (ms < best_ms) {
         best_ms = ms;
         best_block = blk;
@@ -470,6 +400,114 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   return LABS_OK;
 }
 
+// Device memory of the per-problem state, the round records and the snapshot.
+labs_status alloc_state(labs_batch *b) {
+  const size_t n = b->pr.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t o_probs = take(sizeof(BatchProblem) * n), o_budget = take(sizeof(uint64_t) * n),
+               o_target = take(sizeof(int64_t) * n), o_base = take(sizeof(uint32_t) * n),
+               o_ring = take(sizeof(uint32_t) * n), o_fin = take(sizeof(uint32_t) * n),
+               o_done = take(sizeof(int32_t) * n), o_bestE = take(sizeof(int64_t) * n),
+               o_key = take(sizeof(uint32_t) * kKeyWords * n), o_brnd = take(sizeof(int32_t) * n),
+               o_bwalk = take(sizeof(int32_t) * n), o_evals = take(sizeof(unsigned long long) * n),
+               o_planes = take(sizeof(unsigned long long) * n), o_rounds = take(sizeof(int32_t) * n),
+               o_all = take(sizeof(int32_t) * n);
+  char *sb = nullptr;
+  BCU(cudaMalloc((void **)&sb, off));
+  b->state_block = sb;
+  b->d_probs = reinterpret_cast<BatchProblem *>(sb + o_probs);
+  b->d_rec_base = reinterpret_cast<uint32_t *>(sb + o_base);
+  b->d_ring = reinterpret_cast<uint32_t *>(sb + o_ring);
+  b->d_all = reinterpret_cast<int32_t *>(sb + o_all);
+  ProblemState &ps = b->ps;
+  ps.rec_base = b->d_rec_base;
+  ps.ring = b->d_ring;
+  ps.budget = reinterpret_cast<uint64_t *>(sb + o_budget);
+  ps.target = reinterpret_cast<int64_t *>(sb + o_target);
+  ps.fin = reinterpret_cast<uint32_t *>(sb + o_fin);
+  ps.done = reinterpret_cast<int32_t *>(sb + o_done);
+  ps.bestE = reinterpret_cast<int64_t *>(sb + o_bestE);
+  ps.key = reinterpret_cast<uint32_t *>(sb + o_key);
+  ps.best_round = reinterpret_cast<int32_t *>(sb + o_brnd);
+  ps.best_walk = reinterpret_cast<int32_t *>(sb + o_bwalk);
+  ps.evals = reinterpret_cast<unsigned long long *>(sb + o_evals);
+  ps.planes = reinterpret_cast<unsigned long long *>(sb + o_planes);
+  ps.rounds = reinterpret_cast<int32_t *>(sb + o_rounds);
+  std::vector<uint64_t> bud(n);
+  std::vector<int64_t> tgt(n);
+  std::vector<int32_t> all(n);
+  for (size_t i = 0; i < n; ++i) {
+    bud[i] = b->pr[i].step_budget;
+    tgt[i] = b->pr[i].target_E;
+    all[i] = (int32_t)i;
+  }
+  BCU(cudaMemset(sb, 0, off));
+  BCU(cudaMemcpy(sb + o_budget, bud.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(sb + o_target, tgt.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(sb + o_base, b->rec_base.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(sb + o_ring, b->ring.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(sb + o_all, all.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+  // records: the problems' rings and the autotuner's record
+  const size_t nr = (size_t)b->n_records + 1;
+  off = 0;
+  const size_t r_best = take(sizeof(unsigned long long) * nr), r_evals = take(sizeof(unsigned long long) * nr),
+               r_planes = take(sizeof(unsigned long long) * nr), r_left = take(sizeof(uint32_t) * nr),
+               r_round = take(sizeof(uint32_t) * nr),
+               r_keys = take(sizeof(uint32_t) * kKeyWords * nr * b->rec.max_chunks);
+  char *rb = nullptr;
+  BCU(cudaMalloc((void **)&rb, off));
+  b->rec_block = rb;
+  BCU(cudaMemset(rb, 0, off));
+  BCU(cudaMemset(rb + r_round, 0xFF, sizeof(uint32_t) * nr));
+  b->rec.best = reinterpret_cast<unsigned long long *>(rb + r_best);
+  b->rec.evals = reinterpret_cast<unsigned long long *>(rb + r_evals);
+  b->rec.planes = reinterpret_cast<unsigned long long *>(rb + r_planes);
+  b->rec.left = reinterpret_cast<uint32_t *>(rb + r_left);
+  b->rec.round = reinterpret_cast<uint32_t *>(rb + r_round);
+  b->rec.keys = reinterpret_cast<uint32_t *>(rb + r_keys);
+  b->tune_record = b->n_records;
+  // the snapshot block
+  off = 0;
+  const size_t s_done = take(sizeof(int32_t) * n), s_rounds = take(sizeof(int32_t) * n),
+               s_bestE = take(sizeof(int64_t) * n), s_evals = take(sizeof(unsigned long long) * n),
+               s_planes = take(sizeof(unsigned long long) * n), s_seq = take(n * (size_t)b->seq_stride);
+  BCU(cudaMalloc((void **)&b->d_snap, off));
+  BCU(cudaMemset(b->d_snap, 0, off));
+  b->snap_bytes = off;
+  b->snap.done = reinterpret_cast<int32_t *>(b->d_snap + s_done);
+  b->snap.rounds = reinterpret_cast<int32_t *>(b->d_snap + s_rounds);
+  b->snap.bestE = reinterpret_cast<int64_t *>(b->d_snap + s_bestE);
+  b->snap.evals = reinterpret_cast<unsigned long long *>(b->d_snap + s_evals);
+  b->snap.planes = reinterpret_cast<unsigned long long *>(b->d_snap + s_planes);
+  b->snap.seq = reinterpret_cast<int8_t *>(b->d_snap + s_seq);
+  b->snap.stride = b->seq_stride;
+  b->snap.run_evals = nullptr;
+  b->h_snap.resize(off);
+  BCU(dalloc(&b->d_task_next, b->cls.size()));
+  BCU(dalloc(&b->d_err, 1));
+  BCU(cudaMemset(b->d_err, 0, sizeof(int32_t)));
+  return LABS_OK;
+}
+
+// Copy the snapshot to the host (stream-ordered, then synchronised) and
+// unpack the fields the run loop needs.
+labs_status read_snapshot(labs_batch *b, std::vector<int32_t> &done, std::vector<int32_t> &rounds,
+                          std::vector<unsigned long long> &evals) {
+  BCU(cudaMemcpyAsync(b->h_snap.data(), b->d_snap, b->snap_bytes, cudaMemcpyDeviceToHost, b->s));
+  BCU(cudaStreamSynchronize(b->s));
+  const size_t n = b->pr.size();
+  auto at = [&](const void *dev) { return b->h_snap.data() + ((const char *)dev - b->d_snap); };
+  std::memcpy(done.data(), at(b->snap.done), sizeof(int32_t) * n);
+  std::memcpy(rounds.data(), at(b->snap.rounds), sizeof(int32_t) * n);
+  std::memcpy(evals.data(), at(b->snap.evals), sizeof(unsigned long long) * n);
+  return LABS_OK;
+}
+
 }  // namespace
 }  // namespace psaw
 
@@ -482,7 +520,7 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (opts_in) opts = *opts_in;
   if (opts.block_threads < 0 || opts.block_threads > 256 || (opts.block_threads % 32) != 0 ||
       opts.table_factor_x10 < 0 || (opts.table_factor_x10 > 0 && opts.table_factor_x10 < 12) ||
-      opts.rounds_per_launch < 0)
+      opts.rounds_per_launch < 0 || opts.rounds_per_launch > (int32_t)kMaxRingRounds)
     return LABS_EINVAL;
   for (int i = 0; i < n; ++i)
     if (!valid_problem(problems[i])) return LABS_EINVAL;
@@ -505,8 +543,10 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
     delete b;
     return e;
   };
+  uint32_t max_chunks = 1;
   for (int i = 0; i < n; ++i) {
-    const int W = lag_words(problems[i].L);
+    const labs_problem &p = problems[i];
+    const int W = lag_words(p.L);
     b->W.push_back(W);
     ClassPlan *cp = nullptr;
     for (auto &c : b->cls)
@@ -516,34 +556,21 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
       cp = &b->cls.back();
       cp->W = W;
       cp->block = opts.block_threads ? opts.block_threads : 128;
-      cp->factor_x10 = opts.table_factor_x10 ? opts.table_factor_x10 : 15;
+      cp->factor_x10 = opts.table_factor_x10 ? opts.table_factor_x10 : kTableFactorX10;
     }
     cp->probs.push_back(i);
-    b->max_chunks = std::max<uint32_t>(b->max_chunks, (uint32_t)((problems[i].walks + 31) / 32));
-    b->seq_off.push_back(b->seq_total);
-    b->seq_total += (size_t)problems[i].L;
+    max_chunks = std::max<uint32_t>(max_chunks, (uint32_t)((p.walks + 31) / 32));
+    b->seq_stride = std::max(b->seq_stride, (int)p.L);
+    // the problem's ring: the rounds its first launch issues
+    uint64_t r = std::min<uint64_t>(rounds_needed(p, 0), kMaxRingRounds);
+    if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
+    b->rec_base.push_back(b->n_records);
+    b->ring.push_back((uint32_t)r);
+    b->n_records += (uint32_t)r;
   }
+  b->rec.max_chunks = max_chunks;
   std::sort(b->cls.begin(), b->cls.end(), [](const ClassPlan &x, const ClassPlan &y) { return x.W > y.W; });
-  if (cu(dalloc(&b->d_probs, n)) || cu(dalloc(&b->d_budget, n)) || cu(dalloc(&b->d_target, n)) ||
-      cu(dalloc(&b->d_done, n)) || cu(dalloc(&b->d_best_round, n)) || cu(dalloc(&b->d_best_walk, n)) ||
-      cu(dalloc(&b->d_rounds, n)) || cu(dalloc(&b->d_bestE, n)) || cu(dalloc(&b->d_key, (size_t)n * kKeyWords)) ||
-      cu(dalloc(&b->d_evals, n)) || cu(dalloc(&b->d_seq, b->seq_total)) || cu(dalloc(&b->d_first_slot, n)) ||
-      cu(dalloc(&b->d_n_slots, n)) || cu(dalloc(&b->d_task_next, b->cls.size())) || cu(dalloc(&b->d_planes, 1)) ||
-      cu(dalloc(&b->d_err, 1)) || cu(dalloc(&b->d_rb_scratch, n)))
-    return fail(LABS_ENOMEM);
-  if (cudaMemset(b->d_done, 0, sizeof(int32_t) * n) != cudaSuccess ||
-      cudaMemset(b->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
-      cudaMemset(b->d_planes, 0, sizeof(unsigned long long)) != cudaSuccess)
-    return fail(LABS_ECUDA);
-  std::vector<uint64_t> bud(n);
-  std::vector<int64_t> tgt(n);
-  for (int i = 0; i < n; ++i) {
-    bud[i] = problems[i].step_budget;
-    tgt[i] = problems[i].target_E;
-  }
-  if (cudaMemcpy(b->d_budget, bud.data(), sizeof(uint64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_target, tgt.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail(LABS_ECUDA);
+  if ((st = alloc_state(b)) != LABS_OK) return fail(st);
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
     cudaStream_t x;
     cudaEvent_t e;
@@ -579,22 +606,21 @@ extern "C" labs_status labs_batch_run(labs_batch *b, labs_stats *stats) {
   bool any_target = false;
   for (auto &p : b->pr) any_target = any_target || p.target_E >= 0;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
-  labs_status st = LABS_OK;
   BCU(cudaEventCreate(&t0));
   BCU(cudaEventCreate(&t1));
   BCU(cudaEventRecord(t0, b->s));
-  bool first = true, continued = false;
+  bool first = true;
   for (;;) {
     if (first && b->use_graph && !any_target) {
       // the first launch's plan is the same for every run: capture it once
       if (!b->graph) {
-        size_t n_slots = 0;
-        if ((st = plan_launch(b, next_round, done, evals, &n_slots)) != LABS_OK) return st;
+        labs_status st = plan_launch(b, next_round, done, evals);
+        if (st != LABS_OK) return st;
         cudaGraph_t g = nullptr;
         BCU(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
         int cl = 0;
         labs_status cst = reset_state(b, &cl);
-        if (cst == LABS_OK) cst = enqueue_launch(b, n_slots, nullptr, &cl);
+        if (cst == LABS_OK) cst = enqueue_launch(b, nullptr, &cl);
         cudaError_t ee = cudaStreamEndCapture(b->s, &g);
         if (cst != LABS_OK) {
           if (g) cudaGraphDestroy(g);
@@ -610,45 +636,36 @@ extern "C" labs_status labs_batch_run(labs_batch *b, labs_stats *stats) {
       launches += b->launches_per_graph;
       for (auto &c : b->cls) walk_launches += c.n_tasks ? 1 : 0;
     } else {
-      size_t n_slots = 0;
-      if ((st = plan_launch(b, next_round, done, evals, &n_slots)) != LABS_OK) return st;
+      labs_status st = plan_launch(b, next_round, done, evals);
+      if (st != LABS_OK) return st;
       if (first && (st = reset_state(b, &launches)) != LABS_OK) return st;
-      const int before = launches;
-      if ((st = enqueue_launch(b, n_slots, &ev, &launches)) != LABS_OK) return st;
-      walk_launches += launches - before - 1;  // the finalize is the one non-walk launch
-      continued = continued || !first;
+      for (auto &c : b->cls) walk_launches += c.n_tasks ? 1 : 0;
+      if ((st = enqueue_launch(b, &ev, &launches)) != LABS_OK) return st;
+      if (!first && b->graph) {
+        // the graph's task lists were replaced by this launch's: capture afresh next run
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
     }
     first = false;
-    std::vector<int32_t> rounds(n);
-    BCU(cudaMemcpyAsync(done.data(), b->d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->s));
-    BCU(cudaMemcpyAsync(rounds.data(), b->d_rounds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->s));
-    BCU(cudaMemcpyAsync(evals.data(), b->d_evals, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, b->s));
-    BCU(cudaStreamSynchronize(b->s));
+    labs_status st = read_snapshot(b, done, next_round, evals);
+    if (st != LABS_OK) return st;
     bool all = true;
-    for (size_t i = 0; i < n; ++i) {
-      all = all && done[i];
-      next_round[i] = rounds[i];
-    }
+    for (size_t i = 0; i < n; ++i) all = all && done[i];
     if (all) break;
   }
-  if (continued && b->graph) {
-    // later launches reused the plan buffers the graph reads: capture afresh next run
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
-  if ((st = expand_results(b, &launches)) != LABS_OK) return st;
   BCU(cudaEventRecord(t1, b->s));
   int32_t err = 0;
-  unsigned long long planes = 0;
-  b->h_bestE.resize(n);
-  b->h_rounds.resize(n);
-  b->h_seq.resize(b->seq_total);
   BCU(cudaMemcpyAsync(&err, b->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->s));
-  BCU(cudaMemcpyAsync(&planes, b->d_planes, sizeof(planes), cudaMemcpyDeviceToHost, b->s));
-  BCU(cudaMemcpyAsync(b->h_bestE.data(), b->d_bestE, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, b->s));
-  BCU(cudaMemcpyAsync(b->h_rounds.data(), b->d_rounds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->s));
-  BCU(cudaMemcpyAsync(b->h_seq.data(), b->d_seq, b->seq_total, cudaMemcpyDeviceToHost, b->s));
   BCU(cudaStreamSynchronize(b->s));
+  auto at = [&](const void *dev) { return b->h_snap.data() + ((const char *)dev - b->d_snap); };
+  b->h_bestE.resize(n);
+  b->h_planes.resize(n);
+  b->h_seq.resize(n * (size_t)b->seq_stride);
+  std::memcpy(b->h_bestE.data(), at(b->snap.bestE), sizeof(int64_t) * n);
+  std::memcpy(b->h_planes.data(), at(b->snap.planes), sizeof(unsigned long long) * n);
+  std::memcpy(b->h_seq.data(), at(b->snap.seq), b->h_seq.size());
+  b->h_rounds = next_round;
   b->h_evals = evals;
   b->h_done = done;
   b->have_results = true;
@@ -666,9 +683,11 @@ extern "C" labs_status labs_batch_run(labs_batch *b, labs_stats *stats) {
   if (err & kErrRecheck) return LABS_ECHECK;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
+    unsigned long long planes = 0;
     for (size_t i = 0; i < n; ++i) {
       stats->evals += evals[i];
       stats->rounds = std::max(stats->rounds, b->h_rounds[i]);
+      planes += b->h_planes[i];
     }
     stats->launches = launches;
     stats->walk_launches = walk_launches;
@@ -683,10 +702,17 @@ extern "C" labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t 
                                          uint64_t *evals, int32_t *rounds) {
   if (!b || i < 0 || (size_t)i >= b->pr.size()) return LABS_EINVAL;
   if (!b->have_results) return LABS_PENDING;
-  if (best_seq) std::memcpy(best_seq, b->h_seq.data() + b->seq_off[i], (size_t)b->pr[i].L);
+  if (best_seq) std::memcpy(best_seq, b->h_seq.data() + (size_t)i * b->seq_stride, (size_t)b->pr[i].L);
   if (best_E) *best_E = b->h_bestE[i];
   if (evals) *evals = b->h_evals[i];
   if (rounds) *rounds = b->h_rounds[i];
+  return LABS_OK;
+}
+
+extern "C" labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, uint64_t *plane_steps) {
+  if (!b || !plane_steps || i < 0 || (size_t)i >= b->pr.size()) return LABS_EINVAL;
+  if (!b->have_results) return LABS_PENDING;
+  *plane_steps = b->h_planes[i];
   return LABS_OK;
 }
 

@@ -30,6 +30,76 @@ struct MaxRegsFor {
 template <int W>
 constexpr int kBatchWarpWords = MaskTable<W>::kWords + (W + 2) * 32;
 
+__device__ __forceinline__ uint32_t load_volatile(const uint32_t *x) { return *(const volatile uint32_t *)x; }
+__device__ __forceinline__ int32_t load_volatile(const int32_t *x) { return *(const volatile int32_t *)x; }
+
+__device__ __forceinline__ uint32_t record_of(const ProblemState &ps, int p, uint32_t round) {
+  return ps.rec_base[p] + round % ps.ring[p];
+}
+
+// Algorithm 1's update with round r of problem p (its record complete, the
+// caller holding p's finalization lock): add the round's evaluations, keep
+// the strict best (so the earliest round wins ties, and inside a round the
+// lowest walk through the atomicMin key), and stop at the budget or the
+// target.  Returns true when the problem stops here.  Reads bypass L1: the
+// record and the state were written by other SMs.
+__device__ bool finalize_round(const RoundRecords &rec, const ProblemState &ps, int p, uint32_t r) {
+  const uint32_t j = record_of(ps, p, r);
+  const unsigned long long ev = __ldcg(ps.evals + p) + __ldcg(rec.evals + j);
+  ps.evals[p] = ev;
+  ps.planes[p] = __ldcg(ps.planes + p) + __ldcg(rec.planes + j);
+  const unsigned long long rb = __ldcg(rec.best + j);
+  long long best = __ldcg(reinterpret_cast<const long long *>(ps.bestE) + p);
+  if (rb != ~0ull) {
+    const long long E = (long long)(rb >> 32);
+    const uint32_t w = (uint32_t)(rb & 0xFFFFFFFFu);
+    if (E < best) {
+      best = E;
+      ps.bestE[p] = E;
+      const uint32_t *src = rec.keys + ((size_t)j * rec.max_chunks + (w >> 5)) * kKeyWords;
+      for (int i = 0; i < kKeyWords; ++i) ps.key[(size_t)p * kKeyWords + i] = __ldcg(src + i);
+      ps.best_round[p] = (int32_t)r;
+      ps.best_walk[p] = (int32_t)w;
+    }
+  }
+  ps.rounds[p] = (int32_t)r + 1;
+  if (ev >= ps.budget[p] || (ps.target[p] >= 0 && best <= ps.target[p])) {
+    __threadfence();  // the state above is visible before `done`
+    ps.done[p] = 1;
+    return true;
+  }
+  return false;
+}
+
+// Finalize the complete rounds of problem p that are next in round order.
+// Called by one thread after it completed a chunk of one of p's rounds (or by
+// the post-launch pass).  fin[p] = (next round) << 1 | lock: whoever takes the
+// lock finalizes, unlocks, then looks again, so a round that completes while
+// another is being finalized is never left behind (the completer's count
+// update and the finalizer's unlock are each followed by a full fence before
+// each reads the other's word).  A record is the next round's only if it holds
+// that round (records are reused round after round), read before its count.
+__device__ void try_finalize(const RoundRecords &rec, const ProblemState &ps, int p) {
+  for (;;) {
+    if (load_volatile(ps.done + p)) return;
+    __threadfence();
+    const uint32_t st = load_volatile(ps.fin + p);
+    if (st & 1u) return;  // another thread is finalizing; it looks at the next round after
+    const uint32_t r = st >> 1;
+    const uint32_t j = record_of(ps, p, r);
+    if (load_volatile(rec.round + j) != r) return;  // round r not issued yet
+    __threadfence();
+    if (load_volatile(rec.left + j) != 0u) return;  // round r not complete yet
+    if (atomicCAS(ps.fin + p, st, st | 1u) != st) continue;
+    __threadfence();
+    const bool stop = finalize_round(rec, ps, p, r);
+    __threadfence();
+    atomicExch(ps.fin + p, (r + 1u) << 1);
+    __threadfence();
+    if (stop) return;
+  }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::value)
     batch_kernel(const BatchKernelParams p) {
@@ -45,14 +115,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
   uint32_t *mask_rows = batch_smem + (size_t)(threadIdx.x >> 5) * kBatchWarpWords<W>;
   uint32_t *best_park = mask_rows + MaskTable<W>::kWords + lane;
   int rows_L = 0;
-  unsigned long long planes = 0;
   for (;;) {
     uint32_t t = 0;
     if (lane == 0) t = atomicAdd(p.task_next, 1u);
     t = __shfl_sync(0xFFFFFFFFu, t, 0);
     if (t >= p.n_tasks) break;
     const BatchTask task = p.tasks[t];
-    if (p.done && p.done[task.problem]) continue;
+    // a problem stopped by an earlier round (finalized in an earlier launch or
+    // by a warp of this one) needs none of its later rounds: skip them
+    if (load_volatile(p.ps.done + task.problem)) continue;
     const BatchProblem pr = p.probs[task.problem];
     const uint32_t walk = task.chunk * 32u + (uint32_t)lane;
     const bool active = walk < (uint32_t)pr.walks;
@@ -63,7 +134,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
       __syncwarp();
       rows_L = pr.L;
     }
-    unsigned long long packed = ~0ull;
+    unsigned long long packed = ~0ull, planes = 0;
     uint32_t evals = 0;
     WalkOut<NS> o;
     if (active) {
@@ -71,7 +142,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
                                                    pr.walk_len, table, pr.cap, pr.kw64, 0, nullptr, p.err, o);
       packed = ((unsigned long long)(uint32_t)o.bestE << 32) | walk;
       evals = (uint32_t)g.D * (uint32_t)(o.moves + o.stuck);
-      planes += o.planes;
+      planes = o.planes;
     }
     // the chunk's best (lowest E, then lowest walk) publishes its key
     unsigned long long m = packed;
@@ -79,19 +150,29 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
     for (int off = 16; off > 0; off >>= 1) {
       const unsigned long long v = __shfl_xor_sync(0xFFFFFFFFu, m, off);
       m = v < m ? v : m;
+      planes += __shfl_xor_sync(0xFFFFFFFFu, planes, off);
     }
     if (active && packed == m) {
-      uint32_t *k = p.slot_keys + ((size_t)task.slot * p.max_chunks + task.chunk) * kKeyWords;
+      uint32_t *k = p.rec.keys + ((size_t)task.rec * p.rec.max_chunks + task.chunk) * kKeyWords;
 #pragma unroll
       for (int w = 0; w < kKeyWords; ++w) k[w] = w < NS ? o.best_key[w] : 0u;
     }
     const uint32_t ev = __reduce_add_sync(0xFFFFFFFFu, evals);
     if (lane == 0) {
-      atomicMin(&p.slot_best[task.slot], m);
-      atomicAdd(&p.slot_evals[task.slot], (unsigned long long)ev);
+      atomicMin(&p.rec.best[task.rec], m);
+      atomicAdd(&p.rec.evals[task.rec], (unsigned long long)ev);
+      atomicAdd(&p.rec.planes[task.rec], planes);
     }
+    // every lane's results are visible device-wide before the chunk counts as
+    // finished; the warp that finishes a round's last chunk finalizes it
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && atomicSub(&p.rec.left[task.rec], 1u) == 1u) {
+      __threadfence();
+      try_finalize(p.rec, p.ps, (int)task.problem);
+    }
+    __syncwarp();
   }
-  if (p.plane_steps && planes) atomicAdd(p.plane_steps, planes);
 }
 
 // dynamic shared memory of a block: one mask table per warp
@@ -107,7 +188,8 @@ static cudaError_t set_batch_smem(int block) {
 }
 
 template <int W>
-static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out) {
+static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out,
+                                  int max_blocks) {
   int per_sm = 0;
   cudaError_t e = set_batch_smem<W>(block);
   if (e != cudaSuccess) return e;
@@ -116,7 +198,8 @@ static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStr
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  const int grid = per_sm * sms;
+  int grid = per_sm * sms;
+  if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
   if (grid_out) *grid_out = grid;
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   batch_kernel<W><<<grid, block, batch_smem_bytes<W>(block), s>>>(p);
@@ -135,17 +218,18 @@ static int resident_w(int block) {
   return per_sm * sms * block;
 }
 
-cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out) {
+cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out,
+                         int max_blocks) {
   if (block < 32 || block > kBatchMaxThreads || block % 32) return cudaErrorInvalidValue;
   switch (W) {
-    case 1: return launch_batch_w<1>(block, p, s, grid_out);
-    case 2: return launch_batch_w<2>(block, p, s, grid_out);
-    case 3: return launch_batch_w<3>(block, p, s, grid_out);
-    case 4: return launch_batch_w<4>(block, p, s, grid_out);
-    case 5: return launch_batch_w<5>(block, p, s, grid_out);
-    case 6: return launch_batch_w<6>(block, p, s, grid_out);
-    case 7: return launch_batch_w<7>(block, p, s, grid_out);
-    case 8: return launch_batch_w<8>(block, p, s, grid_out);
+    case 1: return launch_batch_w<1>(block, p, s, grid_out, max_blocks);
+    case 2: return launch_batch_w<2>(block, p, s, grid_out, max_blocks);
+    case 3: return launch_batch_w<3>(block, p, s, grid_out, max_blocks);
+    case 4: return launch_batch_w<4>(block, p, s, grid_out, max_blocks);
+    case 5: return launch_batch_w<5>(block, p, s, grid_out, max_blocks);
+    case 6: return launch_batch_w<6>(block, p, s, grid_out, max_blocks);
+    case 7: return launch_batch_w<7>(block, p, s, grid_out, max_blocks);
+    case 8: return launch_batch_w<8>(block, p, s, grid_out, max_blocks);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -164,63 +248,105 @@ int batch_resident_lanes(int W, int block) {
   }
 }
 
-// Algorithm 1's bookkeeping for a batch launch: each problem takes its rounds
-// of this launch in round order (rounds beyond its stop point, run
-// speculatively, are ignored), keeping the strict best (earliest round, then
-// lowest walk on ties) and stopping at the budget or the target.
-__global__ void batch_finalize_kernel(const BatchFinalizeParams f) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= f.n_problems || f.done[p]) return;
-  for (uint32_t k = 0; k < f.n_slots[p]; ++k) {
-    const uint32_t slot = f.first_slot[p] + k;
-    f.evals[p] += f.slot_evals[slot];
-    const unsigned long long rb = f.slot_best[slot];
-    if (rb != ~0ull) {
-      const int64_t E = (int64_t)(rb >> 32);
-      const uint32_t w = (uint32_t)(rb & 0xFFFFFFFFu);
-      if (E < f.bestE[p]) {
-        f.bestE[p] = E;
-        const uint32_t *src = f.slot_keys + ((size_t)slot * f.max_chunks + (w >> 5)) * kKeyWords;
-        for (int i = 0; i < kKeyWords; ++i) f.key[(size_t)p * kKeyWords + i] = src[i];
-        f.best_round[p] = (int32_t)f.slot_round[slot];
-        f.best_walk[p] = (int32_t)w;
-      }
-    }
-    f.rounds[p] = (int32_t)f.slot_round[slot] + 1;
-    if (f.evals[p] >= f.budget[p] || (f.target[p] >= 0 && f.bestE[p] <= f.target[p])) {
-      f.done[p] = 1;
-      break;
-    }
-  }
+// After a launch: finalize what the in-kernel finalization left (normally
+// nothing), one thread per listed problem.
+__global__ void batch_finalize_kernel(const int32_t *problems, int n, const RoundRecords rec, const ProblemState ps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) try_finalize(rec, ps, problems[i]);
 }
 
-cudaError_t launch_batch_finalize(const BatchFinalizeParams &f, cudaStream_t s) {
-  if (f.n_problems <= 0) return cudaSuccess;
-  batch_finalize_kernel<<<(f.n_problems + 127) / 128, 128, 0, s>>>(f);
+cudaError_t launch_batch_finalize(const int32_t *problems, int n, const RoundRecords &rec, const ProblemState &ps,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  batch_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(problems, n, rec, ps);
   return cudaGetLastError();
 }
 
-// Reset the per-problem state of the listed slots (a serving slot taking a new request).
-__global__ void init_slots_kernel(const int32_t *slots, int n, int64_t *bestE, unsigned long long *evals,
-                                  int32_t *done, int32_t *rounds, int32_t *best_round, int32_t *best_walk,
-                                  uint32_t *key) {
+// New rounds in their records: the accumulators and the chunk count first,
+// then (after a fence) the round number, which makes the record the round's.
+__global__ void issue_records_kernel(const RecordInit *list, int n, const RoundRecords rec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int p = slots[i];
-  bestE[p] = INT64_MAX;
-  evals[p] = 0;
-  done[p] = 0;
-  rounds[p] = 0;
-  best_round[p] = -1;
-  best_walk[p] = -1;
-  for (int k = 0; k < kKeyWords; ++k) key[(size_t)p * kKeyWords + k] = 0u;
+  const RecordInit ri = list[i];
+  rec.best[ri.rec] = ~0ull;
+  rec.evals[ri.rec] = 0;
+  rec.planes[ri.rec] = 0;
+  rec.left[ri.rec] = ri.chunks;
+  __threadfence();
+  rec.round[ri.rec] = ri.round;
 }
 
-cudaError_t launch_init_slots(const int32_t *slots, int n, int64_t *bestE, unsigned long long *evals, int32_t *done,
-                              int32_t *rounds, int32_t *best_round, int32_t *best_walk, uint32_t *key,
-                              cudaStream_t s) {
+cudaError_t launch_issue_records(const RecordInit *list, int n, const RoundRecords &rec, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  init_slots_kernel<<<(n + 127) / 128, 128, 0, s>>>(slots, n, bestE, evals, done, rounds, best_round, best_walk, key);
+  issue_records_kernel<<<(n + 127) / 128, 128, 0, s>>>(list, n, rec);
+  return cudaGetLastError();
+}
+
+// A problem starting afresh: its records hold no round, then its state.
+__global__ void init_problems_state_kernel(const int32_t *problems, int n, const RoundRecords rec,
+                                           const ProblemState ps) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int p = problems[i];
+  for (uint32_t k = 0; k < ps.ring[p]; ++k) rec.round[ps.rec_base[p] + k] = ~0u;
+  __threadfence();
+  ps.fin[p] = 0;
+  ps.bestE[p] = INT64_MAX;
+  ps.evals[p] = 0;
+  ps.planes[p] = 0;
+  ps.rounds[p] = 0;
+  ps.best_round[p] = -1;
+  ps.best_walk[p] = -1;
+  for (int k = 0; k < kKeyWords; ++k) ps.key[(size_t)p * kKeyWords + k] = 0u;
+  __threadfence();
+  ps.done[p] = 0;
+}
+
+cudaError_t launch_init_problems_state(const int32_t *problems, int n, const RoundRecords &rec,
+                                       const ProblemState &ps, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  init_problems_state_kernel<<<(n + 127) / 128, 128, 0, s>>>(problems, n, rec, ps);
+  return cudaGetLastError();
+}
+
+// One block per listed problem: its state, read after its done flag (the
+// finalizer writes the flag last, after a fence, so a finished problem's state
+// is complete), and the Eq. 2 expansion of its best key when it is finished.
+// Block 0 also sums the evaluations of the listed records.
+__global__ void snapshot_kernel(const int32_t *problems, int n, const BatchProblem *probs, const ProblemState ps,
+                                const uint32_t *recs, int n_recs, const RoundRecords rec, const Snapshot out) {
+  const int p = problems[blockIdx.x];
+  __shared__ int32_t fin_done;
+  if (threadIdx.x == 0) {
+    const int32_t d = load_volatile(ps.done + p);
+    __threadfence();
+    out.done[p] = d;
+    out.rounds[p] = __ldcg(ps.rounds + p);
+    out.bestE[p] = (int64_t)__ldcg(reinterpret_cast<const long long *>(ps.bestE) + p);
+    out.evals[p] = __ldcg(ps.evals + p);
+    out.planes[p] = __ldcg(ps.planes + p);
+    fin_done = d;
+  }
+  __syncthreads();
+  if (fin_done) {
+    const int L = probs[p].L;
+    uint32_t key[kKeyWords];
+    for (int k = 0; k < kKeyWords; ++k) key[k] = __ldcg(ps.key + (size_t)p * kKeyWords + k);
+    for (int a = threadIdx.x; a < L; a += blockDim.x)
+      out.seq[(size_t)p * out.stride + a] = sequence_bit(key, L, a, false) ? (int8_t)-1 : (int8_t)1;
+  }
+  if (blockIdx.x == 0 && out.run_evals) {
+    unsigned long long sum = 0;
+    for (int i = threadIdx.x; i < n_recs; i += blockDim.x) sum += __ldcg(rec.evals + recs[i]);
+    if (sum) atomicAdd(out.run_evals, sum);
+  }
+}
+
+cudaError_t launch_snapshot(const int32_t *problems, int n, const BatchProblem *probs, const ProblemState &ps,
+                            const uint32_t *recs, int n_recs, const RoundRecords &rec, const Snapshot &out,
+                            cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  snapshot_kernel<<<n, 128, 0, s>>>(problems, n, probs, ps, recs, n_recs, rec, out);
   return cudaGetLastError();
 }
 

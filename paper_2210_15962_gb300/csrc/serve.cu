@@ -1,14 +1,24 @@
 // Serving loop with continuous batching (labs_serve_* in include/labs.h).
 //
 // Requests (one problem each) arrive at any time.  A scheduler thread admits
-// them in arrival order into device slots while a slot is free and the
-// server's memory budget holds their working set, then repeatedly launches
-// the persistent batch kernels over every admitted request at once (a few
-// rounds each per launch), finalizes each request round by round (Algorithm
-// 1's best update and stop rule), hands finished requests back and admits
-// newly arrived ones at the next launch boundary.  A request's result depends
-// only on its own (L, seed, walks, walk_len, budget, target): the same alone
-// and in any mix.
+// them in arrival order into device slots while a slot is free and a launch
+// over every admitted request still fits its half of the server's arena, and
+// keeps two launches of the persistent batch kernels in flight: while one
+// runs, the next is already queued on its own streams, so its tasks start on
+// the SMs the first one's tail frees and the device never drains between
+// launches.  Each launch gives every admitted request its next few rounds.
+// The kernels finalize each request round by round as its rounds complete
+// (Algorithm 1's best update and stop rule) and skip the rounds issued past a
+// request's stop.  After a launch completes, the scheduler reads a snapshot of
+// every admitted request, hands finished ones back, admits new ones and queues
+// the next launch.  A request's result depends only on its own (L, seed,
+// walks, walk_len, budget, target): the same alone and in any mix.
+//
+// Device memory: a fixed block of per-slot state and round records (sized by
+// max_active, rounds_per_launch and max_walks), and an arena of mem_bytes
+// whose two halves hold the task lists and visited-table pools of the two
+// launches in flight.  Admission keeps every launch inside its half, so the
+// bytes in use are bounded by mem_bytes whatever arrives.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,36 +45,120 @@ uint64_t now_ns() {
       .count();
 }
 
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr int kSeqStride = 512;  // bytes per slot of the expanded best sequences (>= LABS_L_MAX)
+constexpr int kDepth = 2;        // launches in flight
+constexpr int kRingFactor = 3;   // round records per slot = kRingFactor x rounds_per_launch
+
 struct Request {
   uint64_t ticket = 0;
   labs_problem p{};
   int W = 0;
-  size_t mem_cost = 0;
   uint64_t t_submit = 0, t_admit = 0, t_done = 0;
   labs_status status = LABS_PENDING;
-  int64_t bestE = -1;
-  uint64_t evals = 0;
-  int32_t rounds = 0;
-  std::vector<int8_t> seq;
   int slot = -1;
-  int32_t next_round = 0;
+  // the host's view, from the latest snapshot that listed the request
+  int64_t bestE = -1;
+  uint64_t evals = 0, planes = 0;
+  int32_t rounds = 0;          // rounds finalized
+  uint32_t issued = 0;         // next round to issue
+  uint64_t first_launch = 0;   // the first launch that lists it
+  std::vector<int8_t> seq;
 };
 
-struct ClassPool {
-  int W = 0;
-  size_t words = 0;  // per lane
-  int resident = 0;
-  uint64_t *pool = nullptr;
-  BatchTask *tasks = nullptr;
-  size_t tasks_cap = 0;
-  uint32_t n_tasks = 0;
+// What one launch runs for one request: its rounds (k) and the sizes that
+// decide the launch's device memory.
+struct Share {
+  int slot, W, L, walk_len;
+  uint32_t k, chunks;
+  size_t table_words;  // 64-bit words of one walk's visited table
 };
 
-template <typename T>
-cudaError_t dalloc(T **p, size_t n) {
-  *p = nullptr;
-  return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+Share share_of(int slot, const labs_problem &p, uint32_t k) {
+  Share s;
+  s.slot = slot;
+  s.W = lag_words(p.L);
+  s.L = p.L;
+  s.walk_len = p.walk_len;
+  s.k = k;
+  s.chunks = (uint32_t)((p.walks + 31) / 32);
+  s.table_words = (size_t)visited_table_cap(p.walk_len) * (size_t)key_words64((p.L + 1) / 2);
+  s.table_words = (s.table_words + 1) / 2 * 2;  // whole 16-byte units (the warp clears in uint4)
+  return s;
 }
+
+// Layout of one launch inside its half of the arena (byte offsets; sizes
+// only when computed for admission): the lists uploaded from the host (the
+// listed problems, the records to issue, the task list of each class), then
+// one visited-table pool per class with a lane for each task the class can run
+// at once.
+struct Carve {
+  size_t problems = 0, issue = 0, recs = 0;
+  std::vector<size_t> tasks;  // per class
+  size_t upload_bytes = 0;
+  std::vector<size_t> pool;        // per class
+  std::vector<size_t> pool_words;  // per class, per lane
+  std::vector<int> lanes;          // per class
+  std::vector<uint32_t> n_tasks;   // per class
+  uint32_t n_problems = 0, n_issue = 0;
+  size_t total = 0;
+};
+
+Carve carve_launch(const std::vector<Share> &sh, const std::vector<int> &resident, int block) {
+  const size_t nc = resident.size();
+  Carve c;
+  c.tasks.assign(nc, 0);
+  c.pool.assign(nc, 0);
+  c.pool_words.assign(nc, 0);
+  c.lanes.assign(nc, 0);
+  c.n_tasks.assign(nc, 0);
+  c.n_problems = (uint32_t)sh.size();
+  for (const Share &s : sh) {
+    c.n_issue += s.k;
+    c.n_tasks[s.W - 1] += s.k * s.chunks;
+    if (s.k) c.pool_words[s.W - 1] = std::max(c.pool_words[s.W - 1], s.table_words);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  c.problems = take(sizeof(int32_t) * c.n_problems);
+  c.issue = take(sizeof(RecordInit) * c.n_issue);
+  c.recs = take(sizeof(uint32_t) * c.n_issue);
+  for (size_t w = 0; w < nc; ++w) c.tasks[w] = take(sizeof(BatchTask) * c.n_tasks[w]);
+  c.upload_bytes = off;
+  for (size_t w = 0; w < nc; ++w) {
+    if (!c.n_tasks[w]) continue;
+    const size_t want = ((size_t)c.n_tasks[w] * 32 + block - 1) / block * block;
+    c.lanes[w] = (int)std::min<size_t>(want, (size_t)resident[w]);
+    c.pool[w] = take(sizeof(uint64_t) * c.pool_words[w] * (size_t)c.lanes[w]);
+  }
+  c.total = off;
+  return c;
+}
+
+// One of the launches in flight: its streams, events, arena half and snapshot.
+struct Launch {
+  uint64_t id = 0;
+  bool in_flight = false;
+  cudaStream_t s = nullptr;
+  std::vector<cudaStream_t> cs;
+  std::vector<cudaEvent_t> cs_done;
+  cudaEvent_t fork = nullptr, ev0 = nullptr, ev1 = nullptr;
+  char *arena = nullptr;
+  unsigned int *task_next = nullptr;  // per class
+  int32_t *init_list = nullptr;       // the slots this launch starts afresh
+  int32_t *snap_err = nullptr;        // the error word, copied before the read-back
+  char *d_snap = nullptr, *h_snap = nullptr;  // h_snap: pinned
+  size_t snap_bytes = 0;
+  Snapshot snap{};
+  std::vector<int> slots;   // the slots it lists
+  size_t carve_bytes = 0;
+  int walk_kernels = 0;
+};
 
 }  // namespace
 }  // namespace psaw
@@ -74,15 +168,15 @@ using namespace psaw;
 struct labs_server {
   labs_serve_cfg cfg{};
   int device = 0;
-  cudaStream_t s = nullptr;
-  bool own_stream = false;
   std::mutex mu;
   std::condition_variable wake;       // scheduler: new request or shutdown
   std::condition_variable finished;   // waiters: a request finished
   std::deque<uint64_t> pending;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
-  std::vector<uint64_t> slot_ticket;  // 0 = free
-  size_t mem_used = 0;
+  std::vector<uint64_t> slot_ticket;     // 0 = free
+  std::vector<uint64_t> slot_listed;     // the last launch that listed the slot
+  std::vector<uint8_t> slot_draining;    // finished, but a launch in flight still lists it
+  size_t mem_used = 0, mem_peak = 0, fixed_bytes = 0, half_bytes = 0;
   uint64_t next_ticket = 1;
   bool stopping = false;
   labs_status failed = LABS_OK;
@@ -90,354 +184,355 @@ struct labs_server {
   // counters
   uint64_t n_submitted = 0, n_completed = 0, evals_done = 0, evals_run = 0;
   uint64_t launches = 0, walk_launches = 0;
-  double busy_ms = 0.0;
-  uint64_t t_created = 0;
-  // device buffers, indexed by slot
+  double busy_ms = 0.0, busy_end_ms = 0.0;
+  // device state
+  void *fixed = nullptr;
   BatchProblem *d_probs = nullptr;
-  uint64_t *d_budget = nullptr;
-  int64_t *d_target = nullptr;
-  int32_t *d_done = nullptr, *d_best_round = nullptr, *d_best_walk = nullptr, *d_rounds = nullptr;
-  int64_t *d_bestE = nullptr;
-  uint32_t *d_key = nullptr;
-  unsigned long long *d_evals = nullptr;
-  int32_t *d_init_list = nullptr;
-  // per launch
-  uint32_t max_chunks = 1, max_slots = 0;
-  unsigned long long *d_slot_best = nullptr, *d_slot_evals = nullptr;
-  uint32_t *d_slot_keys = nullptr, *d_slot_round = nullptr, *d_first_slot = nullptr, *d_n_slots = nullptr;
-  unsigned int *d_task_next = nullptr;
-  unsigned long long *d_planes = nullptr;
+  ProblemState ps{};
+  RoundRecords rec{};
   int32_t *d_err = nullptr;
-  int8_t *d_seq = nullptr;
-  std::vector<ClassPool> pools;  // index W-1
-  std::vector<cudaStream_t> cs;  // one stream per class (overlapping kernels)
-  std::vector<cudaEvent_t> cs_done;
-  cudaEvent_t fork = nullptr;
+  uint32_t ring = 0;
+  char *arena = nullptr;
+  std::vector<int> resident;  // per class W - 1
+  Launch L[kDepth];
+  cudaEvent_t t_ref = nullptr;
+  uint64_t harvested = 0;  // id of the last launch harvested
 
   ~labs_server();
   void loop();
-  labs_status step(std::vector<int> &active);
+  void fail_all(labs_status why);
+  size_t admitted_carve(const Request *extra);                      // caller holds mu
+  labs_status enqueue(Launch &l, const std::vector<int> &admitted);  // caller does not hold mu
+  labs_status harvest(Launch &l);
 };
 
 labs_server::~labs_server() {
-  for (auto x : cs) cudaStreamDestroy(x);
-  for (auto e : cs_done) cudaEventDestroy(e);
-  if (fork) cudaEventDestroy(fork);
-  for (auto &c : pools) {
-    cudaFree(c.pool);
-    cudaFree(c.tasks);
+  for (auto &l : L) {
+    for (auto x : l.cs) cudaStreamDestroy(x);
+    for (auto e : l.cs_done) cudaEventDestroy(e);
+    if (l.fork) cudaEventDestroy(l.fork);
+    if (l.ev0) cudaEventDestroy(l.ev0);
+    if (l.ev1) cudaEventDestroy(l.ev1);
+    if (l.s) cudaStreamDestroy(l.s);
+    cudaFree(l.d_snap);
+    cudaFreeHost(l.h_snap);
   }
-  cudaFree(d_probs);
-  cudaFree(d_budget);
-  cudaFree(d_target);
-  cudaFree(d_done);
-  cudaFree(d_best_round);
-  cudaFree(d_best_walk);
-  cudaFree(d_rounds);
-  cudaFree(d_bestE);
-  cudaFree(d_key);
-  cudaFree(d_evals);
-  cudaFree(d_init_list);
-  cudaFree(d_slot_best);
-  cudaFree(d_slot_evals);
-  cudaFree(d_slot_keys);
-  cudaFree(d_slot_round);
-  cudaFree(d_first_slot);
-  cudaFree(d_n_slots);
-  cudaFree(d_task_next);
-  cudaFree(d_planes);
-  cudaFree(d_err);
-  cudaFree(d_seq);
-  if (own_stream && s) cudaStreamDestroy(s);
+  if (t_ref) cudaEventDestroy(t_ref);
+  cudaFree(fixed);
+  cudaFree(arena);
 }
 
-namespace psaw {
-namespace {
-
-constexpr int kTableFactor = 15;  // visited-table slots per pivot x 10
-
-// working set a request needs while admitted: its walks' visited tables as if
-// all ran at once plus its round slots and chunk keys
-size_t request_cost(const labs_problem &p, int rounds_per_launch) {
-  const int D = (p.L + 1) / 2;
-  const size_t table = (size_t)visited_table_cap(p.walk_len, kTableFactor) * key_words64(D) * 8;
-  const size_t chunks = (size_t)(p.walks + 31) / 32;
-  return (size_t)p.walks * table + (size_t)rounds_per_launch * (16 + chunks * kKeyWords * 4) + 256;
+// Arena bytes of one launch over every admitted request (and `extra`), each
+// running rounds_per_launch rounds (the most a launch gives a request).
+size_t labs_server::admitted_carve(const Request *extra) {
+  std::vector<Share> sh;
+  for (int sl = 0; sl < cfg.max_active; ++sl)
+    if (slot_ticket[sl] && !slot_draining[sl])
+      sh.push_back(share_of(sl, reqs[slot_ticket[sl]]->p, (uint32_t)cfg.rounds_per_launch));
+  if (extra) sh.push_back(share_of(-1, extra->p, (uint32_t)cfg.rounds_per_launch));
+  return carve_launch(sh, resident, cfg.block_threads).total;
 }
 
-}  // namespace
-}  // namespace psaw
+// Rounds the next launch gives a request: what its budget still needs beyond
+// the rounds in flight, at most rounds_per_launch, and never so far ahead of
+// the finalized rounds that the ring would reuse a record still in use.
+static uint32_t rounds_to_issue(const Request &r, int rounds_per_launch, uint32_t ring) {
+  const uint64_t fr = (uint64_t)r.p.walks * (uint64_t)r.p.walk_len * (uint64_t)((r.p.L + 1) / 2);
+  const uint64_t rem = r.p.step_budget > r.evals ? r.p.step_budget - r.evals : 0;
+  const int64_t need = (int64_t)std::max<uint64_t>(1, (rem + fr - 1) / fr);
+  const int64_t in_flight = (int64_t)r.issued - (int64_t)r.rounds;
+  const int64_t room = (int64_t)r.rounds + (int64_t)ring - (int64_t)r.issued;
+  const int64_t k = std::min<int64_t>({need - in_flight, room, (int64_t)rounds_per_launch});
+  return k > 0 ? (uint32_t)k : 0u;
+}
 
-// One scheduling step over the admitted requests: plan, launch, finalize, harvest.
-labs_status labs_server::step(std::vector<int> &active) {
-  // plan rounds per request and tasks per class
+// Plan and queue one launch on l's streams: the new requests' slot state, the
+// records of the rounds issued, the class kernels, the finalization of what
+// they left, and the snapshot of every listed slot with its read-back.
+labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
   const int rpl = cfg.rounds_per_launch;
-  std::vector<uint32_t> first(cfg.max_active, 0), cnt(cfg.max_active, 0), slot_round;
-  uint32_t nslots = 0;
-  std::vector<std::vector<std::pair<double, BatchTask>>> tk(pools.size());
+  std::vector<Share> sh;
+  std::vector<int64_t> target(cfg.max_active, -1);
+  std::vector<uint32_t> first_round(cfg.max_active, 0);
+  std::vector<BatchProblem> adm_probs;
+  std::vector<uint64_t> adm_budget;
+  std::vector<int64_t> adm_target;
   {
     std::lock_guard<std::mutex> lock(mu);
-    for (int sl : active) {
+    for (int sl : admitted) {
+      const Request &r = *reqs[slot_ticket[sl]];
+      BatchProblem bp{};
+      bp.L = r.p.L;
+      bp.W = r.W;
+      bp.walk_len = r.p.walk_len;
+      bp.walks = r.p.walks;
+      bp.cap = visited_table_cap(r.p.walk_len);
+      bp.kw64 = key_words64((r.p.L + 1) / 2);
+      bp.seed = r.p.seed;
+      adm_probs.push_back(bp);
+      adm_budget.push_back(r.p.step_budget);
+      adm_target.push_back(r.p.target_E);
+    }
+    l.slots.clear();
+    for (int sl = 0; sl < cfg.max_active; ++sl) {
+      if (!slot_ticket[sl] || slot_draining[sl]) continue;
       Request &r = *reqs[slot_ticket[sl]];
-      const uint64_t fr = (uint64_t)r.p.walks * r.p.walk_len * (uint64_t)((r.p.L + 1) / 2);
-      const uint64_t rem = r.p.step_budget > r.evals ? r.p.step_budget - r.evals : 0;
-      uint64_t k = rem == 0 ? 1 : (rem + fr - 1) / fr;
-      k = std::max<uint64_t>(1, std::min<uint64_t>(k, (uint64_t)rpl));
-      first[sl] = nslots;
-      cnt[sl] = (uint32_t)k;
-      const uint32_t chunks = (uint32_t)((r.p.walks + 31) / 32);
-      const double cost = (double)r.p.walk_len * ((r.p.L + 1) / 2) * r.W;
-      for (uint32_t j = 0; j < k; ++j) {
-        slot_round.push_back((uint32_t)(r.next_round + (int32_t)j));
-        for (uint32_t ch = 0; ch < chunks; ++ch)
-          tk[r.W - 1].push_back({cost, BatchTask{(uint32_t)sl, (uint32_t)(r.next_round + (int32_t)j), ch, nslots + j}});
-      }
-      nslots += (uint32_t)k;
+      const uint32_t k = rounds_to_issue(r, rpl, ring);
+      sh.push_back(share_of(sl, r.p, k));
+      target[sl] = r.p.target_E;
+      first_round[sl] = r.issued;
+      r.issued += k;
+      if (!r.first_launch) r.first_launch = l.id;
+      slot_listed[sl] = l.id;
+      l.slots.push_back(sl);
     }
   }
-  for (size_t ci = 0; ci < pools.size(); ++ci) {
-    ClassPool &c = pools[ci];
-    auto &v = tk[ci];
-    using Costed = std::pair<double, BatchTask>;
-    std::stable_sort(v.begin(), v.end(), [](const Costed &x, const Costed &y) {
-      return x.first > y.first;
-    });
-    c.n_tasks = (uint32_t)v.size();
-    if (v.empty()) continue;
-    if (v.size() > c.tasks_cap) {
-      cudaFree(c.tasks);
-      c.tasks_cap = std::max(v.size(), 2 * c.tasks_cap);
-      if (dalloc(&c.tasks, c.tasks_cap) != cudaSuccess) return LABS_ENOMEM;
+  const Carve cv = carve_launch(sh, resident, cfg.block_threads);
+  if (cv.total > half_bytes) return LABS_ENOMEM;  // admission keeps this from happening
+  l.carve_bytes = cv.total;
+  // the uploaded lists
+  std::vector<char> up(cv.upload_bytes);
+  int32_t *plist = reinterpret_cast<int32_t *>(up.data() + cv.problems);
+  RecordInit *ilist = reinterpret_cast<RecordInit *>(up.data() + cv.issue);
+  uint32_t *rlist = reinterpret_cast<uint32_t *>(up.data() + cv.recs);
+  std::vector<std::vector<PlannedTask>> tk(resident.size());
+  size_t ni = 0;
+  for (size_t i = 0; i < sh.size(); ++i) {
+    const Share &s = sh[i];
+    plist[i] = s.slot;
+    const double cost = batch_task_cost(s.L, s.walk_len);
+    const bool layered = target[s.slot] >= 0;
+    for (uint32_t j = 0; j < s.k; ++j) {
+      const uint32_t round = first_round[s.slot] + j;
+      const uint32_t recx = (uint32_t)s.slot * ring + round % ring;
+      ilist[ni] = RecordInit{recx, round, s.chunks};
+      rlist[ni] = recx;
+      ++ni;
+      for (uint32_t ch = 0; ch < s.chunks; ++ch)
+        tk[s.W - 1].push_back({layered ? j : 0u, cost, BatchTask{(uint32_t)s.slot, round, ch, recx}});
     }
-    std::vector<BatchTask> flat(v.size());
-    for (size_t j = 0; j < v.size(); ++j) flat[j] = v[j].second;
-    if (cudaMemcpyAsync(c.tasks, flat.data(), sizeof(BatchTask) * flat.size(), cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
+  }
+  for (size_t ci = 0; ci < tk.size(); ++ci) {
+    order_tasks(tk[ci]);
+    BatchTask *dst = reinterpret_cast<BatchTask *>(up.data() + cv.tasks[ci]);
+    for (size_t j = 0; j < tk[ci].size(); ++j) dst[j] = tk[ci][j].t;
+  }
+  cudaStream_t s = l.s;
+  char *a = l.arena;
+  const int32_t *d_plist = reinterpret_cast<const int32_t *>(a + cv.problems);
+  // new requests: their problem, budget and target, then a fresh state
+  for (size_t i = 0; i < admitted.size(); ++i) {
+    const int sl = admitted[i];
+    if (cudaMemcpyAsync(d_probs + sl, &adm_probs[i], sizeof(BatchProblem), cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(const_cast<uint64_t *>(ps.budget) + sl, &adm_budget[i], sizeof(uint64_t),
+                        cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(const_cast<int64_t *>(ps.target) + sl, &adm_target[i], sizeof(int64_t),
+                        cudaMemcpyHostToDevice, s))
       return LABS_ECUDA;
   }
-  if (cudaMemcpyAsync(d_slot_round, slot_round.data(), sizeof(uint32_t) * slot_round.size(), cudaMemcpyHostToDevice,
-                      s) != cudaSuccess ||
-      cudaMemcpyAsync(d_first_slot, first.data(), sizeof(uint32_t) * first.size(), cudaMemcpyHostToDevice, s) !=
+  if (cudaMemcpyAsync(a, up.data(), up.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) return LABS_ECUDA;
+  if (!admitted.empty()) {
+    if (cudaMemcpyAsync(l.init_list, admitted.data(), sizeof(int32_t) * admitted.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        launch_init_problems_state(l.init_list, (int)admitted.size(), rec, ps, s) != cudaSuccess)
+      return LABS_ECUDA;
+    ++launches;
+  }
+  if (cudaEventRecord(l.ev0, s) != cudaSuccess ||
+      launch_issue_records(reinterpret_cast<const RecordInit *>(a + cv.issue), (int)cv.n_issue, rec, s) !=
           cudaSuccess ||
-      cudaMemcpyAsync(d_n_slots, cnt.data(), sizeof(uint32_t) * cnt.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(d_slot_best, 0xFF, sizeof(unsigned long long) * nslots, s) != cudaSuccess ||
-      cudaMemsetAsync(d_slot_evals, 0, sizeof(unsigned long long) * nslots, s) != cudaSuccess ||
-      cudaMemsetAsync(d_task_next, 0, sizeof(unsigned int) * pools.size(), s) != cudaSuccess)
+      cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int) * resident.size(), s) != cudaSuccess ||
+      cudaEventRecord(l.fork, s) != cudaSuccess)
     return LABS_ECUDA;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  if (cudaEventRecord(fork, s) != cudaSuccess) return LABS_ECUDA;
-  for (size_t ci = 0; ci < pools.size(); ++ci) {
-    ClassPool &c = pools[ci];
-    if (!c.n_tasks) continue;
-    if (cudaStreamWaitEvent(cs[ci], fork, 0) != cudaSuccess) return LABS_ECUDA;
+  ++launches;
+  l.walk_kernels = 0;
+  for (size_t ci = 0; ci < resident.size(); ++ci) {
+    if (!cv.n_tasks[ci]) continue;
+    if (cudaStreamWaitEvent(l.cs[ci], l.fork, 0) != cudaSuccess) return LABS_ECUDA;
     BatchKernelParams k{};
     k.probs = d_probs;
-    k.tasks = c.tasks;
-    k.n_tasks = c.n_tasks;
-    k.task_next = d_task_next + ci;
-    k.pool = c.pool;
-    k.pool_words = c.words;
-    k.slot_best = d_slot_best;
-    k.slot_evals = d_slot_evals;
-    k.slot_keys = d_slot_keys;
-    k.max_chunks = max_chunks;
-    k.done = d_done;
+    k.tasks = reinterpret_cast<const BatchTask *>(a + cv.tasks[ci]);
+    k.n_tasks = cv.n_tasks[ci];
+    k.task_next = l.task_next + ci;
+    k.pool = reinterpret_cast<uint64_t *>(a + cv.pool[ci]);
+    k.pool_words = cv.pool_words[ci];
+    k.rec = rec;
+    k.ps = ps;
     k.mul_one = 1u;
     k.mul_two = 2u;
     k.mul_four = 4u;
     k.mul_h31 = 0x80000000u;
     k.mul_h30 = 0x40000000u;
-    k.plane_steps = d_planes;
     k.err = d_err;
-    if (launch_batch(c.W, cfg.block_threads, k, cs[ci], nullptr) != cudaSuccess) return LABS_ECUDA;
-    if (cudaEventRecord(cs_done[ci], cs[ci]) != cudaSuccess || cudaStreamWaitEvent(s, cs_done[ci], 0) != cudaSuccess)
+    // the pool holds cv.lanes[ci] lanes: never more blocks than that
+    if (launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr, cv.lanes[ci] / cfg.block_threads) !=
+        cudaSuccess)
       return LABS_ECUDA;
-    ++walk_launches;
-    ++launches;
+    if (cudaEventRecord(l.cs_done[ci], l.cs[ci]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, l.cs_done[ci], 0) != cudaSuccess)
+      return LABS_ECUDA;
+    ++l.walk_kernels;
   }
-  BatchFinalizeParams f{};
-  f.n_problems = cfg.max_active;
-  f.first_slot = d_first_slot;
-  f.n_slots = d_n_slots;
-  f.slot_round = d_slot_round;
-  f.slot_best = d_slot_best;
-  f.slot_evals = d_slot_evals;
-  f.slot_keys = d_slot_keys;
-  f.max_chunks = max_chunks;
-  f.budget = d_budget;
-  f.target = d_target;
-  f.done = d_done;
-  f.bestE = d_bestE;
-  f.key = d_key;
-  f.best_round = d_best_round;
-  f.best_walk = d_best_walk;
-  f.evals = d_evals;
-  f.rounds = d_rounds;
-  if (launch_batch_finalize(f, s) != cudaSuccess) return LABS_ECUDA;
-  ++launches;
-  cudaEventRecord(e1, s);
-  // harvest
-  const int n = cfg.max_active;
-  std::vector<int32_t> done(n), rounds(n);
-  std::vector<int64_t> bestE(n);
-  std::vector<unsigned long long> evals(n);
-  int32_t err = 0;
-  std::vector<unsigned long long> run_evals(nslots);
-  if (cudaMemcpyAsync(run_evals.data(), d_slot_evals, sizeof(unsigned long long) * nslots, cudaMemcpyDeviceToHost,
-                      s) != cudaSuccess ||
-      cudaMemcpyAsync(done.data(), d_done, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(rounds.data(), d_rounds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(bestE.data(), d_bestE, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(evals.data(), d_evals, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  walk_launches += (uint64_t)l.walk_kernels;
+  launches += (uint64_t)l.walk_kernels;
+  if (cudaMemsetAsync(l.snap.run_evals, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      launch_batch_finalize(d_plist, (int)cv.n_problems, rec, ps, s) != cudaSuccess ||
+      launch_snapshot(d_plist, (int)cv.n_problems, d_probs, ps, reinterpret_cast<const uint32_t *>(a + cv.recs),
+                      (int)cv.n_issue, rec, l.snap, s) != cudaSuccess)
     return LABS_ECUDA;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  busy_ms += ms;
-  if (err) return (err & kErrOverflow) ? LABS_EOVERFLOW : LABS_ECHECK;
-  std::vector<int> finished_slots;
-  for (int sl : active)
-    if (done[sl]) finished_slots.push_back(sl);
-  // sequences of the finished requests
-  std::vector<std::vector<int8_t>> seqs(finished_slots.size());
-  for (size_t i = 0; i < finished_slots.size(); ++i) {
-    const int sl = finished_slots[i];
-    int L;
-    {
-      std::lock_guard<std::mutex> lock(mu);
-      L = reqs[slot_ticket[sl]]->p.L;
-    }
-    seqs[i].resize(L);
-    if (launch_expand(1, L, d_key + (size_t)sl * kKeyWords, kKeyWords, d_seq, s) != cudaSuccess ||
-        cudaMemcpyAsync(seqs[i].data(), d_seq, (size_t)L, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return LABS_ECUDA;
-    ++launches;
-  }
+  launches += 2;
+  if (cudaMemcpyAsync(l.snap_err, d_err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(l.h_snap, l.d_snap, l.snap_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaEventRecord(l.ev1, s) != cudaSuccess)
+    return LABS_ECUDA;
+  l.in_flight = true;
+  return LABS_OK;
+}
+
+// Take in a completed launch's snapshot: every listed request's progress;
+// finished requests get their results; slots no launch in flight lists any
+// more become free.
+labs_status labs_server::harvest(Launch &l) {
+  if (cudaEventSynchronize(l.ev1) != cudaSuccess) return LABS_ECUDA;
+  l.in_flight = false;
+  float t0 = 0.f, t1 = 0.f;
+  cudaEventElapsedTime(&t0, t_ref, l.ev0);
+  cudaEventElapsedTime(&t1, t_ref, l.ev1);
+  auto at = [&](const void *dev) { return l.h_snap + ((const char *)dev - l.d_snap); };
+  const int32_t err = *reinterpret_cast<const int32_t *>(at(l.snap_err));
+  if (err & kErrOverflow) return LABS_EOVERFLOW;
+  if (err & kErrRecheck) return LABS_ECHECK;
+  if (err) return LABS_ECUDA;
+  const int32_t *done = reinterpret_cast<const int32_t *>(at(l.snap.done));
+  const int32_t *rounds = reinterpret_cast<const int32_t *>(at(l.snap.rounds));
+  const int64_t *bestE = reinterpret_cast<const int64_t *>(at(l.snap.bestE));
+  const unsigned long long *evals = reinterpret_cast<const unsigned long long *>(at(l.snap.evals));
+  const unsigned long long *planes = reinterpret_cast<const unsigned long long *>(at(l.snap.planes));
+  const int8_t *seqs = reinterpret_cast<const int8_t *>(at(l.snap.seq));
+  const unsigned long long run = *reinterpret_cast<const unsigned long long *>(at(l.snap.run_evals));
   const uint64_t t = now_ns();
   std::lock_guard<std::mutex> lock(mu);
-  for (unsigned long long x : run_evals) evals_run += x;
-  for (int sl : active) {
+  harvested = l.id;
+  // device time: the union of the launches' intervals
+  const double b0 = std::max<double>(t0, busy_end_ms);
+  if (t1 > b0) busy_ms += t1 - b0;
+  busy_end_ms = std::max<double>(busy_end_ms, t1);
+  mem_peak = std::max(mem_peak, l.carve_bytes);
+  evals_run += run;
+  bool any = false;
+  for (int sl : l.slots) {
+    if (!slot_ticket[sl] || slot_draining[sl]) continue;
     Request &r = *reqs[slot_ticket[sl]];
-    evals_done += evals[sl] - r.evals;
-    r.evals = evals[sl];
-    r.rounds = rounds[sl];
-    r.next_round = rounds[sl];
-    r.bestE = bestE[sl];
+    {
+      evals_done += evals[sl] - r.evals;
+      r.evals = evals[sl];
+      r.planes = planes[sl];
+      r.rounds = rounds[sl];
+      r.bestE = bestE[sl];
+      if (done[sl]) {
+        r.seq.assign(seqs + (size_t)sl * kSeqStride, seqs + (size_t)sl * kSeqStride + r.p.L);
+        r.t_done = t;
+        r.status = LABS_OK;
+        ++n_completed;
+        any = true;
+        slot_draining[sl] = 1;
+      }
+    }
   }
-  for (size_t i = 0; i < finished_slots.size(); ++i) {
-    const int sl = finished_slots[i];
-    Request &r = *reqs[slot_ticket[sl]];
-    r.seq = std::move(seqs[i]);
-    r.t_done = t;
-    r.status = LABS_OK;
-    r.slot = -1;
-    mem_used -= r.mem_cost;
-    slot_ticket[sl] = 0;
-    ++n_completed;
+  // a finished request's slot is free once no launch in flight lists it
+  for (int sl = 0; sl < cfg.max_active; ++sl) {
+    if (slot_ticket[sl] && slot_draining[sl] && slot_listed[sl] <= harvested) {
+      slot_ticket[sl] = 0;
+      slot_draining[sl] = 0;
+    }
   }
-  if (!finished_slots.empty()) finished.notify_all();
+  mem_used = admitted_carve(nullptr);
+  if (any) finished.notify_all();
   return LABS_OK;
+}
+
+void labs_server::fail_all(labs_status why) {
+  std::lock_guard<std::mutex> lock(mu);
+  if (failed == LABS_OK && why != LABS_ESHUTDOWN) failed = why;
+  for (auto &kv : reqs)
+    if (kv.second->status == LABS_PENDING) {
+      kv.second->status = why;
+      kv.second->t_done = now_ns();
+    }
+  pending.clear();
+  std::fill(slot_ticket.begin(), slot_ticket.end(), 0ull);
+  std::fill(slot_draining.begin(), slot_draining.end(), (uint8_t)0);
+  mem_used = 0;
+  finished.notify_all();
 }
 
 void labs_server::loop() {
   cudaSetDevice(device);
+  std::deque<int> inflight;  // indices into L, oldest first
+  uint64_t next_id = 1;
+  labs_status st = LABS_OK;
+  auto harvest_oldest = [&]() {
+    st = harvest(L[inflight.front()]);
+    inflight.pop_front();
+  };
   for (;;) {
-    std::vector<int> active, admitted;
-    std::vector<BatchProblem> adm_probs;
-    std::vector<uint64_t> adm_budget;
-    std::vector<int64_t> adm_target;
+    bool stop;
     {
-      std::unique_lock<std::mutex> lock(mu);
-      for (;;) {
-        if (stopping || failed != LABS_OK) break;
-        // admit in arrival order while a slot is free and the working set fits
-        while (!pending.empty()) {
-          Request &r = *reqs[pending.front()];
-          if (mem_used + r.mem_cost > cfg.mem_bytes) break;
-          auto it = std::find(slot_ticket.begin(), slot_ticket.end(), 0ull);
-          if (it == slot_ticket.end()) break;
-          const int sl = (int)(it - slot_ticket.begin());
-          *it = r.ticket;
-          r.slot = sl;
-          r.t_admit = now_ns();
-          mem_used += r.mem_cost;
-          pending.pop_front();
-          admitted.push_back(sl);
-          BatchProblem bp{};
-          bp.L = r.p.L;
-          bp.W = r.W;
-          bp.walk_len = r.p.walk_len;
-          bp.walks = r.p.walks;
-          bp.cap = visited_table_cap(r.p.walk_len, kTableFactor);
-          bp.kw64 = key_words64((r.p.L + 1) / 2);
-          bp.seed = r.p.seed;
-          adm_probs.push_back(bp);
-          adm_budget.push_back(r.p.step_budget);
-          adm_target.push_back(r.p.target_E);
-        }
-        for (int sl = 0; sl < cfg.max_active; ++sl)
-          if (slot_ticket[sl]) active.push_back(sl);
-        if (!active.empty()) break;
-        wake.wait_for(lock, std::chrono::milliseconds(20));
-      }
-      if (stopping || failed != LABS_OK) {
-        // shutdown: run nothing more; everything still queued or admitted ends with a status
-        labs_status why = failed != LABS_OK ? failed : LABS_ESHUTDOWN;
-        for (auto &kv : reqs)
-          if (kv.second->status == LABS_PENDING) {
-            kv.second->status = why;
-            kv.second->t_done = now_ns();
-          }
-        pending.clear();
-        std::fill(slot_ticket.begin(), slot_ticket.end(), 0ull);
-        mem_used = 0;
-        finished.notify_all();
-        break;
-      }
-    }
-    labs_status st = LABS_OK;
-    if (!admitted.empty()) {
-      // write the new requests into their slots and reset the slots' state
-      for (size_t i = 0; i < admitted.size() && st == LABS_OK; ++i) {
-        const int sl = admitted[i];
-        if (cudaMemcpyAsync(d_probs + sl, &adm_probs[i], sizeof(BatchProblem), cudaMemcpyHostToDevice, s) ||
-            cudaMemcpyAsync(d_budget + sl, &adm_budget[i], sizeof(uint64_t), cudaMemcpyHostToDevice, s) ||
-            cudaMemcpyAsync(d_target + sl, &adm_target[i], sizeof(int64_t), cudaMemcpyHostToDevice, s))
-          st = LABS_ECUDA;
-      }
-      if (st == LABS_OK &&
-          (cudaMemcpyAsync(d_init_list, admitted.data(), sizeof(int32_t) * admitted.size(), cudaMemcpyHostToDevice,
-                           s) != cudaSuccess ||
-           launch_init_slots(d_init_list, (int)admitted.size(), d_bestE, d_evals, d_done, d_rounds, d_best_round,
-                             d_best_walk, d_key, s) != cudaSuccess ||
-           cudaStreamSynchronize(s) != cudaSuccess))
-        st = LABS_ECUDA;
-      ++launches;
-    }
-    if (st == LABS_OK) st = step(active);
-    if (st != LABS_OK) {
       std::lock_guard<std::mutex> lock(mu);
-      failed = st;
-      for (auto &kv : reqs)
-        if (kv.second->status == LABS_PENDING) {
-          kv.second->status = st;
-          kv.second->t_done = now_ns();
-        }
-      pending.clear();
-      std::fill(slot_ticket.begin(), slot_ticket.end(), 0ull);
-      mem_used = 0;
-      finished.notify_all();
-      break;
+      stop = stopping;
     }
+    if (stop || st != LABS_OK) break;
+    // take in the launches that have completed, oldest first
+    while (st == LABS_OK && !inflight.empty() && cudaEventQuery(L[inflight.front()].ev1) == cudaSuccess)
+      harvest_oldest();
+    if (st != LABS_OK) break;
+    if ((int)inflight.size() == kDepth) {
+      harvest_oldest();
+      continue;
+    }
+    // admit in arrival order while a slot is free and a launch over all
+    // admitted requests still fits its half of the arena
+    std::vector<int> admitted;
+    bool work = false;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      while (!pending.empty()) {
+        Request &r = *reqs[pending.front()];
+        auto it = std::find(slot_ticket.begin(), slot_ticket.end(), 0ull);
+        if (it == slot_ticket.end()) break;
+        const size_t need = admitted_carve(&r);
+        if (need > half_bytes) break;
+        const int sl = (int)(it - slot_ticket.begin());
+        *it = r.ticket;
+        r.slot = sl;
+        r.t_admit = now_ns();
+        mem_used = need;
+        pending.pop_front();
+        admitted.push_back(sl);
+      }
+      for (int sl = 0; sl < cfg.max_active && !work; ++sl)
+        if (slot_ticket[sl] && !slot_draining[sl] && rounds_to_issue(*reqs[slot_ticket[sl]], cfg.rounds_per_launch,
+                                                                       ring) > 0)
+          work = true;
+    }
+    if (work || !admitted.empty()) {
+      Launch &l = L[(next_id - 1) % kDepth];
+      l.id = next_id++;
+      st = enqueue(l, admitted);
+      if (st != LABS_OK) break;
+      inflight.push_back((int)((l.id - 1) % kDepth));
+      continue;
+    }
+    if (!inflight.empty()) {
+      harvest_oldest();
+      continue;
+    }
+    std::unique_lock<std::mutex> lock(mu);
+    if (!stopping && pending.empty()) wake.wait_for(lock, std::chrono::milliseconds(20));
   }
+  // device work must end before teardown; requests not finished end with a status
+  for (int li : inflight) cudaEventSynchronize(L[li].ev1);
+  fail_all(st != LABS_OK ? st : LABS_ESHUTDOWN);
 }
 
 extern "C" void labs_serve_cfg_init(labs_serve_cfg *c) {
@@ -448,7 +543,7 @@ extern "C" void labs_serve_cfg_init(labs_serve_cfg *c) {
   c->max_L = 301;
   c->max_walks = 2048;
   c->max_walk_len = 0;
-  c->rounds_per_launch = 8;  // measured: 8 beat 1, 2, 4 and 16 on throughput and median latency
+  c->rounds_per_launch = 4;
   c->block_threads = 128;
 }
 
@@ -462,62 +557,141 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   if (cfg.max_active <= 0 || cfg.max_active > 4096 || cfg.max_L < LABS_L_MIN || cfg.max_L > LABS_L_MAX ||
       !(cfg.max_L & 1) || cfg.max_walks <= 0 || cfg.max_walks > (1 << 20) || cfg.max_walk_len < 0 ||
       cfg.rounds_per_launch <= 0 || cfg.rounds_per_launch > 64 || cfg.block_threads < 32 ||
-      cfg.block_threads > 256 || cfg.block_threads % 32 || cfg.mem_bytes == 0)
+      cfg.block_threads > 256 || cfg.block_threads % 32 || cfg.mem_bytes < 2 * kAlign)
     return LABS_EINVAL;
   if (cfg.max_walk_len == 0) cfg.max_walk_len = 8 * ((cfg.max_L + 1) / 2);
   labs_server *sv = new (std::nothrow) labs_server();
   if (!sv) return LABS_ENOMEM;
   sv->cfg = cfg;
-  sv->t_created = now_ns();
   auto fail = [&](labs_status e) {
     delete sv;
     return e;
   };
   if (cudaGetDevice(&sv->device) != cudaSuccess) return fail(LABS_ECUDA);
-  if (cfg.stream) {
-    sv->s = (cudaStream_t)cfg.stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&sv->s, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
-    sv->own_stream = true;
-  }
   const int n = cfg.max_active;
-  sv->max_chunks = (uint32_t)((cfg.max_walks + 31) / 32);
-  sv->max_slots = (uint32_t)n * (uint32_t)cfg.rounds_per_launch;
-  sv->slot_ticket.assign(n, 0);
-  if (dalloc(&sv->d_probs, n) || dalloc(&sv->d_budget, n) || dalloc(&sv->d_target, n) || dalloc(&sv->d_done, n) ||
-      dalloc(&sv->d_best_round, n) || dalloc(&sv->d_best_walk, n) || dalloc(&sv->d_rounds, n) ||
-      dalloc(&sv->d_bestE, n) || dalloc(&sv->d_key, (size_t)n * kKeyWords) || dalloc(&sv->d_evals, n) ||
-      dalloc(&sv->d_init_list, n) || dalloc(&sv->d_slot_best, sv->max_slots) ||
-      dalloc(&sv->d_slot_evals, sv->max_slots) ||
-      dalloc(&sv->d_slot_keys, (size_t)sv->max_slots * sv->max_chunks * kKeyWords) ||
-      dalloc(&sv->d_slot_round, sv->max_slots) || dalloc(&sv->d_first_slot, n) || dalloc(&sv->d_n_slots, n) ||
-      dalloc(&sv->d_planes, 1) || dalloc(&sv->d_err, 1) || dalloc(&sv->d_seq, LABS_L_MAX + 1))
-    return fail(LABS_ENOMEM);
-  if (cudaMemset(sv->d_done, 0xFF, sizeof(int32_t) * n) != cudaSuccess ||  // free slots count as finished
-      cudaMemset(sv->d_err, 0, sizeof(int32_t)) != cudaSuccess || cudaMemset(sv->d_planes, 0, 8) != cudaSuccess)
-    return fail(LABS_ECUDA);
-  // one visited-table pool per lag-word class up to max_L, sized for the
-  // largest L and walk length that class accepts
   const int Wmax = lag_words(cfg.max_L);
-  if (dalloc(&sv->d_task_next, Wmax)) return fail(LABS_ENOMEM);
-  for (int W = 1; W <= Wmax; ++W) {
-    ClassPool c;
-    c.W = W;
-    const int Lmax = std::min(cfg.max_L, 64 * W + 1);
-    c.words = (size_t)visited_table_cap(cfg.max_walk_len, kTableFactor) * key_words64((Lmax + 1) / 2);
-    c.words = (c.words + 1) / 2 * 2;
-    c.resident = batch_resident_lanes(W, cfg.block_threads);
-    if (c.resident <= 0) return fail(LABS_ECUDA);
-    sv->pools.push_back(c);
-    if (dalloc(&sv->pools.back().pool, (size_t)c.resident * c.words)) return fail(LABS_ENOMEM);
-    cudaStream_t x;
-    cudaEvent_t e;
-    if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
-    sv->cs.push_back(x);
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
-    sv->cs_done.push_back(e);
+  const uint32_t ring = (uint32_t)(kRingFactor * cfg.rounds_per_launch);
+  const uint32_t max_chunks = (uint32_t)((cfg.max_walks + 31) / 32);
+  const size_t nrec = (size_t)n * ring;
+  sv->ring = ring;
+  sv->slot_ticket.assign(n, 0);
+  sv->slot_listed.assign(n, 0);
+  sv->slot_draining.assign(n, 0);
+  // fixed state: per slot, then the round records
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t o_probs = take(sizeof(BatchProblem) * n), o_base = take(sizeof(uint32_t) * n),
+               o_ring = take(sizeof(uint32_t) * n), o_budget = take(sizeof(uint64_t) * n),
+               o_target = take(sizeof(int64_t) * n), o_fin = take(sizeof(uint32_t) * n),
+               o_done = take(sizeof(int32_t) * n), o_bestE = take(sizeof(int64_t) * n),
+               o_key = take(sizeof(uint32_t) * kKeyWords * n), o_brnd = take(sizeof(int32_t) * n),
+               o_bwalk = take(sizeof(int32_t) * n), o_evals = take(sizeof(unsigned long long) * n),
+               o_planes = take(sizeof(unsigned long long) * n), o_rounds = take(sizeof(int32_t) * n),
+               o_err = take(sizeof(int32_t)),
+               o_rbest = take(sizeof(unsigned long long) * nrec), o_revals = take(sizeof(unsigned long long) * nrec),
+               o_rplanes = take(sizeof(unsigned long long) * nrec), o_rleft = take(sizeof(uint32_t) * nrec),
+               o_rround = take(sizeof(uint32_t) * nrec), o_rkeys = take(sizeof(uint32_t) * kKeyWords * nrec * max_chunks);
+  char *fb = nullptr;
+  if (cudaMalloc((void **)&fb, off) != cudaSuccess) return fail(LABS_ENOMEM);
+  sv->fixed = fb;
+  sv->fixed_bytes = off;
+  if (cudaMemset(fb, 0, off) != cudaSuccess) return fail(LABS_ECUDA);
+  sv->d_probs = reinterpret_cast<BatchProblem *>(fb + o_probs);
+  sv->d_err = reinterpret_cast<int32_t *>(fb + o_err);
+  ProblemState &ps = sv->ps;
+  ps.rec_base = reinterpret_cast<uint32_t *>(fb + o_base);
+  ps.ring = reinterpret_cast<uint32_t *>(fb + o_ring);
+  ps.budget = reinterpret_cast<uint64_t *>(fb + o_budget);
+  ps.target = reinterpret_cast<int64_t *>(fb + o_target);
+  ps.fin = reinterpret_cast<uint32_t *>(fb + o_fin);
+  ps.done = reinterpret_cast<int32_t *>(fb + o_done);
+  ps.bestE = reinterpret_cast<int64_t *>(fb + o_bestE);
+  ps.key = reinterpret_cast<uint32_t *>(fb + o_key);
+  ps.best_round = reinterpret_cast<int32_t *>(fb + o_brnd);
+  ps.best_walk = reinterpret_cast<int32_t *>(fb + o_bwalk);
+  ps.evals = reinterpret_cast<unsigned long long *>(fb + o_evals);
+  ps.planes = reinterpret_cast<unsigned long long *>(fb + o_planes);
+  ps.rounds = reinterpret_cast<int32_t *>(fb + o_rounds);
+  RoundRecords &rec = sv->rec;
+  rec.best = reinterpret_cast<unsigned long long *>(fb + o_rbest);
+  rec.evals = reinterpret_cast<unsigned long long *>(fb + o_revals);
+  rec.planes = reinterpret_cast<unsigned long long *>(fb + o_rplanes);
+  rec.left = reinterpret_cast<uint32_t *>(fb + o_rleft);
+  rec.round = reinterpret_cast<uint32_t *>(fb + o_rround);
+  rec.keys = reinterpret_cast<uint32_t *>(fb + o_rkeys);
+  rec.max_chunks = max_chunks;
+  {
+    std::vector<uint32_t> base(n), rng(n, ring);
+    for (int i = 0; i < n; ++i) base[i] = (uint32_t)i * ring;
+    std::vector<int32_t> done(n, 1);  // free slots count as finished
+    if (cudaMemcpy(fb + o_base, base.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(fb + o_ring, rng.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(fb + o_done, done.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(fb + o_rround, 0xFF, sizeof(uint32_t) * nrec) != cudaSuccess)
+      return fail(LABS_ECUDA);
   }
-  if (cudaEventCreateWithFlags(&sv->fork, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
+  sv->half_bytes = cfg.mem_bytes / 2 / kAlign * kAlign;
+  if (cudaMalloc((void **)&sv->arena, cfg.mem_bytes) != cudaSuccess) return fail(LABS_ENOMEM);
+  for (int W = 1; W <= Wmax; ++W) {
+    const int res = batch_resident_lanes(W, cfg.block_threads);
+    if (res <= 0) return fail(LABS_ECUDA);
+    sv->resident.push_back(res);
+  }
+  // the launches in flight: streams, events, arena halves, snapshots
+  for (int d = 0; d < kDepth; ++d) {
+    Launch &l = sv->L[d];
+    l.arena = sv->arena + (size_t)d * sv->half_bytes;
+    if (cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
+    for (int W = 1; W <= Wmax; ++W) {
+      cudaStream_t x;
+      cudaEvent_t e;
+      if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return fail(LABS_ECUDA);
+      l.cs.push_back(x);
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(LABS_ECUDA);
+      l.cs_done.push_back(e);
+    }
+    if (cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&l.ev0) != cudaSuccess || cudaEventCreate(&l.ev1) != cudaSuccess)
+      return fail(LABS_ECUDA);
+    size_t so = 0;
+    auto stake = [&](size_t bytes) {
+      const size_t o = so;
+      so = align_up(so + bytes);
+      return o;
+    };
+    const size_t s_done = stake(sizeof(int32_t) * n), s_rounds = stake(sizeof(int32_t) * n),
+                 s_bestE = stake(sizeof(int64_t) * n), s_evals = stake(sizeof(unsigned long long) * n),
+                 s_planes = stake(sizeof(unsigned long long) * n), s_seq = stake((size_t)kSeqStride * n),
+                 s_next = stake(sizeof(unsigned int) * Wmax), s_init = stake(sizeof(int32_t) * n),
+                 s_run = stake(sizeof(unsigned long long)), s_err = stake(sizeof(int32_t));
+    if (cudaMalloc((void **)&l.d_snap, so) != cudaSuccess) return fail(LABS_ENOMEM);
+    if (cudaMallocHost((void **)&l.h_snap, so) != cudaSuccess) return fail(LABS_ENOMEM);
+    if (cudaMemset(l.d_snap, 0, so) != cudaSuccess) return fail(LABS_ECUDA);
+    sv->fixed_bytes += so;
+    l.snap.done = reinterpret_cast<int32_t *>(l.d_snap + s_done);
+    l.snap.rounds = reinterpret_cast<int32_t *>(l.d_snap + s_rounds);
+    l.snap.bestE = reinterpret_cast<int64_t *>(l.d_snap + s_bestE);
+    l.snap.evals = reinterpret_cast<unsigned long long *>(l.d_snap + s_evals);
+    l.snap.planes = reinterpret_cast<unsigned long long *>(l.d_snap + s_planes);
+    l.snap.seq = reinterpret_cast<int8_t *>(l.d_snap + s_seq);
+    l.snap.stride = kSeqStride;
+    l.task_next = reinterpret_cast<unsigned int *>(l.d_snap + s_next);
+    l.snap.run_evals = reinterpret_cast<unsigned long long *>(l.d_snap + s_run);
+    l.init_list = reinterpret_cast<int32_t *>(l.d_snap + s_init);
+    l.snap_err = reinterpret_cast<int32_t *>(l.d_snap + s_err);
+    l.snap_bytes = so;
+  }
+  if (cudaEventCreate(&sv->t_ref) != cudaSuccess) return fail(LABS_ECUDA);
+  // the server's work starts after what the caller's stream has queued
+  cudaStream_t first = cfg.stream ? (cudaStream_t)cfg.stream : nullptr;
+  if (cudaEventRecord(sv->t_ref, first) != cudaSuccess) return fail(LABS_ECUDA);
+  for (int d = 0; d < kDepth; ++d)
+    if (cudaStreamWaitEvent(sv->L[d].s, sv->t_ref, 0) != cudaSuccess) return fail(LABS_ECUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(LABS_ECUDA);
   try {
     sv->th = std::thread([sv]() { sv->loop(); });
   } catch (...) {
@@ -532,15 +706,17 @@ extern "C" labs_status labs_serve_submit(labs_server *sv, const labs_problem *re
   const labs_problem &p = *req;
   if (p.L < LABS_L_MIN || p.L > LABS_L_MAX || !(p.L & 1) || p.walks < 1 || p.walk_len < 1 || p.step_budget < 1)
     return LABS_EINVAL;
-  // requests that can never be admitted
-  if (p.L > sv->cfg.max_L || p.walks > sv->cfg.max_walks || p.walk_len > sv->cfg.max_walk_len ||
-      request_cost(p, sv->cfg.rounds_per_launch) > sv->cfg.mem_bytes)
-    return LABS_ENOMEM;
+  // requests that can never be admitted: above the server's limits, or a
+  // launch over this request alone does not fit half the arena
+  if (p.L > sv->cfg.max_L || p.walks > sv->cfg.max_walks || p.walk_len > sv->cfg.max_walk_len) return LABS_ENOMEM;
+  {
+    std::vector<Share> one{share_of(-1, p, (uint32_t)sv->cfg.rounds_per_launch)};
+    if (carve_launch(one, sv->resident, sv->cfg.block_threads).total > sv->half_bytes) return LABS_ENOMEM;
+  }
   auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
   if (!r) return LABS_ENOMEM;
   r->p = p;
   r->W = lag_words(p.L);
-  r->mem_cost = request_cost(p, sv->cfg.rounds_per_launch);
   r->t_submit = now_ns();
   std::lock_guard<std::mutex> lock(sv->mu);
   if (sv->stopping) return LABS_ESHUTDOWN;
@@ -568,6 +744,7 @@ static void fill_result(const Request &r, labs_result *out, int8_t *best_seq) {
     out->t_admit_ns = r.t_admit;
     out->t_done_ns = r.t_done;
     out->p_optimal = labs_model_p_optimal(r.p.L, labs_model_nses_of_evals(r.p.L, r.evals));
+    out->plane_steps = r.planes;
   }
   if (best_seq && r.status == LABS_OK) std::memcpy(best_seq, r.seq.data(), r.seq.size());
 }
@@ -615,7 +792,7 @@ extern "C" labs_status labs_serve_get_stats(labs_server *sv, labs_serve_stats *o
   out->completed = sv->n_completed;
   out->pending = sv->pending.size();
   int act = 0;
-  for (auto t : sv->slot_ticket) act += t != 0;
+  for (size_t i = 0; i < sv->slot_ticket.size(); ++i) act += sv->slot_ticket[i] != 0 && !sv->slot_draining[i];
   out->active = (uint64_t)act;
   out->evals = sv->evals_done;
   out->evals_run = sv->evals_run;
@@ -623,6 +800,8 @@ extern "C" labs_status labs_serve_get_stats(labs_server *sv, labs_serve_stats *o
   out->walk_launches = sv->walk_launches;
   out->busy_ms = sv->busy_ms;
   out->mem_used = sv->mem_used;
+  out->mem_peak = sv->mem_peak;
+  out->fixed_bytes = sv->fixed_bytes;
   out->status = sv->failed;
   return LABS_OK;
 }
@@ -635,7 +814,6 @@ extern "C" labs_status labs_serve_destroy(labs_server *sv) {
     sv->wake.notify_all();
   }
   if (sv->th.joinable()) sv->th.join();
-  cudaStreamSynchronize(sv->s);
   delete sv;
   return LABS_OK;
 }

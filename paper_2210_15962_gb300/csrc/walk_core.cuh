@@ -852,4 +852,14 @@ LABS_HD void table_store(uint64_t *table, uint32_t slot, int KW64, const uint32_
 
 LABS_HD int key_words64(int D) { return (D + 1 + 63) / 64; }
 
+// Bit of position a (0-based; 1 <-> -1) of the length-L sequence whose key is
+// k: a skew key holds the D free values and Eq. 2 gives the rest,
+// s_{c+i} = (-1)^i s_{c-i} with c = D-1; a full-space key is the sequence.
+LABS_HD uint32_t sequence_bit(const uint32_t *k, int L, int a, bool full) {
+  const int c = (L - 1) / 2;
+  if (full || a <= c) return (k[a >> 5] >> (a & 31)) & 1u;
+  const int i = a - c, src = c - i;
+  return ((k[src >> 5] >> (src & 31)) & 1u) ^ (uint32_t)(i & 1);
+}
+
 }  // namespace psaw

@@ -81,15 +81,7 @@ __global__ void expand_kernel(int n, int L, const uint32_t *keys, size_t key_str
   if (idx >= (size_t)n * (size_t)L) return;
   const int p = (int)(idx / (size_t)L);
   const int a = (int)(idx - (size_t)p * (size_t)L);
-  const int c = (L - 1) / 2;
-  const uint32_t *k = keys + (size_t)p * key_stride;
-  uint32_t b;
-  if (full || a <= c) {
-    b = (k[a >> 5] >> (a & 31)) & 1u;
-  } else {
-    const int i = a - c, src = c - i;
-    b = ((k[src >> 5] >> (src & 31)) & 1u) ^ (uint32_t)(i & 1);
-  }
+  const uint32_t b = sequence_bit(keys + (size_t)p * key_stride, L, a, full != 0);
   seq_out[(size_t)p * L + a] = b ? (int8_t)-1 : (int8_t)1;
 }
 

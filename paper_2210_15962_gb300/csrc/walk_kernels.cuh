@@ -19,6 +19,7 @@ constexpr int32_t kVariantIncremental = 2;  // stored Delta_j updated after each
 enum ErrorBits : int32_t {
   kErrRecheck = 1,   // incremental state disagreed with the XOR+popc recheck
   kErrOverflow = 2,  // a visited table ran out of slots
+  kErrIncomplete = 4,  // a batch round needed for a result did not complete (a scheduling bug)
 };
 
 // search spaces: the skew-symmetric sequences of odd L, or all sequences

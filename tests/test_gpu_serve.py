@@ -83,19 +83,35 @@ def test_requests_arriving_while_others_run(m):
     assert any(r["t_done_ns"] < results[0]["t_done_ns"] for r in results[1:])
 
 
+def launch_bytes(walks, walk_len, L, rounds):
+    """Arena bytes of one launch over one request that runs `rounds` rounds: a visited
+    table (power-of-two slots >= 1.5 x pivots, 64-bit words of D + 1 bits) for each
+    walk of each round in flight, plus its lists (under 64 KiB here)."""
+    slots = 64
+    while slots < (walk_len + 1) * 15 // 10 + 1:
+        slots *= 2
+    words = slots * (((L + 1) // 2 + 1 + 63) // 64)
+    words += words % 2
+    return ((walks + 31) // 32) * 32 * rounds * words * 8
+
+
 def test_memory_admission_serialises_and_rejects(m):
     big = (121, 256, 488, 7, 256 * 488 * 61 * 3)
-    # a budget that holds one such request at a time
-    one = 256 * 1024 * 8 + 4096 * 2  # 256 walks x 1024-slot tables x 8 B + round state
-    with m.Server(max_walks=256, mem_bytes=int(one * 1.5)) as sv:
+    rpl = 4
+    one = launch_bytes(256, 488, 121, rpl)
+    # each of the two launches in flight gets half of the arena: room for one such request, not two
+    mem = 2 * (one + (64 << 10))
+    with m.Server(max_walks=256, mem_bytes=mem, rounds_per_launch=rpl) as sv:
         t1 = sv.submit(*big)
         t2 = sv.submit(121, 256, 488, 8, 256 * 488 * 61)
         r1, r2 = sv.wait(t1), sv.wait(t2)
         check(m, big, r1)
         check(m, (121, 256, 488, 8, 256 * 488 * 61), r2)
         assert r2["t_admit_ns"] >= r1["t_done_ns"]  # admitted only once the first left
+        st = sv.stats()
+        assert 0 < st["mem_peak"] <= mem // 2
         with pytest.raises(m.LabsError) as ei:
-            sv.submit(121, 256, 4000, 9, 10 ** 9)  # working set above the budget
+            sv.submit(121, 256, 4000, 9, 10 ** 9)  # one launch of it alone exceeds half the arena
         assert ei.value.status == m.LABS_ENOMEM
         with pytest.raises(m.LabsError) as ei:
             sv.submit(401, 64, 100, 9, 10 ** 6)  # above the server's max_L
@@ -103,6 +119,31 @@ def test_memory_admission_serialises_and_rejects(m):
         with pytest.raises(m.LabsError) as ei:
             sv.submit(120, 64, 100, 9, 10 ** 6)  # even L
         assert ei.value.status == m.LABS_EINVAL
+
+
+def test_device_bytes_stay_within_the_arena_while_requests_queue(m):
+    # requests of three classes queue behind a small arena; the bytes any launch
+    # uses never exceed its half, every request completes and matches labs_walks
+    reqs = [(121, 128, 488, 40 + i, 128 * 488 * 61 * 2) for i in range(3)] + \
+           [(161, 96, 648, 50 + i, 96 * 648 * 81 * 2) for i in range(2)] + [(223, 64, 896, 60, 64 * 896 * 112)]
+    rpl = 2
+    mem = 2 * (launch_bytes(128, 488, 121, rpl) + launch_bytes(64, 896, 223, rpl) + (256 << 10))
+    with m.Server(max_walks=128, mem_bytes=mem, rounds_per_launch=rpl) as sv:
+        tickets = [sv.submit(*p) for p in reqs]
+        seen = []
+        while len(seen) < 400:
+            st = sv.stats()
+            seen.append((st["mem_used"], st["mem_peak"], st["pending"]))
+            if st["completed"] == len(reqs):
+                break
+            time.sleep(0.005)
+        results = [sv.wait(t) for t in tickets]
+        st = sv.stats()
+    assert all(u <= mem // 2 and pk <= mem // 2 for u, pk, _ in seen)
+    assert 0 < st["mem_peak"] <= mem // 2
+    assert any(q > 0 for _, _, q in seen)  # requests did wait for memory
+    for p, r in zip(reqs, results):
+        check(m, p, r)
 
 
 def test_tickets_timeouts_and_shutdown(m):
