@@ -38,6 +38,7 @@ WALK_LEN = 8192
 BUDGET = 10 ** 11
 SEED = 1
 INT_LANES_PER_SM = 64          # int32 ALU-pipe lanes per SM per clock (LOP3/SHF/IADD3 class)
+POPC_LANES_PER_SM = 16         # population counts per SM per clock (XU pipe)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -73,6 +74,55 @@ def core_alu_ops_per_eval(L, planes, full=False):
     (L-1)/2 even ones of a skew sequence or all L-1 in the full space."""
     m = (L - 1) if full else (L - 1) // 2
     return 4.0 * planes * m / 32.0
+
+
+def popc_words_per_step(L):
+    """(nw, n2) of the skew scan's formulation at length L, summed over the D
+    flips of one walk step: nw = 32-lag words holding any valid lag of the
+    flip, n2 = words holding valid lags on both sides.  A flip j (position
+    a = j, class q = a % 2, index t = a // 2) has x-side lags i = 1..t and
+    y-side lags i = 1..N_q-1-t without the lag of its own mirror pair
+    (c - a), N_q = D - q, and no y side at the centre a = c = D - 1."""
+    D, m = (L + 1) // 2, (L - 1) // 2
+    c, W = D - 1, (m + 31) // 32
+    nw = n2 = 0
+    for a in range(D):
+        q, t = a & 1, a >> 1
+        xs_hi = t                       # x lags 1..t
+        ys = set() if a == c else set(range(1, D - q - t)) - {c - a}
+        for w in range(W):
+            lo, hi = 32 * w + 1, 32 * w + 32
+            xw = xs_hi >= lo
+            yw = any(lo <= i <= hi for i in ys)
+            nw += xw or yw
+            n2 += xw and yw
+    return nw, n2
+
+
+def popc_needed(L, evals, plane_steps):
+    """Population counts the bit-sliced evaluation needs for `evals` neighbour
+    evaluations at length L whose steps used `plane_steps` digit planes in all:
+    per flip and 32-lag word, one count per digit plane over the valid lags
+    (TP), plus two for a word with lags on both sides (the top digit of the
+    equal-bits lags and the count of those lags).  One step evaluates D flips."""
+    nw, n2 = popc_words_per_step(L)
+    steps = evals / ((L + 1) // 2)
+    return plane_steps * nw + 2.0 * steps * n2
+
+
+def popc_peak_tops():
+    """The XU pipe: POPC_LANES_PER_SM population counts per SM per clock, all SMs, at the maximum clock."""
+    return SM_COUNT * POPC_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def popc_roofline(needed, seconds, **extra):
+    achieved = needed / seconds / 1e12
+    peak = popc_peak_tops()
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T popcount lane-ops/s (XU pipe)",
+           "frac": achieved / peak,
+           "peak_basis": "152 SMs x 16 POPC lanes/clk/SM x 2070 MHz max clock (of measured: 16.00 lanes/clk)"}
+    out.update(extra)
+    return out
 
 
 class ClockSampler:
@@ -224,11 +274,76 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def measure_batched(args, rank, steps, warmup):
+    """The batched workload: args.instances instances of odd L in [101, 223],
+    args.batch_walks walks each, walk length 8*D, log-uniform budgets in
+    [1e8, 1e10], seed 1000+i (+1000*rank).  The persistent batch path (CUDA
+    graph replay, autotuned shapes) against one labs_walks per instance on the
+    same problems.  Returns the measurements as a dict."""
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    from paper_2210_15962_gb300 import workloads
+    wl = workloads.batched_instances(n=args.instances, walks=args.batch_walks)
+    probs = [(p.L, p.walks, p.walk_len, p.seed + 1000 * rank, p.step_budget) for p in wl.problems]
+    stream = torch.cuda.Stream()
+    b = pkg.Batch(probs, use_graph=True, autotune=True, stream=stream)
+    for _ in range(warmup):
+        b.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ev = launches = wlaunch = 0
+    kms = 0.0
+    for _ in range(steps):
+        st = b.run()
+        ev += st["evals"]
+        launches += st["launches"]
+        kms += st["walk_kernel_ms"]
+        wlaunch += st["walk_launches"]
+    e1.record(stream)
+    e1.synchronize()
+    dev_s = e0.elapsed_time(e1) / 1e3
+    res = b.results()
+    shapes = {W: b.shape(W) for W in sorted({((p[0] - 1) // 2 + 31) // 32 for p in probs})}
+    b.close()
+    # the algorithm's popcounts of one run, from each problem's digit planes (every run is the same)
+    needed = sum(popc_needed(p[0], r["evals"], r["plane_steps"]) for p, r in zip(probs, res))
+    # the plain path: one solve per instance, each its own launch sequence
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    plain_ev = 0
+    same = True
+    t0.record(stream)
+    for i, p in enumerate(probs[:args.plain_instances]):
+        r = pkg.labs_walks(p[0], [p[3]], p[1], p[2], p[4], stream=stream)
+        plain_ev += int(r["evals"][0])
+        same = same and int(r["best_E"][0]) == res[i]["best_E"] and int(r["evals"][0]) == res[i]["evals"] \
+            and bool((r["best_seq"][0] == res[i]["best_seq"]).all())
+    t1.record(stream)
+    t1.synchronize()
+    plain_s = t0.elapsed_time(t1) / 1e3
+    Ls = [p[0] for p in probs]
+    return {
+        "value": ev / dev_s, "unit": "neighbour_evals/s", "steps": steps, "ms_per_step": dev_s * 1e3 / steps,
+        "evals": ev, "seconds": dev_s, "launches": launches, "walk_launches": wlaunch,
+        "config": {"workload": wl.name, "instances": len(probs), "walks": args.batch_walks,
+                   "L_range": [min(Ls), max(Ls)], "walk_len": "8*D",
+                   "budget_range": [min(p[4] for p in probs), max(p[4] for p in probs)],
+                   "path": "batched persistent kernel, CUDA graph replay, autotuned shapes",
+                   "shapes": {str(k): v for k, v in shapes.items()}},
+        "roofline": popc_roofline(needed * steps, kms / 1e3, kernel="batch_kernel<W> (all classes, concurrent)",
+                                  kernel_ms_per_run=kms / steps,
+                                  popc_per_eval=needed / max(1, ev / steps)),
+        "plain": {"value": plain_ev / plain_s, "unit": "neighbour_evals/s",
+                  "instances": min(args.plain_instances, len(probs)),
+                  "path": "labs_walks per instance (one launch sequence per L)", "same_results": bool(same)},
+    }
+
+
 def run_batched(args, world, rank, local):
-    """64 instances of odd L in [101, 223], 2048 walks each, walk length 8*D,
-    log-uniform budgets in [1e8, 1e10], seed 1000+i (weak scaling: rank r adds
-    1000*r to the seeds).  The batched persistent path (one CUDA-graph replay,
-    autotuned shapes) against one labs_walks launch sequence per instance."""
+    """The batched workload on its own (see measure_batched); weak scaling over ranks."""
     import torch
     import paper_2210_15962_gb300 as pkg
     from paper_2210_15962_gb300 import workloads
@@ -238,112 +353,56 @@ def run_batched(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.load()
-    wl = workloads.batched_instances(n=args.instances, walks=args.batch_walks)
-    probs = [(p.L, p.walks, p.walk_len, p.seed + 1000 * rank, p.step_budget) for p in wl.problems]
-    stream = torch.cuda.Stream()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    b = pkg.Batch(probs, use_graph=True, autotune=True, stream=stream)
-    for _ in range(args.warmup):
-        b.run()
-    barrier()
+    if dist is not None:
+        dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ev = launches = planes = 0
-    kms = 0.0
-    wlaunch = 0
-    for _ in range(args.steps):
-        st = b.run()
-        ev += st["evals"]
-        launches += st["launches"]
-        planes += st["plane_steps"]
-        kms += st["walk_kernel_ms"]
-        wlaunch += st["walk_launches"]
-    e1.record(stream)
-    e1.synchronize()
+    m = measure_batched(args, rank, args.steps, args.warmup)
     clocks = sampler.stop()
-    dev_s = e0.elapsed_time(e1) / 1e3
-    res = b.results()
-    shapes = {W: b.shape(W) for W in sorted({((p[0] - 1) // 2 + 31) // 32 for p in probs})}
-    b.close()
-    barrier()
-    # the plain path: one solve per instance, each its own launch sequence
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    plain_ev = 0
-    same = True
-    t0.record(stream)
-    for i, p in enumerate(probs[:args.plain_instances]):
-        r = pkg.labs_walks(p[0], [p[3]], p[1], p[2], p[4], stream=stream)
-        plain_ev += int(r["evals"][0])
-        same = same and int(r["best_E"][0]) == res[i]["best_E"] and int(r["evals"][0]) == res[i]["evals"]
-    t1.record(stream)
-    t1.synchronize()
-    plain_s = t0.elapsed_time(t1) / 1e3
-    (dev_s, plain_s), (tot_ev, tot_plain) = combine_ranks([dev_s, plain_s], [ev, plain_ev], dist, "cuda")
+    (dev_s, _), (tot_ev, _) = combine_ranks([m["seconds"], 0.0], [m["evals"], 0], dist, "cuda")
     if rank == 0:
-        Ls = [p[0] for p in probs]
         line = {
             "metric": "neighbour_evals_per_s", "value": tot_ev / dev_s, "unit": "neighbour_evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (Philox starts; instances from SplitMix64 seed %d)" % workloads.MANIFEST_SEED,
-            "config": {"workload": wl.name, "instances": len(probs), "walks": args.batch_walks,
-                       "L_range": [min(Ls), max(Ls)], "walk_len": "8*D",
-                       "budget_range": [min(p[4] for p in probs), max(p[4] for p in probs)],
-                       "path": "batched persistent kernel, CUDA graph replay, autotuned shapes",
-                       "shapes": {str(k): v for k, v in shapes.items()},
-                       "l2": "visited-table pools larger than L2"},
-            "plain": {"value": tot_plain / plain_s, "unit": "neighbour_evals/s",
-                      "instances": min(args.plain_instances, len(probs)),
-                      "path": "labs_walks per instance (one launch sequence per L)",
-                      "same_results": bool(same)},
-            "gpu_launches": launches,
-            "walk_kernel_ms": kms, "walk_launches": wlaunch,
-            "plane_steps": planes,
-            "clocks": clocks,
+            "config": dict(m["config"], l2="visited-table pools larger than L2"),
+            "roofline": m["roofline"], "plain": m["plain"], "gpu_launches": m["launches"], "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_serving(args, world, rank, local):
+def serving_targets(pkg, Ls, budget):
+    """Per-L target energies: the best the plain path reaches with `budget`
+    evaluations, 2048 walks of 8*D steps, seed 99."""
+    from paper_2210_15962_gb300 import workloads
+    out = {}
+    for L in sorted(set(Ls)):
+        r = pkg.labs_walks(L, [99], 2048, workloads.paper_walk_len(L), budget)
+        out[L] = int(r["best_E"][0])
+    return out
+
+
+def measure_serving(args, warmup):
     """Poisson request stream (mean args.rate/s for args.serve_seconds s) of odd L
-    uniform in [121, 301], 2048 walks, walk length 8*D, budget 1e10, stop at
-    the budget or at a per-L target energy; continuous batching with memory
-    admission.  Targets: for each L, the best energy the plain path reaches
-    with a calibration budget (args.target_budget) and seed 99."""
+    uniform in [121, 301], 2048 walks, walk length 8*D, budget args.serve_budget,
+    stop at the budget or at a per-L target energy (serving_targets); continuous
+    batching with memory admission.  Beside it, the plain path on the first
+    requests, one labs_walks per request, one at a time.  Returns a dict."""
     import numpy as np
-    import torch
     import paper_2210_15962_gb300 as pkg
     from paper_2210_15962_gb300 import workloads
-    torch.cuda.set_device(local)
-    pkg.load()
     wl = workloads.serving_stream(duration_s=args.serve_seconds, rate_per_s=args.rate, budget=args.serve_budget)
     reqs = wl.problems
-    # per-L targets from the plain path
-    targets = {}
-    for L in sorted({p.L for p in reqs}):
-        wlen = workloads.paper_walk_len(L)
-        r = pkg.labs_walks(L, [99], 2048, wlen, args.target_budget)
-        targets[L] = int(r["best_E"][0])
-    sampler = ClockSampler(local)
+    targets = serving_targets(pkg, [p.L for p in reqs], args.target_budget)
     sv = pkg.Server(max_L=301, max_walks=2048, max_active=args.max_active, mem_bytes=args.mem_gib << 30,
                     rounds_per_launch=args.rounds_per_launch)
-    # warm-up: a few requests end to end
-    for i in range(args.warmup):
+    for i in range(warmup):  # a few requests end to end
         p = reqs[i % len(reqs)]
         sv.wait(sv.submit(p.L, p.walks, p.walk_len, 10 ** 6 + i, p.walk_len * p.walks))
-    sampler.start()
+    st0 = sv.stats()
     tickets = []
     t0 = time.perf_counter()
     for p in reqs:
@@ -353,13 +412,13 @@ def run_serving(args, world, rank, local):
         tickets.append(sv.submit(p.L, p.walks, p.walk_len, p.seed, p.step_budget, targets[p.L]))
     results = [sv.wait(t, timeout_s=3600) for t in tickets]
     t1 = time.perf_counter()
-    clocks = sampler.stop()
     st = sv.stats()
     sv.close()
     lat = np.array([r["latency_s"] for r in results])
     qwait = np.array([(r["t_admit_ns"] - r["t_submit_ns"]) / 1e9 for r in results])
     evals = sum(r["evals"] for r in results)
-    reached = sum(r["reached_target"] for r in results)
+    busy_s = (st["busy_ms"] - st0["busy_ms"]) / 1e3
+    needed = sum(popc_needed(p.L, r["evals"], r["plane_steps"]) for p, r in zip(reqs, results))
     # the plain path on the first requests, one labs_walks per request
     tp0 = time.perf_counter()
     plain_ev = 0
@@ -367,13 +426,11 @@ def run_serving(args, world, rank, local):
     for p, r in list(zip(reqs, results))[:args.plain_requests]:
         g = pkg.labs_walks(p.L, [p.seed], p.walks, p.walk_len, p.step_budget, target_E=targets[p.L])
         plain_ev += int(g["evals"][0])
-        same = same and int(g["best_E"][0]) == r["best_E"] and int(g["evals"][0]) == r["evals"]
+        same = same and int(g["best_E"][0]) == r["best_E"] and int(g["evals"][0]) == r["evals"] \
+            and bool((g["best_seq"][0] == r["best_seq"]).all())
     tp1 = time.perf_counter()
-    line = {
-        "metric": "neighbour_evals_per_s", "value": evals / (t1 - t0), "unit": "neighbour_evals/s",
-        "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": (t1 - t0) * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic request stream (SplitMix64 seed %d)" % workloads.MANIFEST_SEED,
+    return {
+        "value": evals / (t1 - t0), "unit": "neighbour_evals/s", "seconds": t1 - t0, "evals": evals,
         "config": {"workload": wl.name, "requests": len(reqs), "duration_s": args.serve_seconds,
                    "rate_per_s": args.rate, "walks": 2048, "walk_len": "8*D", "budget": args.serve_budget,
                    "targets": "per L: plain-path best with budget %g, seed 99" % args.target_budget,
@@ -382,17 +439,44 @@ def run_serving(args, world, rank, local):
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean()), "max": float(lat.max())},
         "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
-        "completed": len(results), "reached_target": int(reached),
+        "completed": len(results), "reached_target": int(sum(r["reached_target"] for r in results)),
         # Eq. 7 of the predictive model for each request's evaluations
         "p_optimal": {"p50": float(np.percentile([r["p_optimal"] for r in results], 50)),
                       "min": float(min(r["p_optimal"] for r in results))},
-        "device_busy_frac": st["busy_ms"] / 1e3 / (t1 - t0),
-        "evals_run": st["evals_run"], "useful_frac": st["evals"] / max(1, st["evals_run"]),
+        "device_busy_frac": busy_s / (t1 - t0),
+        "evals_run": st["evals_run"] - st0["evals_run"],
+        "useful_frac": (st["evals"] - st0["evals"]) / max(1, st["evals_run"] - st0["evals_run"]),
+        "mem_peak_bytes": st["mem_peak"],
+        "roofline": popc_roofline(needed, busy_s, kernel="batch_kernel<W> (all classes, two launches in flight)",
+                                  popc_per_eval=needed / max(1, evals),
+                                  note="useful evaluations only (rounds past a request's stop not counted), "
+                                       "over the device's busy time"),
         "plain": {"value": plain_ev / (tp1 - tp0), "unit": "neighbour_evals/s",
                   "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
                   "same_results": bool(same)},
-        "gpu_launches": st["launches"], "clocks": clocks,
+        "gpu_launches": st["launches"] - st0["launches"],
     }
+
+
+def run_serving(args, world, rank, local):
+    """The serving workload on its own (see measure_serving)."""
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    from paper_2210_15962_gb300 import workloads
+    torch.cuda.set_device(local)
+    pkg.load()
+    sampler = ClockSampler(local)
+    sampler.start()
+    m = measure_serving(args, args.warmup)
+    clocks = sampler.stop()
+    line = {
+        "metric": "neighbour_evals_per_s", "value": m["value"], "unit": "neighbour_evals/s",
+        "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": m["seconds"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic request stream (SplitMix64 seed %d)" % workloads.MANIFEST_SEED,
+        "clocks": clocks,
+    }
+    line.update({k: v for k, v in m.items() if k not in ("value", "unit", "seconds", "evals")})
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -594,6 +678,47 @@ def run_walklen(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_variants(args, world, rank, local):
+    """One lane per walk against one warp per walk (labs_opts.kernel 1 and 3)
+    and the library's timed choice (kernel 0): one round of --walk-len-variants
+    steps at each L of --variants-L and each walk count of --variants-walks,
+    evaluations per second of each (CUDA events around the call's kernels)."""
+    import torch
+    import paper_2210_15962_gb300 as pkg
+    torch.cuda.set_device(local)
+    pkg.load()
+    stream = torch.cuda.Stream()
+    rows = []
+    sampler = ClockSampler(local)
+    sampler.start()
+    for L in [int(x) for x in args.variants_L.split(",")]:
+        D = (L + 1) // 2
+        wl = args.walk_len_variants
+        for walks in [int(x) for x in args.variants_walks.split(",")]:
+            row = {"L": L, "walks": walks, "walk_len": wl}
+            ref = None
+            for name, k in (("lane_per_walk", 1), ("warp_per_walk", 3), ("library_choice", 0)):
+                pkg.labs_walks(L, [7], walks, min(wl, 64), walks * min(wl, 64) * D, kernel=k, stream=stream)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = pkg.labs_walks(L, [7], walks, wl, walks * wl * D, kernel=k, stream=stream)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                row[name] = {"evals_per_s": int(r["evals"][0]) / (r["stats"]["walk_kernel_ms"] / 1e3),
+                             "wall_s": dt}
+                got = (int(r["best_E"][0]), r["best_seq"][0].tobytes(), int(r["evals"][0]))
+                ref = ref or got
+                row["same_results"] = row.get("same_results", True) and got == ref
+            rows.append(row)
+    clocks = sampler.stop()
+    line = {"metric": "neighbour_evals_per_s", "value": None, "unit": "neighbour_evals/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox starts, seed 7)",
+            "config": {"workload": "variants"}, "rows": rows, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -607,8 +732,13 @@ def main():
     ap.add_argument("--ref-walks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--device-only", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--plain-only", action="store_true",
+                    help="the plain workload alone, without the batched and serving sub-measurements")
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "batched", "serving", "large", "table1", "walklen"])
+                    choices=["plain", "batched", "serving", "large", "table1", "walklen", "variants"])
+    ap.add_argument("--variants-L", default="121,301,449,511")
+    ap.add_argument("--variants-walks", default="1024,8192,65536")
+    ap.add_argument("--walk-len-variants", type=int, default=2048)
     ap.add_argument("--walklen-cal-budget", type=int, default=10 ** 12)
     ap.add_argument("--walklen-seeds", type=int, default=4)
     ap.add_argument("--walklen-seconds", type=float, default=20.0)
@@ -622,7 +752,7 @@ def main():
     ap.add_argument("--large-rounds", type=int, default=3)
     ap.add_argument("--walks-large", type=int, default=65536)
     ap.add_argument("--walk-len-large", type=int, default=16384)
-    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--serve-budget", type=int, default=10 ** 10)
     ap.add_argument("--target-budget", type=int, default=2 * 10 ** 9)
@@ -649,6 +779,9 @@ def main():
         return
     if args.workload == "walklen" and args.impl != "reference":
         run_walklen(args, world, rank, local)
+        return
+    if args.workload == "variants" and args.impl != "reference":
+        run_variants(args, world, rank, local)
         return
 
     if args.impl == "reference":
@@ -743,6 +876,23 @@ def main():
         ops_per_eval = core_alu_ops_per_eval(L, avg_planes, full)
         achieved = evals_per_launch * ops_per_eval / (per_launch_ms / 1e3) / 1e12
         peak = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+        traffic = (TRAFFIC["bytes_per_launch"] if (walk_sources_hash() == TRAFFIC["sources_sha256_prefix"]
+                                                  and (L, walks, wl, full) == (DEFAULT_L, WALKS, WALK_LEN, False))
+                   else None)
+        kernel_name = ("full_walk_kernel<W=%d,K=4>" % ((L - 1 + 31) // 32) if full
+                       else "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32))
+        alu = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
+               "frac": achieved / peak, "ops_per_eval": ops_per_eval,
+               "basis": "4 LOP3 per 32 lags and digit plane; 152 SMs x 64 lanes/clk x 2070 MHz"}
+        if full:
+            # the full space's formulation has its own popcount count; its roofline stays in ALU lane-ops
+            roofline = dict(alu, traffic=traffic, kernel=kernel_name, kernel_ms_per_launch=per_launch_ms,
+                            avg_digit_planes=avg_planes)
+        else:
+            needed = popc_needed(L, evals_per_launch, planes / max(walk_launches, 1))
+            roofline = popc_roofline(needed, per_launch_ms / 1e3, traffic=traffic, kernel=kernel_name,
+                                     kernel_ms_per_launch=per_launch_ms, popc_per_eval=needed / evals_per_launch,
+                                     avg_digit_planes=avg_planes, alu_lane_ops=alu)
         line = {
             "metric": "neighbour_evals_per_s", "value": value, "unit": "neighbour_evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_s * 1e3 / args.steps,
@@ -758,21 +908,21 @@ def main():
                                                                      (walks * wl * flips))),
                        "parallelism": "independent problem per GPU" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: %.1f GiB of visited tables per round" % (ws_bytes / 2 ** 30)},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (int32 ALU-pipe lane-ops)",
-                         "frac": achieved / peak,
-                         "traffic": (TRAFFIC["bytes_per_launch"]
-                                     if (walk_sources_hash() == TRAFFIC["sources_sha256_prefix"]
-                                         and (L, walks, wl, full) == (DEFAULT_L, WALKS, WALK_LEN, False)) else None),
-                         "kernel": ("full_walk_kernel<W=%d,K=4>" % ((L - 1 + 31) // 32) if full
-                                    else "walk_kernel<W=%d,K=4>" % (((L - 1) // 2 + 31) // 32)),
-                         "kernel_ms_per_launch": per_launch_ms,
-                         "ops_per_eval": ops_per_eval, "avg_digit_planes": avg_planes,
-                         "peak_basis": "152 SMs x 64 lanes/clk (measured LOP3 rate) x 2070 MHz max clock"},
+            "roofline": roofline,
             "e2e": ({"value": tot_e2e / e2e_s, "unit": "neighbour_evals/s", "h2d_bytes_per_step": h2d,
                      "d2h_bytes_per_step": d2h} if e2e_s > 0 else None),
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        if world == 1 and not args.plain_only and not full:
+            # the batched and serving paths of the same library, each against
+            # the plain path on the same problems
+            sampler = ClockSampler(local)
+            sampler.start()
+            line["batched"] = measure_batched(args, rank, max(2, min(args.steps, 5)), 1)
+            line["serving"] = measure_serving(args, 2)
+            line["batched_serving_clocks"] = sampler.stop()
+            line["gpu_launches_batched_serving"] = line["batched"]["launches"] + line["serving"]["gpu_launches"]
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(walk_len=wl, L=L, total_walks=walks, full=full, one_core=True)
         print(json.dumps(line), flush=True)

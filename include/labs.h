@@ -80,11 +80,15 @@ typedef struct labs_opts {
   int64_t target_E;       /* stop a problem after the first round whose best E <= target_E;
                              < 0 = no target.  Set to -1 by labs_opts_init. */
   int32_t max_rounds;     /* 0 = no limit; else stop every problem after this many rounds */
-  int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (the full
-                             scan, the faster of the two on GB300 at every L),
-                             1 = full scan (every neighbour from the correlations each step),
-                             2 = incremental (stored neighbour deltas updated after each move);
-                             all give the same results; other values: LABS_EINVAL */
+  int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (1 or 3,
+                             whichever ran a short sample round of the same launch size faster;
+                             timed once per process per lag-word class and launch size),
+                             1 = full scan, one lane per walk (every neighbour from the
+                                 correlations each step),
+                             2 = incremental (stored neighbour deltas updated after each move),
+                             3 = full scan, one warp per walk (the lanes split the D flips);
+                             all give the same results; other values: LABS_EINVAL (the full
+                             search space takes 0 and 1 only) */
   void *workspace;        /* optional device scratch of workspace_bytes bytes (e.g. from
                              PyTorch); NULL = the library allocates and frees it itself */
   size_t workspace_bytes;

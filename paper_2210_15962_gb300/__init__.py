@@ -30,6 +30,7 @@ LABS_L_MAX = 511
 KERNEL_AUTO = 0
 KERNEL_FULL_SCAN = 1
 KERNEL_INCREMENTAL = 2
+KERNEL_WARP = 3
 
 
 class LabsError(RuntimeError):

@@ -5,7 +5,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/labs.h"
@@ -141,14 +144,33 @@ struct RunConfig {
   int32_t space;  // kSpaceSkew or kSpaceFull
 };
 
-// The library's choice of neighbourhood evaluation for labs_opts.kernel == 0.
-// The library's choice: the full scan, measured faster than the incremental
-// variant at every lag-word class (the incremental pass pays a fixed per-flip
-// cost at small W and is occupancy-limited by its shared-memory state at large W).
+// The neighbourhood evaluation of labs_opts.kernel (0 is resolved by
+// Run::pick_variant before any round runs; the full scan stands in for it).
 int32_t resolve_variant(int32_t kernel) {
-  if (kernel == kVariantFullScan || kernel == kVariantIncremental) return kernel;
+  if (kernel == kVariantFullScan || kernel == kVariantIncremental || kernel == kVariantWarp) return kernel;
   return kVariantFullScan;
 }
+
+// The library's choice for labs_opts.kernel == 0 (skew space): one lane per
+// walk or one warp per walk, whichever ran a sample round of the same launch
+// size faster, timed once per process for each lag-word class and launch size
+// (log2 of the walks in one launch).  The incremental variant is never chosen:
+// it measured slower than the full scan at every class (it pays a fixed
+// per-flip cost at small W and its shared-memory state caps occupancy at
+// large W).  Every variant gives the same results.
+std::mutex g_variant_mu;
+std::map<std::pair<int, int>, int32_t> g_variant;
+
+int ilog2(uint64_t x) {
+  int r = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+constexpr int32_t kSampleSteps = 64;  // steps per walk of a variant-choice sample round
 
 }  // namespace
 }  // namespace psaw
@@ -370,6 +392,60 @@ struct Run {
     return p;
   }
 
+  // Resolve labs_opts.kernel == 0 (see g_variant).  Runs before the problems'
+  // state is initialised: the sample rounds write only per-walk outputs, the
+  // tables and accumulators that the real rounds reset.
+  labs_status pick_variant() {
+    if (cfg.kernel != 0) return LABS_OK;
+    if (cfg.space != kSpaceSkew) {
+      cfg.kernel = kVariantFullScan;
+      return LABS_OK;
+    }
+    const std::pair<int, int> key{W, ilog2(g_chunk)};
+    {
+      std::lock_guard<std::mutex> lock(g_variant_mu);
+      auto it = g_variant.find(key);
+      if (it != g_variant.end()) {
+        cfg.kernel = it->second;
+        return LABS_OK;
+      }
+    }
+    const int32_t cand[2] = {kVariantFullScan, kVariantWarp};
+    float best_ms = 1e30f;
+    int32_t best = kVariantFullScan;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LABS_ECUDA;
+    labs_status st = LABS_OK;
+    for (int32_t v : cand) {
+      WalkParams p = params(0xFFFFF000u, 0, (uint32_t)g_chunk);
+      p.variant = v;
+      p.walk_len = std::min(cfg.walk_len, kSampleSteps);
+      p.cap = visited_table_cap(p.walk_len);
+      p.done = nullptr;
+      p.recheck_every = 0;
+      p.plane_steps = nullptr;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == LABS_OK; ++rep) {  // the first launch warms up
+        if (cudaEventRecord(e0, s) != cudaSuccess || launch_walk_round(W, p, s) != cudaSuccess ||
+            cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          st = LABS_ECUDA;
+      }
+      if (st != LABS_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LABS_OK) return st;
+    cfg.kernel = best;
+    std::lock_guard<std::mutex> lock(g_variant_mu);
+    g_variant[key] = best;
+    return LABS_OK;
+  }
+
   cudaError_t launch_round(uint32_t round, int32_t *trace, uint32_t trace_begin, uint32_t trace_count) {
     for (size_t g0 = 0; g0 < n_walks; g0 += g_chunk) {
       WalkParams p = params(round, (uint32_t)g0, (uint32_t)std::min(g_chunk, n_walks - g0));
@@ -450,7 +526,7 @@ static labs_status walks_impl(int32_t space, int32_t L, const uint64_t *seeds, i
   if (opts_in) opts = *opts_in;
   else labs_opts_init(&opts);
   // the full search space has the full-scan kernel only
-  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantIncremental;
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantWarp;
   if (!valid_space_L(space, L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 ||
       walk_len < 1 || walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0 ||
       opts.kernel < 0 || opts.kernel > max_kernel)
@@ -472,6 +548,7 @@ static labs_status walks_impl(int32_t space, int32_t L, const uint64_t *seeds, i
 
   st = run.setup(opts.workspace, opts.workspace_bytes);
   if (st != LABS_OK) return st;
+  if ((st = run.pick_variant()) != LABS_OK) return st;
   LABS_CU(run.init_problems(seeds, in_kind));
   t0 = run.timer.rec(run.s);
   for (;;) {
@@ -545,7 +622,7 @@ static labs_status saw_round_impl(int32_t space, int32_t L, uint64_t seed, uint3
                                   int32_t *walk_best_step, int32_t *trace_flips, int32_t trace_begin,
                                   int32_t trace_count, int32_t visited_walk, uint64_t *visited_keys,
                                   int32_t visited_cap, int32_t *visited_count, int32_t kernel) {
-  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantIncremental;
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantWarp;
   if (!valid_space_L(space, L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 ||
       kernel < 0 || kernel > max_kernel)
     return LABS_EINVAL;
@@ -565,6 +642,7 @@ static labs_status saw_round_impl(int32_t space, int32_t L, uint64_t seed, uint3
   st = run.setup(nullptr, 0);
   if (st != LABS_OK) return st;
   if (run.g_chunk < (size_t)n_walks) return LABS_ENOMEM;  // the tables of the round must stay resident
+  if ((st = run.pick_variant()) != LABS_OK) return st;
   LABS_CU(run.init_problems(&seed, cudaMemcpyHostToDevice));
   if (trace_n) {
     LABS_CU(cudaMalloc(&d_trace, trace_n * sizeof(int32_t)));

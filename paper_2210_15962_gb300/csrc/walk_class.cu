@@ -4,6 +4,7 @@
 // compiled once per class with -DPSAW_W=W (1..8), so that the classes' large,
 // pattern-specialised kernels build in parallel.
 #include "walk_device.cuh"
+#include "walk_warp.cuh"
 
 #ifndef PSAW_W
 #error "walk_class.cu is compiled once per lag-word class with -DPSAW_W=1..8"
@@ -140,6 +141,59 @@ static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One warp = one walk (walk_warp.cuh): same contract as walk_kernel; the
+// block's warps run walks lid = 4 * block + warp, each lane a share of its
+// walk's flips.
+template <int W, int T, int K, int MINB>
+__global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_warp(const WalkParams p) {
+  constexpr int NS = W + 1;
+  constexpr int kWarps = kWalkBlock / 32;
+  constexpr int kSm = WarpWalkSmem<W>::kWords;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lid = blockIdx.x * kWarps + warp;
+  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
+  const uint32_t gw = p.g_begin + lid;
+  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
+  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
+  const bool live = lid < p.g_count && !(p.done && p.done[prob]);  // the same on the whole warp
+  uint64_t *table = p.tables + (size_t)lid * table_words;
+  const Geometry g = make_geometry(p.L, T);
+  __shared__ __align__(16) uint32_t mask_rows[MaskTable<W>::kWords];
+  __shared__ uint32_t warp_sm[kWarps * kSm];
+  fill_mask_rows<W>(g, mask_rows, threadIdx.x, blockDim.x);
+  __syncthreads();
+  if (!live) return;
+  // the walk's table, zeroed by the warp with 16-byte stores (table_words is even)
+  uint4 *t4 = reinterpret_cast<uint4 *>(table);
+  for (size_t i = (size_t)lane; i < table_words / 2; i += 32) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  int32_t *trace = nullptr;
+  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
+    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
+  WalkOut<NS> o;
+  run_walk_warp<W, T, K>(g, mu, mask_rows, warp_sm + warp * kSm, p.seeds[prob], walk, p.round, p.walk_len, table,
+                         p.cap, p.kw64, p.recheck_every, trace, p.err, o);
+  if (lane != 0) return;
+  p.w_bestE[gw] = o.bestE;
+  p.w_moves[gw] = o.moves;
+  p.w_stuck[gw] = o.stuck;
+  p.w_best_step[gw] = o.best_step;
+#pragma unroll
+  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
+  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
+  if (p.plane_steps) atomicAdd(p.plane_steps, (unsigned long long)o.planes);
+  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
+}
+
+template <int W>
+static cudaError_t launch_w_warp(const WalkParams &p, cudaStream_t s) {
+  constexpr int T = PlanesFor<W>::value;
+  const unsigned blocks = (p.g_count + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
+  walk_kernel_warp<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 // The full search space (full_core.cuh): same contract as walk_kernel with L
 // flips per step and the whole sequence as key (kKeyWords >= W + 1 words).
 template <int W, int T, int K, int MINB>
@@ -187,7 +241,9 @@ static cudaError_t launch_full(const WalkParams &p, cudaStream_t s) {
 template <int W>
 cudaError_t launch_walk_class(const WalkParams &p, cudaStream_t s) {
   if (p.space == kSpaceFull) return launch_full<W>(p, s);
-  return p.variant == kVariantIncremental ? launch_w_incr<W>(p, s) : launch_w<W>(p, s);
+  if (p.variant == kVariantIncremental) return launch_w_incr<W>(p, s);
+  if (p.variant == kVariantWarp) return launch_w_warp<W>(p, s);
+  return launch_w<W>(p, s);
 }
 
 template cudaError_t launch_walk_class<PSAW_W>(const WalkParams &p, cudaStream_t s);

@@ -501,8 +501,11 @@ struct SteppedKey {
 
 // NX, NY >= 0 fix at compile time how many leading words have valid x / y
 // lags (the caller guarantees NX = ceil(t/32), NY = ceil((Nq-1-t)/32));
-// -1 decides per flip.  kbase, kdiff: the flip's key_base / key_diff.
-template <int W, int T, int TP, bool CENTRE, int NX = -1, int NY = -1>
+// -1 decides per flip.  ALL_WORDS evaluates every word that can hold lags
+// on the two-sided path without testing which sides are empty (an empty
+// side's zero mask makes its terms vanish), for callers whose lanes hold
+// different flips.  kbase, kdiff: the flip's key_base / key_diff.
+template <int W, int T, int TP, bool CENTRE, int NX = -1, int NY = -1, bool ALL_WORDS = false>
 LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint32_t (&B)[W], const uint32_t (&F)[W],
                           const uint32_t (&Vx)[W], const uint32_t (&Vye)[W], uint32_t ba, uint32_t kbase,
                           uint32_t kdiff, int t, int Nq) {
@@ -515,7 +518,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
     // x lags i <= t, y lags i <= Nq-1-t.  Wide classes keep every word on the
     // two-sided path: with few resident warps they rely on the compiler
     // interleaving the words' independent chains.
-    constexpr bool kSkip = W <= kSkipMaxWords;
+    constexpr bool kSkip = W <= kSkipMaxWords && !ALL_WORDS;
     const bool xa = w < x_words<W>() && (NX >= 0 ? (w < NX) : (kSkip ? (t > 32 * w) : true));
     const bool ya = CENTRE ? false : (NY >= 0 ? (w < NY) : (kSkip ? (Nq - 1 - t > 32 * w) : true));
     const uint32_t vx = Vx[w];

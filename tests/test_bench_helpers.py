@@ -40,6 +40,21 @@ def test_roofline_unit_counts_the_lags_of_each_space():
     assert bench.core_alu_ops_per_eval(121, 5.0, full=True) == 4.0 * 5.0 * 120 / 32
 
 
+def test_popcount_count_of_the_skew_scan():
+    # counted by hand: L=5 (D=3) has one one-sided word at flips 0 and 2 and
+    # none at flip 1 (its only y lag is its own mirror pair); at L=27 (one
+    # word) every flip has a valid lag and flips 2..12 have both sides
+    assert bench.popc_words_per_step(5) == (2, 0)
+    assert bench.popc_words_per_step(27) == (14, 11)
+    # per evaluation: TP counts per word with lags + 2 per two-sided word
+    assert bench.popc_needed(27, 14, 5) == 5 * 14 + 2 * 11
+    # the walk kernel's ncu profile at L=121 (5.0 digit planes) counted 11.5
+    # POPC per warp-flip; the formulation's count is within 1% of it
+    per_eval = bench.popc_needed(121, 61 * 1000, 5 * 1000) / (61 * 1000)
+    assert abs(per_eval - 11.5) / 11.5 < 0.01
+    assert abs(bench.popc_peak_tops() - 152 * 16 * 2.07e9 / 1e12) < 1e-9
+
+
 def test_cpu_sample_is_bounded_and_whole_per_core():
     def work(n, L, wl, full=False):
         flips = L if full else (L + 1) // 2
