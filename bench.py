@@ -398,7 +398,7 @@ def measure_serving(args, warmup):
     reqs = wl.problems
     targets = serving_targets(pkg, [p.L for p in reqs], args.target_budget)
     sv = pkg.Server(max_L=301, max_walks=2048, max_active=args.max_active, mem_bytes=args.mem_gib << 30,
-                    rounds_per_launch=args.rounds_per_launch)
+                    rounds_per_launch=args.rounds_per_launch, walk_mode=args.serve_walk_mode)
     for i in range(warmup):  # a few requests end to end
         p = reqs[i % len(reqs)]
         sv.wait(sv.submit(p.L, p.walks, p.walk_len, 10 ** 6 + i, p.walk_len * p.walks))
@@ -435,7 +435,8 @@ def measure_serving(args, warmup):
                    "rate_per_s": args.rate, "walks": 2048, "walk_len": "8*D", "budget": args.serve_budget,
                    "targets": "per L: plain-path best with budget %g, seed 99" % args.target_budget,
                    "max_active": args.max_active, "mem_gib": args.mem_gib,
-                   "rounds_per_launch": args.rounds_per_launch},
+                   "rounds_per_launch": args.rounds_per_launch,
+                   "walk_mode": ["chosen per launch", "lane per walk", "warp per walk"][args.serve_walk_mode]},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean()), "max": float(lat.max())},
         "queue_wait_s": {"p50": float(np.percentile(qwait, 50)), "p99": float(np.percentile(qwait, 99))},
@@ -482,19 +483,23 @@ def run_serving(args, world, rank, local):
 
 
 def run_large(args, world, rank, local):
-    """L=449 (D=225), 65536 walks x 16384 steps per round, seed 1+rank.  The plain
-    path (labs_walks: one walk-kernel launch per round) runs R rounds; its best
-    energy is the target.  Time-to-target of the plain path and of the
-    persistent batch path (one round per launch, no wave quantisation) for that
-    target; both reach it in the same round, so the difference is speed only."""
+    """Time to a target energy at L=449 (D=225), 65536 walks x 16384 steps per
+    round, plain path against batched path.  The target is fixed independently
+    of both arms: the best energy of a calibration solve with its own seed (99)
+    and --large-cal-rounds rounds.  Each arm then solves --large-seeds seeds
+    (1..) to that target, each capped at --large-cap-s seconds of rounds, and
+    the median and spread of the times are reported.  Plain: labs_walks (one
+    walk-kernel launch per round).  Batched: the persistent batch path with the
+    instance alone (--large-rpl rounds per launch, the later ones skipped on
+    the device once a round reaches the target)."""
+    import numpy as np
     import torch
     import paper_2210_15962_gb300 as pkg
     torch.cuda.set_device(local)
     pkg.load()
-    L, walks, wl, seed = 449, args.walks_large, args.walk_len_large, rank_seed(rank)
+    L, walks, wl = 449, args.walks_large, args.walk_len_large
     D = (L + 1) // 2
     per_round = walks * wl * D
-    budget = args.large_rounds * per_round
     stream = torch.cuda.Stream()
 
     def timed(fn):
@@ -506,31 +511,46 @@ def run_large(args, world, rank, local):
 
     sampler = ClockSampler(local)
     sampler.start()
-    ref, t_ref = timed(lambda: pkg.labs_walks(L, [seed], walks, wl, budget, stream=stream))
-    target = int(ref["best_E"][0])
-    plain, t_plain = timed(lambda: pkg.labs_walks(L, [seed], walks, wl, budget, target_E=target, stream=stream))
-    b = pkg.Batch([(L, walks, wl, seed, budget, target)], rounds_per_launch=1, stream=stream)
-    bst, t_batch = timed(b.run)
-    bres = b.result(0)
-    b.close()
-    b2 = pkg.Batch([(L, walks, wl, seed, budget)], stream=stream)
-    b2st, t_batch_full = timed(b2.run)
-    b2res = b2.result(0)
-    b2.close()
+    cal, t_cal = timed(lambda: pkg.labs_walks(L, [99], walks, wl, args.large_cal_rounds * per_round, stream=stream))
+    target = int(cal["best_E"][0])
+    round_s = t_cal / args.large_cal_rounds
+    max_rounds = max(1, int(args.large_cap_s / round_s))
+    budget = max_rounds * per_round
+    arms = {"plain": [], "batched": []}
+    for sd in range(1, args.large_seeds + 1):
+        seed = sd + 1000 * rank
+        r, t = timed(lambda: pkg.labs_walks(L, [seed], walks, wl, budget, target_E=target, stream=stream))
+        arms["plain"].append({"seed": seed, "seconds": t, "reached": int(r["best_E"][0]) <= target,
+                              "rounds": int(r["rounds"][0]), "evals": int(r["evals"][0]), "best_E": int(r["best_E"][0])})
+        b = pkg.Batch([(L, walks, wl, seed, budget, target)], rounds_per_launch=args.large_rpl, stream=stream)
+        st, t = timed(b.run)
+        res = b.result(0)
+        b.close()
+        arms["batched"].append({"seed": seed, "seconds": t, "reached": res["best_E"] <= target, "rounds": res["rounds"],
+                                "evals": res["evals"], "best_E": res["best_E"],
+                                "same_as_plain": res["best_E"] == arms["plain"][-1]["best_E"]
+                                and res["rounds"] == arms["plain"][-1]["rounds"]})
     clocks = sampler.stop()
+
+    def summary(rows):
+        ts = [x["seconds"] if x["reached"] else float("inf") for x in rows]
+        ok = [x for x in ts if x != float("inf")]
+        return {"median_s": float(np.median(ts)), "min_s": min(ts), "max_s": max(ts),
+                "quartiles_s": [float(np.percentile(ts, 25)), float(np.percentile(ts, 75))],
+                "reached": len(ok), "runs": len(rows),
+                "evals_per_s": sum(x["evals"] for x in rows) / sum(x["seconds"] for x in rows),
+                "runs_detail": rows}
+
     line = {
-        "metric": "neighbour_evals_per_s", "value": b2st["evals"] / t_batch_full, "unit": "neighbour_evals/s",
-        "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": t_batch_full * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox starts, seed %d)" % seed,
-        "config": {"workload": "plain_vs_batched_L449_%dx%d_%drounds" % (walks, wl, args.large_rounds), "L": L,
-                   "walks": walks, "walk_len": wl, "rounds": args.large_rounds},
-        "plain": {"value": int(ref["evals"][0]) / t_ref, "seconds": t_ref, "best_E": target,
-                  "F": L * L / (2.0 * target)},
-        "batched": {"value": b2st["evals"] / t_batch_full, "seconds": t_batch_full, "best_E": b2res["best_E"],
-                    "same_result": b2res["best_E"] == target and b2res["evals"] == int(ref["evals"][0])},
-        "time_to_target_s": {"target_E": target, "plain": t_plain, "batched": t_batch,
-                             "round_reached": int(plain["rounds"][0]),
-                             "same_round": int(plain["rounds"][0]) == bres["rounds"]},
+        "metric": "time_to_target_s", "value": summary(arms["batched"])["median_s"], "unit": "s", "n_gpus": world,
+        "steps": args.large_seeds, "warmup": 1, "ms_per_step": None, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (Philox starts, seeds 1..%d)" % args.large_seeds,
+        "config": {"workload": "time_to_target_L449_%dx%d" % (walks, wl), "L": L, "walks": walks, "walk_len": wl,
+                   "target_E": target, "target_F": L * L / (2.0 * target),
+                   "target_from": "best of a %d-round calibration solve, seed 99 (%.1f s)" % (args.large_cal_rounds,
+                                                                                            t_cal),
+                   "cap_rounds": max_rounds, "cap_s": args.large_cap_s, "batched_rounds_per_launch": args.large_rpl},
+        "plain": summary(arms["plain"]), "batched": summary(arms["batched"]),
         "clocks": clocks,
     }
     if rank == 0:
@@ -749,7 +769,10 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="0 library choice, 1 full scan, 2 incremental")
     ap.add_argument("--space", default="skew", choices=["skew", "full"],
                     help="plain workload over the skew-symmetric sequences or all length-L sequences")
-    ap.add_argument("--large-rounds", type=int, default=3)
+    ap.add_argument("--large-cal-rounds", type=int, default=2)
+    ap.add_argument("--large-seeds", type=int, default=8)
+    ap.add_argument("--large-cap-s", type=float, default=45.0)
+    ap.add_argument("--large-rpl", type=int, default=2)
     ap.add_argument("--walks-large", type=int, default=65536)
     ap.add_argument("--walk-len-large", type=int, default=16384)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -759,6 +782,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--mem-gib", type=int, default=16)
     ap.add_argument("--rounds-per-launch", type=int, default=4)
+    ap.add_argument("--serve-walk-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="0: lane or warp per walk chosen per launch, 1: lane per walk, 2: warp per walk")
     ap.add_argument("--plain-requests", type=int, default=10)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)

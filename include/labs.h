@@ -203,12 +203,16 @@ typedef struct labs_batch_opts {
   void *stream;              /* cudaStream_t; NULL = the batch creates its own stream */
   int32_t use_graph;         /* 1: when no problem has a target, the first launch sequence is
                                 captured as a CUDA graph on the first run and replayed after */
-  int32_t autotune;          /* 1: pick walks per CTA and table capacity per class by timing
-                                candidates on a sample (cached per process) */
+  int32_t autotune;          /* 1: pick per class, by timing candidates on a sample of its first
+                                launch (cached per process): one walk per lane with 64, 128 or
+                                256 walks per CTA and 1.5 or 3 table slots per pivot, or one
+                                walk per warp (offered while every problem has <= 4096 walks) */
   int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
   int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 15 or autotuned */
   int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
-  int32_t reserved;
+  int32_t walk_mode;         /* 0: one walk per lane, or what autotune picks; 1: one walk per lane;
+                                2: one walk per warp in every class (every problem <= 4096 walks,
+                                else LABS_EINVAL); all give the same results */
 } labs_batch_opts;
 
 typedef struct labs_batch labs_batch; /* opaque, owns its device memory */
@@ -228,9 +232,11 @@ labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t *best_seq, 
 /* Work accounting of problem i of the last run: the digit planes its
  * neighbourhood scans used, summed over the walk steps of its rounds. */
 labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, uint64_t *plane_steps);
-/* Launch shape chosen for class W: walks per CTA, table factor x 10, walks resident at once. */
+/* Launch shape chosen for class W (any output may be NULL): threads per CTA,
+ * table factor x 10, walks resident at once, and 1 if the class runs one walk
+ * per warp (the lanes split each walk's flips) or 0 for one walk per lane. */
 labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads, int32_t *table_factor_x10,
-                             int32_t *resident_walks);
+                             int32_t *resident_walks, int32_t *warp_per_walk);
 labs_status labs_batch_destroy(labs_batch *b);
 
 /* ---------------------------------------------------------------- serving
@@ -259,7 +265,11 @@ typedef struct labs_serve_cfg {
   int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
   int32_t rounds_per_launch; /* rounds each admitted request gets per launch at most, default 4
                                 (two launches are in flight: the next is queued while one runs) */
-  int32_t block_threads;     /* walks per CTA of the batch kernels, default 128 */
+  int32_t block_threads;     /* threads per CTA of the batch kernels, default 128 */
+  int32_t walk_mode;         /* 0: per launch and class, one walk per lane or per warp, whichever
+                                keeps the GPU faster busy with the launch's tasks (rates measured
+                                at create); 1: always one walk per lane; 2: always one walk per
+                                warp (max_walks <= 4096, else LABS_EINVAL); same results */
 } labs_serve_cfg;
 
 typedef struct labs_result {

@@ -25,6 +25,9 @@ LABS_EOVERFLOW = -5
 LABS_ENOTFOUND = -6
 LABS_ECHECK = -7
 LABS_ESHUTDOWN = -8
+WALK_MODE_AUTO = 0
+WALK_MODE_LANE = 1
+WALK_MODE_WARP = 2
 LABS_L_MIN = 5
 LABS_L_MAX = 511
 KERNEL_AUTO = 0
@@ -90,7 +93,7 @@ class labs_batch_opts(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("table_factor_x10", ctypes.c_int32),
         ("rounds_per_launch", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("walk_mode", ctypes.c_int32),
     ]
 
 
@@ -104,6 +107,7 @@ class labs_serve_cfg(ctypes.Structure):
         ("max_walk_len", ctypes.c_int32),
         ("rounds_per_launch", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
+        ("walk_mode", ctypes.c_int32),
     ]
 
 
@@ -171,7 +175,7 @@ _EXPORTS = {
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "labs_batch_plane_steps": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "labs_batch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_void_p]),
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "labs_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "labs_serve_cfg_init": (None, [ctypes.POINTER(labs_serve_cfg)]),
     "labs_serve_create": (ctypes.c_int32, [ctypes.POINTER(labs_serve_cfg), ctypes.POINTER(ctypes.c_void_p)]),
@@ -444,7 +448,7 @@ class Batch:
     """
 
     def __init__(self, problems, *, use_graph=False, autotune=False, block_threads=0, table_factor_x10=0,
-                 rounds_per_launch=0, stream=None):
+                 rounds_per_launch=0, walk_mode=0, stream=None):
         probs = [p if isinstance(p, labs_problem) else make_problem(*p) for p in problems]
         self.problems = probs
         arr = (labs_problem * len(probs))(*probs)
@@ -456,6 +460,7 @@ class Batch:
         o.block_threads = int(block_threads)
         o.table_factor_x10 = int(table_factor_x10)
         o.rounds_per_launch = int(rounds_per_launch)
+        o.walk_mode = int(walk_mode)
         h = ctypes.c_void_p()
         _check(load().labs_batch_create(arr, len(probs), ctypes.byref(o), ctypes.byref(h)), "labs_batch_create")
         self._h = h
@@ -481,9 +486,11 @@ class Batch:
         return [self.result(i) for i in range(len(self.problems))]
 
     def shape(self, W: int) -> dict:
-        v = np.zeros(3, dtype=np.int32)
-        _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3])), "labs_batch_shape")
-        return {"block_threads": int(v[0]), "table_factor_x10": int(v[1]), "resident_walks": int(v[2])}
+        v = np.zeros(4, dtype=np.int32)
+        _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3]), _ptr(v[3:4])),
+               "labs_batch_shape")
+        return {"block_threads": int(v[0]), "table_factor_x10": int(v[1]), "resident_walks": int(v[2]),
+                "warp_per_walk": bool(v[3])}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -507,12 +514,12 @@ class Server:
     """labs_serve_*: a continuous-batching solve server on the current device."""
 
     def __init__(self, *, mem_bytes=None, max_active=None, max_L=None, max_walks=None, max_walk_len=None,
-                 rounds_per_launch=None, block_threads=None, stream=None):
+                 rounds_per_launch=None, block_threads=None, walk_mode=None, stream=None):
         c = labs_serve_cfg()
         load().labs_serve_cfg_init(ctypes.byref(c))
         for k, v in dict(mem_bytes=mem_bytes, max_active=max_active, max_L=max_L, max_walks=max_walks,
                          max_walk_len=max_walk_len, rounds_per_launch=rounds_per_launch,
-                         block_threads=block_threads).items():
+                         block_threads=block_threads, walk_mode=walk_mode).items():
             if v is not None:
                 setattr(c, k, int(v))
         if stream is not None:

@@ -32,7 +32,8 @@ struct BatchProblem {
   uint64_t seed;
 };
 
-// one warp task: 32 walks (chunk) of one round of one problem, and the round's record
+// one warp task: 32 walks (chunk) of one round of one problem, or in warp
+// mode one walk (chunk = the walk's index), and the round's record
 struct BatchTask {
   uint32_t problem, round, chunk, rec;
 };
@@ -44,8 +45,9 @@ struct RoundRecords {
   unsigned long long *planes;  // digit planes summed over the round's walk steps
   uint32_t *left;              // chunks not finished yet
   uint32_t *round;             // the round the record holds (~0 = none)
-  uint32_t *keys;              // [record][max_chunks][kKeyWords]: best key of each chunk
-  uint32_t max_chunks;
+  uint32_t *shift;             // key slot of walk w = w >> shift: 5 (a slot per chunk) or 0 (per walk)
+  const unsigned long long *key_base;  // per record: its first key slot
+  uint32_t *keys;              // [slot][kKeyWords]: best key of each chunk or walk of each record
 };
 
 // Per-problem state of Algorithm 1, kept across the problem's launches.
@@ -75,9 +77,10 @@ struct BatchKernelParams {
   int32_t *err;
 };
 
-// A record about to hold `round` of a problem, whose tasks have `chunks` chunks.
+// A record about to hold `round` of a problem, which `chunks` tasks run
+// (chunks of 32 walks, key shift 5; or single walks in warp mode, shift 0).
 struct RecordInit {
-  uint32_t rec, round, chunks;
+  uint32_t rec, round, chunks, shift;
 };
 
 // A task with its place in a launch's order.  Problems with a target run the
@@ -114,6 +117,10 @@ cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStrea
                          int max_blocks = 0);
 // Lanes the persistent kernel of class W keeps resident with `block` threads per block.
 int batch_resident_lanes(int W, int block);
+// Warp mode (one walk per warp, tasks of one walk; the pool holds one table
+// per warp of the grid): the launch, and the warps it keeps resident.
+cudaError_t launch_batch_warp(int W, int block, const BatchKernelParams &p, cudaStream_t s, int max_blocks = 0);
+int batch_resident_warps(int W, int block);
 // Finalize, in round order, the complete rounds of the listed problems (those
 // the in-kernel finalization left, normally none).
 cudaError_t launch_batch_finalize(const int32_t *problems, int n, const RoundRecords &rec, const ProblemState &ps,

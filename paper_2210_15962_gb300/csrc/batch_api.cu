@@ -20,7 +20,13 @@
 namespace psaw {
 namespace {
 
-constexpr uint32_t kMaxRingRounds = 64;  // rounds of one problem issued in one launch at most
+constexpr uint32_t kMaxRingRounds = 1024;  // rounds of one problem issued in one launch at most
+// key slots of the autotuner's record: more than any one wave of tasks needs
+// (warps resident on a 152-SM device, 64 per SM)
+constexpr size_t kTuneKeySlots = 152 * 64;
+// Warp mode (one walk per warp) keeps a key slot per walk in every round
+// record, so it is offered only while every problem has at most this many walks.
+constexpr int kWarpModeMaxWalks = 4096;
 
 bool valid_problem(const labs_problem &p) {
   return p.L >= LABS_L_MIN && p.L <= LABS_L_MAX && (p.L & 1) && p.walks >= 1 && p.walks <= (1 << 24) &&
@@ -36,6 +42,7 @@ cudaError_t dalloc(T **p, size_t n) {
 
 struct ClassPlan {
   int W = 0;
+  bool warp = false;  // warp mode: one walk per warp, tasks of one walk
   int block = 128;
   int factor_x10 = kTableFactorX10;
   std::vector<int> probs;  // problem indices of this class
@@ -54,7 +61,11 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tuned;  // -> (block, factor_x10)
+struct Tuned {
+  int block, factor_x10;
+  bool warp;
+};
+std::map<TuneKey, Tuned> g_tuned;
 
 int ilog2(uint64_t x) {
   int r = 0;
@@ -89,6 +100,7 @@ struct labs_batch {
   bool own_stream = false;
   bool use_graph = false;
   int rounds_per_launch = 4;
+  bool warp_allowed = false;  // every problem has at most kWarpModeMaxWalks walks
   // per-problem device state, one allocation
   void *state_block = nullptr;
   BatchProblem *d_probs = nullptr;
@@ -98,6 +110,8 @@ struct labs_batch {
   std::vector<uint32_t> rec_base, ring;
   // round records (one ring per problem, plus one record the autotuner's sample uses)
   void *rec_block = nullptr;
+  uint32_t *keys_block = nullptr;  // the records' key slots, sized once the classes' modes are known
+  unsigned long long *d_key_base = nullptr;
   RoundRecords rec{};
   uint32_t n_records = 0, tune_record = 0;
   // per launch
@@ -141,6 +155,7 @@ labs_batch::~labs_batch() {
   }
   cudaFree(state_block);
   cudaFree(rec_block);
+  cudaFree(keys_block);
   cudaFree(d_issue);
   cudaFree(d_task_next);
   cudaFree(d_err);
@@ -197,7 +212,8 @@ labs_status build_pools(labs_batch *b) {
       words = std::max(words, w);
     }
     c.pool_words = (words + 1) / 2 * 2;
-    c.resident = batch_resident_lanes(c.W, c.block);
+    // a table per lane, or per warp in warp mode
+    c.resident = c.warp ? batch_resident_warps(c.W, c.block) : batch_resident_lanes(c.W, c.block);
     if (c.resident <= 0) return LABS_ECUDA;
     BCU(dalloc(&c.pool, (size_t)c.resident * c.pool_words));
   }
@@ -236,12 +252,13 @@ labs_status plan_launch(labs_batch *b, const std::vector<int32_t> &next_round, c
       const labs_problem &p = b->pr[i];
       uint64_t r = std::min<uint64_t>(rounds_needed(p, evals[i]), b->ring[i]);
       if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
-      const uint32_t chunks = (uint32_t)((p.walks + 31) / 32);
+      const bool warp = b->cls[ci].warp;
+      const uint32_t chunks = warp ? (uint32_t)p.walks : (uint32_t)((p.walks + 31) / 32);
       const double cost = task_cost(p);
       for (uint32_t k = 0; k < (uint32_t)r; ++k) {
         const uint32_t round = (uint32_t)next_round[i] + k;
         const uint32_t rec = b->rec_base[i] + round % b->ring[i];
-        issue.push_back(RecordInit{rec, round, chunks});
+        issue.push_back(RecordInit{rec, round, chunks, warp ? 0u : 5u});
         for (uint32_t ch = 0; ch < chunks; ++ch)
           tk[ci].push_back({p.target_E >= 0 ? k : 0u, cost, BatchTask{(uint32_t)i, round, ch, rec}});
       }
@@ -293,7 +310,8 @@ labs_status enqueue_launch(labs_batch *b, std::vector<std::pair<cudaEvent_t, cud
     cudaStream_t x = b->cs[ci];
     BCU(cudaStreamWaitEvent(x, b->fork, 0));
     if (c.n_tasks) {
-      BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr));
+      if (c.warp) BCU(launch_batch_warp(c.W, c.block, kernel_params(b, c, (int)ci), x));
+      else BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr));
       ++*launches;
     }
     BCU(cudaEventRecord(b->cs_done[ci], x));
@@ -316,87 +334,116 @@ labs_status reset_state(labs_batch *b, int *launches) {
   return LABS_OK;
 }
 
-// Time candidate shapes (walks per CTA x table capacity) of one class on a
-// sample of its tasks (rounds no solve uses) with walks shortened to at most
-// 256 steps; the sample's tasks all count into one record that never completes.
+// Rounds problem p's first launch runs.
+uint32_t first_launch_rounds(const labs_batch *b, const labs_problem &p) {
+  uint64_t r = std::min<uint64_t>(rounds_needed(p, 0), kMaxRingRounds);
+  if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
+  return (uint32_t)r;
+}
+
+// Time candidate launch shapes of one class: lane mode (one walk per lane,
+// tasks of 32 walks) with walks per CTA in {64, 128, 256} and table capacity
+// in {1.5, 3} x pivots, and warp mode (one walk per warp) with 128 or 256
+// threads per CTA.  Each candidate runs the class's first launch as far as one
+// wave of its resident lanes (or warps) reaches, on rounds no solve uses, with
+// walks shortened to at most 256 steps; the one with the lowest time per
+// neighbour evaluation wins (cached per process).  The sample's tasks all
+// count into one record that never completes.
 labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
-  int max_len = 0, max_walks = 0;
+  int max_len = 0;
+  uint64_t lane_tasks = 0, walk_tasks = 0;
   for (int i : c.probs) {
-    max_len = std::max(max_len, b->pr[i].walk_len);
-    max_walks = std::max(max_walks, b->pr[i].walks);
+    const labs_problem &p = b->pr[i];
+    max_len = std::max(max_len, p.walk_len);
+    lane_tasks += (uint64_t)((p.walks + 31) / 32) * first_launch_rounds(b, p);
+    walk_tasks += (uint64_t)p.walks * first_launch_rounds(b, p);
   }
-  const TuneKey key{c.W, ilog2((uint64_t)max_len), ilog2((uint64_t)max_walks)};
+  const TuneKey key{c.W, ilog2((uint64_t)max_len), ilog2(walk_tasks)};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      c.block = it->second.first;
-      c.factor_x10 = it->second.second;
+      c.block = it->second.block;
+      c.factor_x10 = it->second.factor_x10;
+      c.warp = it->second.warp;
       return LABS_OK;
     }
   }
-  const int blocks[] = {64, 128, 256};
-  const int factors[] = {15, 30};
-  float best_ms = 1e30f;
-  int best_block = c.block, best_factor = c.factor_x10;
+  struct Cand {
+    bool warp;
+    int block, factor;
+  };
+  std::vector<Cand> cands;
+  for (int fct : {15, 30})
+    for (int blk : {64, 128, 256}) cands.push_back({false, blk, fct});
+  if (b->warp_allowed)
+    for (int blk : {128, 256}) cands.push_back({true, blk, kTableFactorX10});
+  double best_ns = 1e300;
+  Cand best = {c.warp, c.block, c.factor_x10};
   std::vector<labs_problem> saved = b->pr;
   for (int i : c.probs) b->pr[i].walk_len = std::min(b->pr[i].walk_len, 256);
   auto restore = [&](labs_status st) {
     b->pr = saved;
     return st;
   };
-  for (int fct : factors) {
-    for (int blk : blocks) {
-      c.block = blk;
-      c.factor_x10 = fct;
-      labs_status st = build_pools(b);
-      if (st != LABS_OK) return restore(st);
-      // one wave of tasks
-      std::vector<BatchTask> tk;
-      const size_t want = (size_t)std::max(1, c.resident / 32);
-      for (size_t k = 0; tk.size() < want && k < 4 * want; ++k) {
-        const int i = c.probs[k % c.probs.size()];
-        const uint32_t chunks = (uint32_t)((b->pr[i].walks + 31) / 32);
-        tk.push_back(BatchTask{(uint32_t)i, 1000u + (uint32_t)(k / c.probs.size()), (uint32_t)(k % chunks),
-                               b->tune_record});
-      }
-      if (tk.size() > c.tasks_cap) {
-        cudaFree(c.tasks);
-        c.tasks_cap = tk.size();
-        if (dalloc(&c.tasks, c.tasks_cap) != cudaSuccess) return restore(LABS_ENOMEM);
-      }
-      if (cudaMemcpy(c.tasks, tk.data(), sizeof(BatchTask) * tk.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-        return restore(LABS_ECUDA);
-      c.n_tasks = (uint32_t)tk.size();
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaMemsetAsync(b->d_task_next + ci, 0, sizeof(unsigned int), b->s);
-        cudaMemsetAsync(b->rec.left + b->tune_record, 0xFF, sizeof(uint32_t), b->s);
-        cudaEventRecord(e0, b->s);
-        launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr);
-        cudaEventRecord(e1, b->s);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&ms, e0, e1);
-      }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      if (cudaGetLastError() != cudaSuccess) return restore(LABS_ECUDA);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_block = blk;
-        best_factor = fct;
-      }
+  for (const Cand &cd : cands) {
+    c.warp = cd.warp;
+    c.block = cd.block;
+    c.factor_x10 = cd.factor;
+    labs_status st = build_pools(b);
+    if (st != LABS_OK) return restore(st);
+    // the first launch's tasks, as far as one wave reaches
+    const uint64_t wave = cd.warp ? (uint64_t)c.resident : (uint64_t)c.resident / 32;
+    const uint64_t want = std::max<uint64_t>(1, std::min(cd.warp ? walk_tasks : lane_tasks, wave));
+    std::vector<BatchTask> tk;
+    for (uint64_t k = 0; tk.size() < want; ++k) {
+      const int i = c.probs[k % c.probs.size()];
+      const uint32_t units = cd.warp ? (uint32_t)b->pr[i].walks : (uint32_t)((b->pr[i].walks + 31) / 32);
+      const uint64_t pass = k / c.probs.size();
+      tk.push_back(BatchTask{(uint32_t)i, 1000u + (uint32_t)(pass / units), (uint32_t)(pass % units),
+                             b->tune_record});
+    }
+    if (tk.size() > c.tasks_cap) {
+      cudaFree(c.tasks);
+      c.tasks_cap = tk.size();
+      if (dalloc(&c.tasks, c.tasks_cap) != cudaSuccess) return restore(LABS_ENOMEM);
+    }
+    if (cudaMemcpy(c.tasks, tk.data(), sizeof(BatchTask) * tk.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return restore(LABS_ECUDA);
+    c.n_tasks = (uint32_t)tk.size();
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float ms = 0.f;
+    unsigned long long evals = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      cudaMemsetAsync(b->d_task_next + ci, 0, sizeof(unsigned int), b->s);
+      cudaMemsetAsync(b->rec.left + b->tune_record, 0xFF, sizeof(uint32_t), b->s);
+      cudaMemsetAsync(b->rec.evals + b->tune_record, 0, sizeof(unsigned long long), b->s);
+      cudaEventRecord(e0, b->s);
+      if (cd.warp) launch_batch_warp(c.W, c.block, kernel_params(b, c, ci), b->s);
+      else launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr);
+      cudaEventRecord(e1, b->s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaMemcpy(&evals, b->rec.evals + b->tune_record, sizeof(evals), cudaMemcpyDeviceToHost);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return restore(LABS_ECUDA);
+    const double ns = 1e6 * (double)ms / (double)std::max<unsigned long long>(1, evals);
+    if (ns < best_ns) {
+      best_ns = ns;
+      best = cd;
     }
   }
   b->pr = saved;
-  c.block = best_block;
-  c.factor_x10 = best_factor;
+  c.warp = best.warp;
+  c.block = best.block;
+  c.factor_x10 = best.factor;
   c.n_tasks = 0;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[key] = {best_block, best_factor};
+  g_tuned[key] = Tuned{best.block, best.factor, best.warp};
   return LABS_OK;
 }
 
@@ -457,8 +504,8 @@ labs_status alloc_state(labs_batch *b) {
   off = 0;
   const size_t r_best = take(sizeof(unsigned long long) * nr), r_evals = take(sizeof(unsigned long long) * nr),
                r_planes = take(sizeof(unsigned long long) * nr), r_left = take(sizeof(uint32_t) * nr),
-               r_round = take(sizeof(uint32_t) * nr),
-               r_keys = take(sizeof(uint32_t) * kKeyWords * nr * b->rec.max_chunks);
+               r_round = take(sizeof(uint32_t) * nr), r_shift = take(sizeof(uint32_t) * nr),
+               r_kbase = take(sizeof(unsigned long long) * nr);
   char *rb = nullptr;
   BCU(cudaMalloc((void **)&rb, off));
   b->rec_block = rb;
@@ -469,8 +516,14 @@ labs_status alloc_state(labs_batch *b) {
   b->rec.planes = reinterpret_cast<unsigned long long *>(rb + r_planes);
   b->rec.left = reinterpret_cast<uint32_t *>(rb + r_left);
   b->rec.round = reinterpret_cast<uint32_t *>(rb + r_round);
-  b->rec.keys = reinterpret_cast<uint32_t *>(rb + r_keys);
+  b->rec.shift = reinterpret_cast<uint32_t *>(rb + r_shift);
+  b->d_key_base = reinterpret_cast<unsigned long long *>(rb + r_kbase);
+  b->rec.key_base = b->d_key_base;
   b->tune_record = b->n_records;
+  // until the classes' modes are known only the autotuner's record has key
+  // slots (every record's base is 0 meanwhile; none of them runs before alloc_keys)
+  BCU(dalloc(&b->keys_block, kTuneKeySlots * kKeyWords));
+  b->rec.keys = b->keys_block;
   // the snapshot block
   off = 0;
   const size_t s_done = take(sizeof(int32_t) * n), s_rounds = take(sizeof(int32_t) * n),
@@ -491,6 +544,31 @@ labs_status alloc_state(labs_batch *b) {
   BCU(dalloc(&b->d_task_next, b->cls.size()));
   BCU(dalloc(&b->d_err, 1));
   BCU(cudaMemset(b->d_err, 0, sizeof(int32_t)));
+  return LABS_OK;
+}
+
+// Key slots of every record for the classes' chosen modes: a slot per chunk of
+// 32 walks in lane mode, per walk in warp mode; the autotuner's slots first.
+labs_status alloc_keys(labs_batch *b) {
+  std::vector<unsigned long long> base(b->n_records + 1);
+  unsigned long long next = kTuneKeySlots;
+  base[b->tune_record] = 0;
+  for (size_t i = 0; i < b->pr.size(); ++i) {
+    bool warp = false;
+    for (auto &c : b->cls)
+      if (c.W == b->W[i]) warp = c.warp;
+    const unsigned long long slots = warp ? (unsigned long long)b->pr[i].walks
+                                          : (unsigned long long)((b->pr[i].walks + 31) / 32);
+    for (uint32_t k = 0; k < b->ring[i]; ++k) {
+      base[b->rec_base[i] + k] = next;
+      next += slots;
+    }
+  }
+  cudaFree(b->keys_block);
+  b->keys_block = nullptr;
+  BCU(dalloc(&b->keys_block, (size_t)next * kKeyWords));
+  b->rec.keys = b->keys_block;
+  BCU(cudaMemcpy(b->d_key_base, base.data(), sizeof(unsigned long long) * base.size(), cudaMemcpyHostToDevice));
   return LABS_OK;
 }
 
@@ -520,7 +598,8 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (opts_in) opts = *opts_in;
   if (opts.block_threads < 0 || opts.block_threads > 256 || (opts.block_threads % 32) != 0 ||
       opts.table_factor_x10 < 0 || (opts.table_factor_x10 > 0 && opts.table_factor_x10 < 12) ||
-      opts.rounds_per_launch < 0 || opts.rounds_per_launch > (int32_t)kMaxRingRounds)
+      opts.rounds_per_launch < 0 || opts.rounds_per_launch > (int32_t)kMaxRingRounds || opts.walk_mode < 0 ||
+      opts.walk_mode > 2)
     return LABS_EINVAL;
   for (int i = 0; i < n; ++i)
     if (!valid_problem(problems[i])) return LABS_EINVAL;
@@ -543,7 +622,7 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
     delete b;
     return e;
   };
-  uint32_t max_chunks = 1;
+  uint32_t max_walks = 1;
   for (int i = 0; i < n; ++i) {
     const labs_problem &p = problems[i];
     const int W = lag_words(p.L);
@@ -559,16 +638,17 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
       cp->factor_x10 = opts.table_factor_x10 ? opts.table_factor_x10 : kTableFactorX10;
     }
     cp->probs.push_back(i);
-    max_chunks = std::max<uint32_t>(max_chunks, (uint32_t)((p.walks + 31) / 32));
+    max_walks = std::max<uint32_t>(max_walks, (uint32_t)p.walks);
     b->seq_stride = std::max(b->seq_stride, (int)p.L);
     // the problem's ring: the rounds its first launch issues
-    uint64_t r = std::min<uint64_t>(rounds_needed(p, 0), kMaxRingRounds);
-    if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
+    const uint32_t r = first_launch_rounds(b, p);
     b->rec_base.push_back(b->n_records);
     b->ring.push_back((uint32_t)r);
     b->n_records += (uint32_t)r;
   }
-  b->rec.max_chunks = max_chunks;
+  b->warp_allowed = max_walks <= (uint32_t)kWarpModeMaxWalks && opts.walk_mode != 1;
+  if (opts.walk_mode == 2 && !b->warp_allowed) return fail(LABS_EINVAL);
+  for (auto &c : b->cls) c.warp = opts.walk_mode == 2;
   std::sort(b->cls.begin(), b->cls.end(), [](const ClassPlan &x, const ClassPlan &y) { return x.W > y.W; });
   if ((st = alloc_state(b)) != LABS_OK) return fail(st);
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
@@ -584,13 +664,14 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (opts.autotune) {
     for (size_t ci = 0; ci < b->cls.size(); ++ci) {
       ClassPlan &c = b->cls[ci];
-      const bool fixed = opts.block_threads && opts.table_factor_x10;
+      const bool fixed = (opts.block_threads && opts.table_factor_x10) || opts.walk_mode == 2;
       if (!fixed && (st = autotune_class(b, c, (int)ci)) != LABS_OK) return fail(st);
       if (opts.block_threads) c.block = opts.block_threads;
       if (opts.table_factor_x10) c.factor_x10 = opts.table_factor_x10;
     }
     if ((st = build_pools(b)) != LABS_OK) return fail(st);
   }
+  if ((st = alloc_keys(b)) != LABS_OK) return fail(st);
   *out = b;
   return LABS_OK;
 }
@@ -632,7 +713,13 @@ extern "C" labs_status labs_batch_run(labs_batch *b, labs_stats *stats) {
         BCU(ee);
         b->launches_per_graph = cl;
       }
+      cudaEvent_t g0 = nullptr, g1 = nullptr;
+      BCU(cudaEventCreate(&g0));
+      BCU(cudaEventCreate(&g1));
+      BCU(cudaEventRecord(g0, b->s));
       BCU(cudaGraphLaunch(b->graph, b->s));
+      BCU(cudaEventRecord(g1, b->s));
+      ev.push_back({g0, g1});
       launches += b->launches_per_graph;
       for (auto &c : b->cls) walk_launches += c.n_tasks ? 1 : 0;
     } else {
@@ -717,13 +804,15 @@ extern "C" labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, ui
 }
 
 extern "C" labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads,
-                                        int32_t *table_factor_x10, int32_t *resident_walks) {
+                                        int32_t *table_factor_x10, int32_t *resident_walks,
+                                        int32_t *warp_per_walk) {
   if (!b) return LABS_EINVAL;
   for (auto &c : b->cls) {
     if (c.W != W) continue;
     if (block_threads) *block_threads = c.block;
     if (table_factor_x10) *table_factor_x10 = c.factor_x10;
     if (resident_walks) *resident_walks = c.resident;
+    if (warp_per_walk) *warp_per_walk = c.warp ? 1 : 0;
     return LABS_OK;
   }
   return LABS_ENOTFOUND;

@@ -7,6 +7,7 @@
 
 #include "batch.cuh"
 #include "walk_device.cuh"
+#include "walk_warp.cuh"
 
 namespace psaw {
 
@@ -29,6 +30,10 @@ struct MaxRegsFor {
 // shared memory words of one warp: mask table, then (W + 2) parked words per lane
 template <int W>
 constexpr int kBatchWarpWords = MaskTable<W>::kWords + (W + 2) * 32;
+// in warp mode (one walk per warp): mask table, then the walk's shared words,
+// rounded to 16 bytes so that every warp's mask table stays 16-byte aligned
+template <int W>
+constexpr int kBatchWalkWarpWords = (MaskTable<W>::kWords + WarpWalkSmem<W>::kWords + 3) / 4 * 4;
 
 __device__ __forceinline__ uint32_t load_volatile(const uint32_t *x) { return *(const volatile uint32_t *)x; }
 __device__ __forceinline__ int32_t load_volatile(const int32_t *x) { return *(const volatile int32_t *)x; }
@@ -56,7 +61,8 @@ __device__ bool finalize_round(const RoundRecords &rec, const ProblemState &ps, 
     if (E < best) {
       best = E;
       ps.bestE[p] = E;
-      const uint32_t *src = rec.keys + ((size_t)j * rec.max_chunks + (w >> 5)) * kKeyWords;
+      // the round's key slots: one per chunk of 32 walks, or one per walk (warp mode)
+      const uint32_t *src = rec.keys + (__ldcg(rec.key_base + j) + (w >> __ldcg(rec.shift + j))) * kKeyWords;
       for (int i = 0; i < kKeyWords; ++i) ps.key[(size_t)p * kKeyWords + i] = __ldcg(src + i);
       ps.best_round[p] = (int32_t)r;
       ps.best_walk[p] = (int32_t)w;
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
       planes += __shfl_xor_sync(0xFFFFFFFFu, planes, off);
     }
     if (active && packed == m) {
-      uint32_t *k = p.rec.keys + ((size_t)task.rec * p.rec.max_chunks + task.chunk) * kKeyWords;
+      uint32_t *k = p.rec.keys + (p.rec.key_base[task.rec] + task.chunk) * kKeyWords;
 #pragma unroll
       for (int w = 0; w < kKeyWords; ++w) k[w] = w < NS ? o.best_key[w] : 0u;
     }
@@ -175,6 +181,61 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
   }
 }
 
+// Warp mode: every warp takes tasks of one walk (task.chunk = the walk's
+// index) and runs the walk with its 32 lanes splitting the flips
+// (run_walk_warp); one visited table per warp.  The walk publishes its best
+// key in its own key slot of the round's record.
+template <int W>
+__global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::value)
+    batch_kernel_warp(const BatchKernelParams p) {
+  constexpr int T = PlanesFor<W>::value;
+  constexpr int NS = W + 1;
+  const int lane = threadIdx.x & 31;
+  const size_t gwarp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint64_t *table = p.pool + gwarp * p.pool_words;
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  extern __shared__ __align__(16) uint32_t batch_smem[];
+  uint32_t *mask_rows = batch_smem + (size_t)(threadIdx.x >> 5) * kBatchWalkWarpWords<W>;
+  uint32_t *wsm = mask_rows + MaskTable<W>::kWords;
+  int rows_L = 0;
+  for (;;) {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(p.task_next, 1u);
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    if (t >= p.n_tasks) break;
+    const BatchTask task = p.tasks[t];
+    if (load_volatile(p.ps.done + task.problem)) continue;
+    const BatchProblem pr = p.probs[task.problem];
+    const uint32_t walk = task.chunk;
+    const size_t words = (size_t)pr.cap * (size_t)pr.kw64;  // even: cap >= 64
+    uint4 *t4 = reinterpret_cast<uint4 *>(table);
+    for (size_t i = (size_t)lane; i < words / 2; i += 32) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    const Geometry g = make_geometry(pr.L, T);
+    if (pr.L != rows_L) {
+      fill_mask_rows<W>(g, mask_rows, lane, 32);
+      rows_L = pr.L;
+    }
+    __syncwarp();
+    WalkOut<NS> o;
+    run_walk_warp<W, T, kTopK>(g, mu, mask_rows, wsm, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
+                               pr.kw64, 0, nullptr, p.err, o);
+    if (lane == 0) {
+      uint32_t *k = p.rec.keys + (p.rec.key_base[task.rec] + walk) * kKeyWords;
+#pragma unroll
+      for (int w = 0; w < kKeyWords; ++w) k[w] = w < NS ? o.best_key[w] : 0u;
+      atomicMin(&p.rec.best[task.rec], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
+      atomicAdd(&p.rec.evals[task.rec], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
+      atomicAdd(&p.rec.planes[task.rec], (unsigned long long)o.planes);
+      __threadfence();
+      if (atomicSub(&p.rec.left[task.rec], 1u) == 1u) {
+        __threadfence();
+        try_finalize(p.rec, p.ps, (int)task.problem);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // dynamic shared memory of a block: one mask table per warp
 template <int W>
 static size_t batch_smem_bytes(int block) {
@@ -185,6 +246,41 @@ template <int W>
 static cudaError_t set_batch_smem(int block) {
   return cudaFuncSetAttribute(batch_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)batch_smem_bytes<W>(block));
+}
+
+template <int W>
+static size_t batch_warp_smem_bytes(int block) {
+  return (size_t)(block / 32) * kBatchWalkWarpWords<W> * sizeof(uint32_t);
+}
+
+template <int W>
+static cudaError_t launch_batch_warp_w(int block, const BatchKernelParams &p, cudaStream_t s, int max_blocks) {
+  const size_t smem = batch_warp_smem_bytes<W>(block);
+  cudaError_t e = cudaFuncSetAttribute(batch_kernel_warp<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_warp<W>, block, smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  int grid = per_sm * sms;
+  if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  batch_kernel_warp<W><<<grid, block, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int W>
+static int resident_warps_w(int block) {
+  const size_t smem = batch_warp_smem_bytes<W>(block);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaFuncSetAttribute(batch_kernel_warp<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_warp<W>, block, smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return per_sm * sms * (block / 32);
 }
 
 template <int W>
@@ -216,6 +312,35 @@ static int resident_w(int block) {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   return per_sm * sms * block;
+}
+
+cudaError_t launch_batch_warp(int W, int block, const BatchKernelParams &p, cudaStream_t s, int max_blocks) {
+  if (block < 32 || block > kBatchMaxThreads || block % 32) return cudaErrorInvalidValue;
+  switch (W) {
+    case 1: return launch_batch_warp_w<1>(block, p, s, max_blocks);
+    case 2: return launch_batch_warp_w<2>(block, p, s, max_blocks);
+    case 3: return launch_batch_warp_w<3>(block, p, s, max_blocks);
+    case 4: return launch_batch_warp_w<4>(block, p, s, max_blocks);
+    case 5: return launch_batch_warp_w<5>(block, p, s, max_blocks);
+    case 6: return launch_batch_warp_w<6>(block, p, s, max_blocks);
+    case 7: return launch_batch_warp_w<7>(block, p, s, max_blocks);
+    case 8: return launch_batch_warp_w<8>(block, p, s, max_blocks);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batch_resident_warps(int W, int block) {
+  switch (W) {
+    case 1: return resident_warps_w<1>(block);
+    case 2: return resident_warps_w<2>(block);
+    case 3: return resident_warps_w<3>(block);
+    case 4: return resident_warps_w<4>(block);
+    case 5: return resident_warps_w<5>(block);
+    case 6: return resident_warps_w<6>(block);
+    case 7: return resident_warps_w<7>(block);
+    case 8: return resident_warps_w<8>(block);
+    default: return 0;
+  }
 }
 
 cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out,
@@ -272,6 +397,7 @@ __global__ void issue_records_kernel(const RecordInit *list, int n, const RoundR
   rec.evals[ri.rec] = 0;
   rec.planes[ri.rec] = 0;
   rec.left[ri.rec] = ri.chunks;
+  rec.shift[ri.rec] = ri.shift;
   __threadfence();
   rec.round[ri.rec] = ri.round;
 }

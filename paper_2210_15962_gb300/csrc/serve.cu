@@ -50,6 +50,9 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr int kSeqStride = 512;  // bytes per slot of the expanded best sequences (>= LABS_L_MAX)
 constexpr int kDepth = 2;        // launches in flight
 constexpr int kRingFactor = 3;   // round records per slot = kRingFactor x rounds_per_launch
+// Warp mode keeps a key slot per walk in every round record: it is offered
+// while max_walks is at most this.
+constexpr int kWarpModeMaxWalks = 4096;
 
 struct Request {
   uint64_t ticket = 0;
@@ -70,7 +73,7 @@ struct Request {
 // What one launch runs for one request: its rounds (k) and the sizes that
 // decide the launch's device memory.
 struct Share {
-  int slot, W, L, walk_len;
+  int slot, W, L, walk_len, walks;
   uint32_t k, chunks;
   size_t table_words;  // 64-bit words of one walk's visited table
 };
@@ -81,6 +84,7 @@ Share share_of(int slot, const labs_problem &p, uint32_t k) {
   s.W = lag_words(p.L);
   s.L = p.L;
   s.walk_len = p.walk_len;
+  s.walks = p.walks;
   s.k = k;
   s.chunks = (uint32_t)((p.walks + 31) / 32);
   s.table_words = (size_t)visited_table_cap(p.walk_len) * (size_t)key_words64((p.L + 1) / 2);
@@ -88,36 +92,63 @@ Share share_of(int slot, const labs_problem &p, uint32_t k) {
   return s;
 }
 
+// What the scheduler knows of each lag-word class: the lanes (one walk per
+// lane) and warps (one walk per warp) its kernels keep resident, and the
+// evaluations per second one resident warp does in each mode, measured when
+// the server is created.
+struct ClassInfo {
+  int lanes = 0, warps = 0;
+  double rate_lane = 1.0, rate_warp = 0.0;  // per resident warp; 0 = warp mode not offered
+};
+
+// Lane or warp mode for a class in one launch: the one whose resident warps,
+// filled with as many of the launch's tasks as there are, evaluate faster (one
+// walk per lane fills a warp per 32 walks, one walk per warp a warp per walk).
+bool choose_warp(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) {
+  if (ci.rate_warp <= 0.0) return false;
+  const double lane = (double)std::min<uint64_t>(chunk_tasks, (uint64_t)ci.lanes / 32) * ci.rate_lane;
+  const double warp = (double)std::min<uint64_t>(walk_tasks, (uint64_t)ci.warps) * ci.rate_warp;
+  return warp > lane;
+}
+
 // Layout of one launch inside its half of the arena (byte offsets; sizes
 // only when computed for admission): the lists uploaded from the host (the
 // listed problems, the records to issue, the task list of each class), then
-// one visited-table pool per class with a lane for each task the class can run
-// at once.
+// one visited-table pool per class with a table for each lane (or warp, in
+// warp mode) that can run one of its tasks at once.
 struct Carve {
   size_t problems = 0, issue = 0, recs = 0;
   std::vector<size_t> tasks;  // per class
   size_t upload_bytes = 0;
   std::vector<size_t> pool;        // per class
   std::vector<size_t> pool_words;  // per class, per lane
-  std::vector<int> lanes;          // per class
+  std::vector<int> lanes;          // per class: lanes, or warps in warp mode, of the grid
   std::vector<uint32_t> n_tasks;   // per class
+  std::vector<uint8_t> warp;       // per class: warp mode
   uint32_t n_problems = 0, n_issue = 0;
   size_t total = 0;
 };
 
-Carve carve_launch(const std::vector<Share> &sh, const std::vector<int> &resident, int block) {
-  const size_t nc = resident.size();
+Carve carve_launch(const std::vector<Share> &sh, const std::vector<ClassInfo> &cls, int block) {
+  const size_t nc = cls.size();
   Carve c;
   c.tasks.assign(nc, 0);
   c.pool.assign(nc, 0);
   c.pool_words.assign(nc, 0);
   c.lanes.assign(nc, 0);
   c.n_tasks.assign(nc, 0);
+  c.warp.assign(nc, 0);
   c.n_problems = (uint32_t)sh.size();
+  std::vector<uint64_t> chunk_tasks(nc, 0), walk_tasks(nc, 0);
   for (const Share &s : sh) {
     c.n_issue += s.k;
-    c.n_tasks[s.W - 1] += s.k * s.chunks;
+    chunk_tasks[s.W - 1] += (uint64_t)s.k * s.chunks;
+    walk_tasks[s.W - 1] += (uint64_t)s.k * (uint64_t)s.walks;
     if (s.k) c.pool_words[s.W - 1] = std::max(c.pool_words[s.W - 1], s.table_words);
+  }
+  for (size_t w = 0; w < nc; ++w) {
+    c.warp[w] = choose_warp(cls[w], chunk_tasks[w], walk_tasks[w]) ? 1 : 0;
+    c.n_tasks[w] = (uint32_t)(c.warp[w] ? walk_tasks[w] : chunk_tasks[w]);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -132,8 +163,11 @@ Carve carve_launch(const std::vector<Share> &sh, const std::vector<int> &residen
   c.upload_bytes = off;
   for (size_t w = 0; w < nc; ++w) {
     if (!c.n_tasks[w]) continue;
-    const size_t want = ((size_t)c.n_tasks[w] * 32 + block - 1) / block * block;
-    c.lanes[w] = (int)std::min<size_t>(want, (size_t)resident[w]);
+    // a table per lane (32 per task) or per warp (one per task), whole CTAs, at most the resident ones
+    const size_t per_block = c.warp[w] ? (size_t)block / 32 : (size_t)block;
+    const size_t units = c.warp[w] ? (size_t)c.n_tasks[w] : (size_t)c.n_tasks[w] * 32;
+    const size_t want = (units + per_block - 1) / per_block * per_block;
+    c.lanes[w] = (int)std::min<size_t>(want, (size_t)(c.warp[w] ? cls[w].warps : cls[w].lanes));
     c.pool[w] = take(sizeof(uint64_t) * c.pool_words[w] * (size_t)c.lanes[w]);
   }
   c.total = off;
@@ -193,7 +227,8 @@ struct labs_server {
   int32_t *d_err = nullptr;
   uint32_t ring = 0;
   char *arena = nullptr;
-  std::vector<int> resident;  // per class W - 1
+  std::vector<ClassInfo> cls;  // per class W - 1
+  bool warp_allowed = false;
   Launch L[kDepth];
   cudaEvent_t t_ref = nullptr;
   uint64_t harvested = 0;  // id of the last launch harvested
@@ -204,6 +239,8 @@ struct labs_server {
   size_t admitted_carve(const Request *extra);                      // caller holds mu
   labs_status enqueue(Launch &l, const std::vector<int> &admitted);  // caller does not hold mu
   labs_status harvest(Launch &l);
+  labs_status tune_modes();
+  uint32_t tune_record = 0;
 };
 
 labs_server::~labs_server() {
@@ -230,7 +267,7 @@ size_t labs_server::admitted_carve(const Request *extra) {
     if (slot_ticket[sl] && !slot_draining[sl])
       sh.push_back(share_of(sl, reqs[slot_ticket[sl]]->p, (uint32_t)cfg.rounds_per_launch));
   if (extra) sh.push_back(share_of(-1, extra->p, (uint32_t)cfg.rounds_per_launch));
-  return carve_launch(sh, resident, cfg.block_threads).total;
+  return carve_launch(sh, cls, cfg.block_threads).total;
 }
 
 // Rounds the next launch gives a request: what its budget still needs beyond
@@ -287,7 +324,7 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
       l.slots.push_back(sl);
     }
   }
-  const Carve cv = carve_launch(sh, resident, cfg.block_threads);
+  const Carve cv = carve_launch(sh, cls, cfg.block_threads);
   if (cv.total > half_bytes) return LABS_ENOMEM;  // admission keeps this from happening
   l.carve_bytes = cv.total;
   // the uploaded lists
@@ -295,21 +332,23 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
   int32_t *plist = reinterpret_cast<int32_t *>(up.data() + cv.problems);
   RecordInit *ilist = reinterpret_cast<RecordInit *>(up.data() + cv.issue);
   uint32_t *rlist = reinterpret_cast<uint32_t *>(up.data() + cv.recs);
-  std::vector<std::vector<PlannedTask>> tk(resident.size());
+  std::vector<std::vector<PlannedTask>> tk(cls.size());
   size_t ni = 0;
   for (size_t i = 0; i < sh.size(); ++i) {
     const Share &s = sh[i];
     plist[i] = s.slot;
     const double cost = batch_task_cost(s.L, s.walk_len);
     const bool layered = target[s.slot] >= 0;
+    const bool warp = cv.warp[s.W - 1] != 0;
+    const uint32_t units = warp ? (uint32_t)s.walks : s.chunks;  // tasks per round: walks, or chunks of 32
     for (uint32_t j = 0; j < s.k; ++j) {
       const uint32_t round = first_round[s.slot] + j;
       const uint32_t recx = (uint32_t)s.slot * ring + round % ring;
-      ilist[ni] = RecordInit{recx, round, s.chunks};
+      ilist[ni] = RecordInit{recx, round, units, warp ? 0u : 5u};
       rlist[ni] = recx;
       ++ni;
-      for (uint32_t ch = 0; ch < s.chunks; ++ch)
-        tk[s.W - 1].push_back({layered ? j : 0u, cost, BatchTask{(uint32_t)s.slot, round, ch, recx}});
+      for (uint32_t u = 0; u < units; ++u)
+        tk[s.W - 1].push_back({layered ? j : 0u, cost, BatchTask{(uint32_t)s.slot, round, u, recx}});
     }
   }
   for (size_t ci = 0; ci < tk.size(); ++ci) {
@@ -341,12 +380,12 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
   if (cudaEventRecord(l.ev0, s) != cudaSuccess ||
       launch_issue_records(reinterpret_cast<const RecordInit *>(a + cv.issue), (int)cv.n_issue, rec, s) !=
           cudaSuccess ||
-      cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int) * resident.size(), s) != cudaSuccess ||
+      cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int) * cls.size(), s) != cudaSuccess ||
       cudaEventRecord(l.fork, s) != cudaSuccess)
     return LABS_ECUDA;
   ++launches;
   l.walk_kernels = 0;
-  for (size_t ci = 0; ci < resident.size(); ++ci) {
+  for (size_t ci = 0; ci < cls.size(); ++ci) {
     if (!cv.n_tasks[ci]) continue;
     if (cudaStreamWaitEvent(l.cs[ci], l.fork, 0) != cudaSuccess) return LABS_ECUDA;
     BatchKernelParams k{};
@@ -364,10 +403,13 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
     k.mul_h31 = 0x80000000u;
     k.mul_h30 = 0x40000000u;
     k.err = d_err;
-    // the pool holds cv.lanes[ci] lanes: never more blocks than that
-    if (launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr, cv.lanes[ci] / cfg.block_threads) !=
-        cudaSuccess)
-      return LABS_ECUDA;
+    // the pool holds cv.lanes[ci] tables: never more blocks than that
+    const cudaError_t e =
+        cv.warp[ci] ? launch_batch_warp((int)ci + 1, cfg.block_threads, k, l.cs[ci],
+                                        cv.lanes[ci] / (cfg.block_threads / 32))
+                    : launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr,
+                                   cv.lanes[ci] / cfg.block_threads);
+    if (e != cudaSuccess) return LABS_ECUDA;
     if (cudaEventRecord(l.cs_done[ci], l.cs[ci]) != cudaSuccess ||
         cudaStreamWaitEvent(s, l.cs_done[ci], 0) != cudaSuccess)
       return LABS_ECUDA;
@@ -423,6 +465,9 @@ labs_status labs_server::harvest(Launch &l) {
   for (int sl : l.slots) {
     if (!slot_ticket[sl] || slot_draining[sl]) continue;
     Request &r = *reqs[slot_ticket[sl]];
+    // launches overlap, so a snapshot can be older than one already taken in:
+    // keep the view that has the most rounds finalized
+    if (rounds[sl] < r.rounds || (rounds[sl] == r.rounds && !done[sl] && r.rounds > 0)) continue;
     {
       evals_done += evals[sl] - r.evals;
       r.evals = evals[sl];
@@ -449,6 +494,108 @@ labs_status labs_server::harvest(Launch &l) {
   mem_used = admitted_carve(nullptr);
   if (any) finished.notify_all();
   return LABS_OK;
+}
+
+// Measure, for every class, the evaluations per second of one resident warp
+// in lane mode and in warp mode: one wave of each (as many lanes or warps as
+// stay resident, as far as half the arena holds their tables) on a sample
+// problem, the class's largest L up to max_L with walks of 128 steps, on a
+// round no request uses.  Slot 0 holds the sample problem meanwhile; its
+// tasks count into one record that never completes.
+labs_status labs_server::tune_modes() {
+  Launch &l = L[0];
+  cudaStream_t s = l.s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LABS_ECUDA;
+  labs_status st = LABS_OK;
+  for (size_t ci = 0; ci < cls.size() && st == LABS_OK; ++ci) {
+    const int W = (int)ci + 1;
+    const int L = std::min(cfg.max_L, 64 * W + 1);
+    const int D = (L + 1) / 2;
+    BatchProblem pr{};
+    pr.L = L;
+    pr.W = W;
+    pr.walk_len = std::min(8 * D, 128);
+    pr.walks = std::max(cls[ci].lanes, cls[ci].warps);
+    pr.cap = visited_table_cap(pr.walk_len);
+    pr.kw64 = key_words64(D);
+    pr.seed = 0x5EEDu;
+    const size_t words = ((size_t)pr.cap * pr.kw64 + 1) / 2 * 2;
+    const int32_t not_done = 0;
+    if (cudaMemcpyAsync(d_probs, &pr, sizeof(pr), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ps.done, &not_done, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      st = LABS_ECUDA;
+      break;
+    }
+    for (int mode = 0; mode < (warp_allowed ? 2 : 1) && st == LABS_OK; ++mode) {
+      const bool warp = mode == 1;
+      const int per_block = warp ? cfg.block_threads / 32 : cfg.block_threads;
+      size_t units = (size_t)(warp ? cls[ci].warps : cls[ci].lanes);
+      const size_t task_bytes = align_up(sizeof(BatchTask) * units);
+      const size_t fit = half_bytes > task_bytes ? (half_bytes - task_bytes) / (words * 8) : 0;
+      units = std::min(units, fit) / per_block * per_block;
+      if (!warp && units < 32) units = 0;
+      if (units == 0) {
+        if (warp) cls[ci].rate_warp = 0.0;
+        continue;
+      }
+      const size_t n_tasks = warp ? units : units / 32;
+      std::vector<BatchTask> tk(n_tasks);
+      for (size_t i = 0; i < n_tasks; ++i) tk[i] = BatchTask{0u, 1000000u, (uint32_t)i, tune_record};
+      BatchKernelParams k{};
+      k.probs = d_probs;
+      k.tasks = reinterpret_cast<const BatchTask *>(l.arena);
+      k.n_tasks = (uint32_t)n_tasks;
+      k.task_next = l.task_next;
+      k.pool = reinterpret_cast<uint64_t *>(l.arena + task_bytes);
+      k.pool_words = words;
+      k.rec = rec;
+      k.ps = ps;
+      k.mul_one = 1u;
+      k.mul_two = 2u;
+      k.mul_four = 4u;
+      k.mul_h31 = 0x80000000u;
+      k.mul_h30 = 0x40000000u;
+      k.err = d_err;
+      float ms = 0.f;
+      unsigned long long evals = 0;
+      if (cudaMemcpyAsync(l.arena, tk.data(), sizeof(BatchTask) * n_tasks, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+        st = LABS_ECUDA;
+      for (int rep = 0; rep < 2 && st == LABS_OK; ++rep) {  // the first run warms up
+        const cudaError_t e =
+            (cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int), s) != cudaSuccess ||
+             cudaMemsetAsync(rec.left + tune_record, 0xFF, sizeof(uint32_t), s) != cudaSuccess ||
+             cudaMemsetAsync(rec.evals + tune_record, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+             cudaEventRecord(e0, s) != cudaSuccess)
+                ? cudaErrorUnknown
+                : (warp ? launch_batch_warp(W, cfg.block_threads, k, s, (int)(units / per_block))
+                        : launch_batch(W, cfg.block_threads, k, s, nullptr, (int)(units / per_block)));
+        if (e != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          st = LABS_ECUDA;
+      }
+      if (st == LABS_OK &&
+          cudaMemcpy(&evals, rec.evals + tune_record, sizeof(evals), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = LABS_ECUDA;
+      if (st != LABS_OK) break;
+      const double warps_used = warp ? (double)units : (double)units / 32.0;
+      const double rate = (double)evals / (std::max(ms, 1e-3f) / 1e3) / warps_used;
+      if (warp) cls[ci].rate_warp = rate;
+      else cls[ci].rate_lane = rate;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int32_t free_slot = 1;
+  int32_t err = 0;
+  if (st == LABS_OK &&
+      (cudaMemcpyAsync(ps.done, &free_slot, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+       cudaMemcpyAsync(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    st = LABS_ECUDA;
+  if (st == LABS_OK && err) st = (err & kErrOverflow) ? LABS_EOVERFLOW : LABS_ECUDA;
+  return st;
 }
 
 void labs_server::fail_all(labs_status why) {
@@ -557,7 +704,8 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   if (cfg.max_active <= 0 || cfg.max_active > 4096 || cfg.max_L < LABS_L_MIN || cfg.max_L > LABS_L_MAX ||
       !(cfg.max_L & 1) || cfg.max_walks <= 0 || cfg.max_walks > (1 << 20) || cfg.max_walk_len < 0 ||
       cfg.rounds_per_launch <= 0 || cfg.rounds_per_launch > 64 || cfg.block_threads < 32 ||
-      cfg.block_threads > 256 || cfg.block_threads % 32 || cfg.mem_bytes < 2 * kAlign)
+      cfg.block_threads > 256 || cfg.block_threads % 32 || cfg.mem_bytes < 2 * kAlign || cfg.walk_mode < 0 ||
+      cfg.walk_mode > 2 || (cfg.walk_mode == 2 && cfg.max_walks > kWarpModeMaxWalks))
     return LABS_EINVAL;
   if (cfg.max_walk_len == 0) cfg.max_walk_len = 8 * ((cfg.max_L + 1) / 2);
   labs_server *sv = new (std::nothrow) labs_server();
@@ -573,6 +721,18 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   const uint32_t ring = (uint32_t)(kRingFactor * cfg.rounds_per_launch);
   const uint32_t max_chunks = (uint32_t)((cfg.max_walks + 31) / 32);
   const size_t nrec = (size_t)n * ring;
+  sv->warp_allowed = cfg.max_walks <= kWarpModeMaxWalks && cfg.walk_mode != 1;
+  const uint32_t max_keys = sv->warp_allowed ? (uint32_t)cfg.max_walks : max_chunks;
+  // what each class keeps resident in either mode (rates measured below)
+  size_t tune_slots = 1;
+  for (int W = 1; W <= Wmax; ++W) {
+    ClassInfo ci;
+    ci.lanes = batch_resident_lanes(W, cfg.block_threads);
+    ci.warps = batch_resident_warps(W, cfg.block_threads);
+    if (ci.lanes <= 0 || ci.warps <= 0) return fail(LABS_ECUDA);
+    sv->cls.push_back(ci);
+    tune_slots = std::max<size_t>(tune_slots, std::max(ci.lanes / 32, ci.warps));
+  }
   sv->ring = ring;
   sv->slot_ticket.assign(n, 0);
   sv->slot_listed.assign(n, 0);
@@ -592,9 +752,13 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
                o_bwalk = take(sizeof(int32_t) * n), o_evals = take(sizeof(unsigned long long) * n),
                o_planes = take(sizeof(unsigned long long) * n), o_rounds = take(sizeof(int32_t) * n),
                o_err = take(sizeof(int32_t)),
-               o_rbest = take(sizeof(unsigned long long) * nrec), o_revals = take(sizeof(unsigned long long) * nrec),
-               o_rplanes = take(sizeof(unsigned long long) * nrec), o_rleft = take(sizeof(uint32_t) * nrec),
-               o_rround = take(sizeof(uint32_t) * nrec), o_rkeys = take(sizeof(uint32_t) * kKeyWords * nrec * max_chunks);
+               o_rbest = take(sizeof(unsigned long long) * (nrec + 1)),
+               o_revals = take(sizeof(unsigned long long) * (nrec + 1)),
+               o_rplanes = take(sizeof(unsigned long long) * (nrec + 1)), o_rleft = take(sizeof(uint32_t) * (nrec + 1)),
+               o_rround = take(sizeof(uint32_t) * (nrec + 1)), o_rshift = take(sizeof(uint32_t) * (nrec + 1)),
+               o_rkbase = take(sizeof(unsigned long long) * (nrec + 1)),
+               // the records' key slots, then those of the one record the mode timing uses
+               o_rkeys = take(sizeof(uint32_t) * kKeyWords * (nrec * max_keys + tune_slots));
   char *fb = nullptr;
   if (cudaMalloc((void **)&fb, off) != cudaSuccess) return fail(LABS_ENOMEM);
   sv->fixed = fb;
@@ -622,25 +786,26 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   rec.planes = reinterpret_cast<unsigned long long *>(fb + o_rplanes);
   rec.left = reinterpret_cast<uint32_t *>(fb + o_rleft);
   rec.round = reinterpret_cast<uint32_t *>(fb + o_rround);
+  rec.shift = reinterpret_cast<uint32_t *>(fb + o_rshift);
   rec.keys = reinterpret_cast<uint32_t *>(fb + o_rkeys);
-  rec.max_chunks = max_chunks;
+  rec.key_base = reinterpret_cast<unsigned long long *>(fb + o_rkbase);
+  sv->tune_record = (uint32_t)nrec;
   {
     std::vector<uint32_t> base(n), rng(n, ring);
     for (int i = 0; i < n; ++i) base[i] = (uint32_t)i * ring;
     std::vector<int32_t> done(n, 1);  // free slots count as finished
+    std::vector<unsigned long long> kbase(nrec + 1);  // max_keys slots per record, then the timing record's
+    for (size_t j = 0; j <= nrec; ++j) kbase[j] = (unsigned long long)j * max_keys;
     if (cudaMemcpy(fb + o_base, base.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(fb + o_ring, rng.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(fb + o_done, done.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(fb + o_rround, 0xFF, sizeof(uint32_t) * nrec) != cudaSuccess)
+        cudaMemcpy(fb + o_rkbase, kbase.data(), sizeof(unsigned long long) * (nrec + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemset(fb + o_rround, 0xFF, sizeof(uint32_t) * (nrec + 1)) != cudaSuccess)
       return fail(LABS_ECUDA);
   }
   sv->half_bytes = cfg.mem_bytes / 2 / kAlign * kAlign;
   if (cudaMalloc((void **)&sv->arena, cfg.mem_bytes) != cudaSuccess) return fail(LABS_ENOMEM);
-  for (int W = 1; W <= Wmax; ++W) {
-    const int res = batch_resident_lanes(W, cfg.block_threads);
-    if (res <= 0) return fail(LABS_ECUDA);
-    sv->resident.push_back(res);
-  }
   // the launches in flight: streams, events, arena halves, snapshots
   for (int d = 0; d < kDepth; ++d) {
     Launch &l = sv->L[d];
@@ -692,6 +857,13 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   for (int d = 0; d < kDepth; ++d)
     if (cudaStreamWaitEvent(sv->L[d].s, sv->t_ref, 0) != cudaSuccess) return fail(LABS_ECUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LABS_ECUDA);
+  labs_status tst = sv->tune_modes();
+  if (tst != LABS_OK) return fail(tst);
+  if (cfg.walk_mode == 2)  // every launch in warp mode
+    for (auto &ci : sv->cls) {
+      ci.rate_warp = 1.0;
+      ci.rate_lane = 0.0;
+    }
   try {
     sv->th = std::thread([sv]() { sv->loop(); });
   } catch (...) {
@@ -711,7 +883,7 @@ extern "C" labs_status labs_serve_submit(labs_server *sv, const labs_problem *re
   if (p.L > sv->cfg.max_L || p.walks > sv->cfg.max_walks || p.walk_len > sv->cfg.max_walk_len) return LABS_ENOMEM;
   {
     std::vector<Share> one{share_of(-1, p, (uint32_t)sv->cfg.rounds_per_launch)};
-    if (carve_launch(one, sv->resident, sv->cfg.block_threads).total > sv->half_bytes) return LABS_ENOMEM;
+    if (carve_launch(one, sv->cls, sv->cfg.block_threads).total > sv->half_bytes) return LABS_ENOMEM;
   }
   auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
   if (!r) return LABS_ENOMEM;

@@ -201,7 +201,7 @@ def test_batch_rejects_bad_problems(lib, bad):
 
 def test_batch_rejects_bad_options(lib):
     import paper_2210_15962_gb300 as m
-    for kw in [dict(block_threads=48), dict(block_threads=512), dict(table_factor_x10=5)]:
+    for kw in [dict(block_threads=48), dict(block_threads=512), dict(table_factor_x10=5), dict(walk_mode=3)]:
         with pytest.raises(m.LabsError) as ei:
             m.Batch([(27, 64, 100, 1, 1000)], **kw)
         assert ei.value.status == m.LABS_EINVAL
@@ -210,7 +210,8 @@ def test_batch_rejects_bad_options(lib):
 def test_serve_rejects_bad_config(lib):
     import paper_2210_15962_gb300 as m
     for kw in [dict(max_active=0), dict(max_L=100), dict(max_L=1001), dict(rounds_per_launch=0),
-               dict(block_threads=40), dict(mem_bytes=0), dict(max_walks=0)]:
+               dict(block_threads=40), dict(mem_bytes=0), dict(max_walks=0), dict(walk_mode=3),
+               dict(walk_mode=2, max_walks=8192)]:
         with pytest.raises(m.LabsError) as ei:
             m.Server(**kw)
         assert ei.value.status == m.LABS_EINVAL

@@ -174,3 +174,28 @@ def test_batch_vs_oracle_targets_and_graph(m):
         for _ in range(2):
             b.run()
             check_oracle(budget_only, b.results())
+
+
+def test_batch_warp_mode_vs_oracle_every_class(m):
+    # one walk per warp (the lanes split each walk's flips) in every class,
+    # budget and target problems, against the oracle
+    probs = list(CLASS_PROBS)
+    tgt = target_after_rounds(161, 40, 120, 401, 2)
+    probs.append((161, 40, 120, 401, 10 ** 12, tgt))
+    with m.Batch(probs, walk_mode=2, rounds_per_launch=2) as b:
+        b.run()
+        check_oracle(probs, b.results())
+        for W in {((p[0] - 1) // 2 + 31) // 32 for p in probs}:
+            assert b.shape(W)["warp_per_walk"]
+
+
+def test_batch_autotune_offers_warp_mode(m):
+    # few walks per class: the autotuner times lane and warp mode on the
+    # first launch's tasks; whatever it picks, the results are the oracle's
+    probs = [(301, 64, 300, 501, 64 * 300 * 151), (449, 48, 200, 502, 48 * 200 * 225 * 2)]
+    with m.Batch(probs, autotune=True) as b:
+        b.run()
+        check_oracle(probs, b.results())
+        for W in (5, 7):
+            sh = b.shape(W)
+            assert sh["block_threads"] in (64, 128, 256) and sh["resident_walks"] > 0

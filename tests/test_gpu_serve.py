@@ -193,12 +193,14 @@ def test_probability_target_sets_the_budget(m):
             check(m, (L, w, wl, seed, budget), r)
 
 
-def test_served_results_match_oracle_every_class(m):
+@pytest.mark.parametrize("walk_mode", [0, 1, 2])
+def test_served_results_match_oracle_every_class(m, walk_mode):
     # a mixed submission across the lag-word classes W = 1..5 (L = 61, 121, 161,
     # 223, 301), with budgets over several rounds and one target request; every
-    # result is compared with the oracle's Algorithm 1 + Algorithm 2 directly
+    # result is compared with the oracle's Algorithm 1 + Algorithm 2 directly,
+    # for launches in the mode chosen per launch (0), one walk per lane (1) and
+    # one walk per warp (2)
     import oracle
-    D = lambda L: (L + 1) // 2
     reqs = [
         (61, 40, 160, 301, 40 * 160 * 31 * 3),
         (121, 50, 150, 302, 50 * 150 * 61 * 2),
@@ -208,7 +210,7 @@ def test_served_results_match_oracle_every_class(m):
     ]
     o = oracle.solve(161, [306], 32, 120, 32 * 120 * 81 * 2, threads=8)
     reqs.append((161, 32, 120, 306, 10 ** 12, int(o["best_E"][0])))  # stops within two rounds
-    with m.Server(max_walks=64, rounds_per_launch=2) as sv:
+    with m.Server(max_walks=64, rounds_per_launch=2, walk_mode=walk_mode) as sv:
         tickets = [sv.submit(*p) for p in reqs]
         results = [sv.wait(t) for t in tickets]
     for p, r in zip(reqs, results):
