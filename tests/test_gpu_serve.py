@@ -65,11 +65,12 @@ def test_requests_same_alone_and_mixed(m):
 
 
 def test_requests_arriving_while_others_run(m):
-    # the first request runs six rounds at L=301 (a few hundred ms on its own),
-    # so the others, submitted 10 ms apart, arrive while it is on the GPU
-    first = (301, 256, 1208, 12, 256 * 1208 * 151 * 6)
+    # the first request runs 40 rounds of 2048 walks at L=301 (several hundred
+    # ms on its own), so the others, submitted 10 ms apart, arrive while it is
+    # on the GPU
+    first = (301, 2048, 1208, 12, 2048 * 1208 * 151 * 40)
     reqs = [first] + REQS
-    with m.Server(max_walks=512, rounds_per_launch=1) as sv:
+    with m.Server(max_walks=2048, rounds_per_launch=1) as sv:
         tickets = [sv.submit(*first)]
         for p in REQS:
             time.sleep(0.01)
@@ -77,7 +78,7 @@ def test_requests_arriving_while_others_run(m):
         results = [sv.wait(t) for t in tickets]
     for p, r in zip(reqs, results):
         check(m, p, r)
-    assert results[0]["rounds"] == 6
+    assert results[0]["rounds"] == 40
     # later requests were admitted, and finished, while the first one was running
     assert any(r["t_admit_ns"] < results[0]["t_done_ns"] for r in results[1:])
     assert any(r["t_done_ns"] < results[0]["t_done_ns"] for r in results[1:])
