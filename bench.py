@@ -413,7 +413,21 @@ def measure_serving(args, warmup):
     results = [sv.wait(t, timeout_s=3600) for t in tickets]
     t1 = time.perf_counter()
     st = sv.stats()
+    # capacity: the first requests of the stream all submitted at once, so that
+    # the server is never short of work (throughput is then the server's own,
+    # not the stream's offered load)
+    cap_reqs = reqs[:args.capacity_requests]
+    tc0 = time.perf_counter()
+    cap_t = [sv.submit(p.L, p.walks, p.walk_len, p.seed, p.step_budget, targets[p.L]) for p in cap_reqs]
+    cap_res = [sv.wait(t, timeout_s=3600) for t in cap_t]
+    tc1 = time.perf_counter()
+    stc = sv.stats()
     sv.close()
+    cap_evals = sum(r["evals"] for r in cap_res)
+    cap_busy = (stc["busy_ms"] - st["busy_ms"]) / 1e3
+    cap_needed = sum(popc_needed(p.L, r["evals"], r["plane_steps"]) for p, r in zip(cap_reqs, cap_res))
+    cap_lat = np.array([r["latency_s"] for r in cap_res])
+    same_cap = all(a["best_E"] == b["best_E"] and a["evals"] == b["evals"] for a, b in zip(cap_res, results))
     lat = np.array([r["latency_s"] for r in results])
     qwait = np.array([(r["t_admit_ns"] - r["t_submit_ns"]) / 1e9 for r in results])
     evals = sum(r["evals"] for r in results)
@@ -456,6 +470,15 @@ def measure_serving(args, warmup):
                   "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
                   "same_results": bool(same)},
         "gpu_launches": st["launches"] - st0["launches"],
+        "capacity": {
+            "value": cap_evals / (tc1 - tc0), "unit": "neighbour_evals/s", "requests": len(cap_reqs),
+            "seconds": tc1 - tc0, "device_busy_frac": cap_busy / (tc1 - tc0),
+            "useful_frac": (stc["evals"] - st["evals"]) / max(1, stc["evals_run"] - st["evals_run"]),
+            "latency_s": {"p50": float(np.percentile(cap_lat, 50)), "p99": float(np.percentile(cap_lat, 99))},
+            "same_results_as_stream": bool(same_cap),
+            "roofline": popc_roofline(cap_needed, cap_busy, popc_per_eval=cap_needed / max(1, cap_evals),
+                                      note="useful evaluations only, over the device's busy time"),
+            "note": "the stream's first requests submitted at once (same seeds and targets)"},
     }
 
 
@@ -785,6 +808,7 @@ def main():
     ap.add_argument("--serve-walk-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: lane or warp per walk chosen per launch, 1: lane per walk, 2: warp per walk")
     ap.add_argument("--plain-requests", type=int, default=10)
+    ap.add_argument("--capacity-requests", type=int, default=96)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=64)

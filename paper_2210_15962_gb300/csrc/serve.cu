@@ -92,22 +92,43 @@ Share share_of(int slot, const labs_problem &p, uint32_t k) {
   return s;
 }
 
-// What the scheduler knows of each lag-word class: the lanes (one walk per
-// lane) and warps (one walk per warp) its kernels keep resident, and the
-// evaluations per second one resident warp does in each mode, measured when
-// the server is created.
-struct ClassInfo {
-  int lanes = 0, warps = 0;
-  double rate_lane = 1.0, rate_warp = 0.0;  // per resident warp; 0 = warp mode not offered
+// Evaluations per second of one mode of a class as a function of the warps
+// its tasks occupy: measured at kLevels occupancies (when the server is
+// created) and interpolated linearly between (0, 0) and those points, flat past
+// the last.  Throughput is not proportional to the warps busy: it saturates as
+// the SMs fill, so the choice between modes needs the curve, not one rate.
+constexpr int kLevels = 3;
+struct Curve {
+  double warps[kLevels] = {0, 0, 0}, evals_per_s[kLevels] = {0, 0, 0};
+  double at(double n) const {
+    double x0 = 0, y0 = 0;
+    for (int i = 0; i < kLevels; ++i) {
+      if (n <= warps[i]) return warps[i] > x0 ? y0 + (evals_per_s[i] - y0) * (n - x0) / (warps[i] - x0) : y0;
+      x0 = warps[i];
+      y0 = evals_per_s[i];
+    }
+    return y0;
+  }
 };
 
-// Lane or warp mode for a class in one launch: the one whose resident warps,
-// filled with as many of the launch's tasks as there are, evaluate faster (one
-// walk per lane fills a warp per 32 walks, one walk per warp a warp per walk).
+// What the scheduler knows of each lag-word class: the lanes (one walk per
+// lane) and warps (one walk per warp) its kernels keep resident, and the
+// throughput curve of each mode.
+struct ClassInfo {
+  int lanes = 0, warps = 0;
+  Curve lane, warp;
+  bool warp_offered = false;
+  int forced = 0;  // 1: always lane mode, 2: always warp mode
+};
+
+// Lane or warp mode for a class in one launch: the one whose curve is higher at
+// the warps the launch's tasks occupy (one walk per lane fills a warp per 32
+// walks, one walk per warp a warp per walk).
 bool choose_warp(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) {
-  if (ci.rate_warp <= 0.0) return false;
-  const double lane = (double)std::min<uint64_t>(chunk_tasks, (uint64_t)ci.lanes / 32) * ci.rate_lane;
-  const double warp = (double)std::min<uint64_t>(walk_tasks, (uint64_t)ci.warps) * ci.rate_warp;
+  if (ci.forced) return ci.forced == 2;
+  if (!ci.warp_offered) return false;
+  const double lane = ci.lane.at((double)std::min<uint64_t>(chunk_tasks, (uint64_t)ci.lanes / 32));
+  const double warp = ci.warp.at((double)std::min<uint64_t>(walk_tasks, (uint64_t)ci.warps));
   return warp > lane;
 }
 
@@ -496,12 +517,12 @@ labs_status labs_server::harvest(Launch &l) {
   return LABS_OK;
 }
 
-// Measure, for every class, the evaluations per second of one resident warp
-// in lane mode and in warp mode: one wave of each (as many lanes or warps as
-// stay resident, as far as half the arena holds their tables) on a sample
-// problem, the class's largest L up to max_L with walks of 128 steps, on a
-// round no request uses.  Slot 0 holds the sample problem meanwhile; its
-// tasks count into one record that never completes.
+// Measure, for every class, the throughput curve of lane mode and of warp
+// mode: evaluations per second with 1/8, 1/2 and all of the warps each mode
+// keeps resident busy (as far as half the arena holds their tables), on a
+// sample problem (the class's largest L up to max_L, walks of 128 steps, a
+// round no request uses).  Slot 0 holds the sample problem meanwhile; the
+// sample's tasks count into one record that never completes.
 labs_status labs_server::tune_modes() {
   Launch &l = L[0];
   cudaStream_t s = l.s;
@@ -527,62 +548,72 @@ labs_status labs_server::tune_modes() {
       st = LABS_ECUDA;
       break;
     }
+    cls[ci].warp_offered = warp_allowed;
     for (int mode = 0; mode < (warp_allowed ? 2 : 1) && st == LABS_OK; ++mode) {
       const bool warp = mode == 1;
       const int per_block = warp ? cfg.block_threads / 32 : cfg.block_threads;
-      size_t units = (size_t)(warp ? cls[ci].warps : cls[ci].lanes);
-      const size_t task_bytes = align_up(sizeof(BatchTask) * units);
-      const size_t fit = half_bytes > task_bytes ? (half_bytes - task_bytes) / (words * 8) : 0;
-      units = std::min(units, fit) / per_block * per_block;
-      if (!warp && units < 32) units = 0;
-      if (units == 0) {
-        if (warp) cls[ci].rate_warp = 0.0;
-        continue;
-      }
-      const size_t n_tasks = warp ? units : units / 32;
-      std::vector<BatchTask> tk(n_tasks);
-      for (size_t i = 0; i < n_tasks; ++i) tk[i] = BatchTask{0u, 1000000u, (uint32_t)i, tune_record};
-      BatchKernelParams k{};
-      k.probs = d_probs;
-      k.tasks = reinterpret_cast<const BatchTask *>(l.arena);
-      k.n_tasks = (uint32_t)n_tasks;
-      k.task_next = l.task_next;
-      k.pool = reinterpret_cast<uint64_t *>(l.arena + task_bytes);
-      k.pool_words = words;
-      k.rec = rec;
-      k.ps = ps;
-      k.mul_one = 1u;
-      k.mul_two = 2u;
-      k.mul_four = 4u;
-      k.mul_h31 = 0x80000000u;
-      k.mul_h30 = 0x40000000u;
-      k.err = d_err;
-      float ms = 0.f;
-      unsigned long long evals = 0;
-      if (cudaMemcpyAsync(l.arena, tk.data(), sizeof(BatchTask) * n_tasks, cudaMemcpyHostToDevice, s) !=
-          cudaSuccess)
-        st = LABS_ECUDA;
-      for (int rep = 0; rep < 2 && st == LABS_OK; ++rep) {  // the first run warms up
-        const cudaError_t e =
-            (cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int), s) != cudaSuccess ||
-             cudaMemsetAsync(rec.left + tune_record, 0xFF, sizeof(uint32_t), s) != cudaSuccess ||
-             cudaMemsetAsync(rec.evals + tune_record, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-             cudaEventRecord(e0, s) != cudaSuccess)
-                ? cudaErrorUnknown
-                : (warp ? launch_batch_warp(W, cfg.block_threads, k, s, (int)(units / per_block))
-                        : launch_batch(W, cfg.block_threads, k, s, nullptr, (int)(units / per_block)));
-        if (e != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      const int tables_per_warp = warp ? 1 : 32;
+      const size_t resident_warps = (size_t)(warp ? cls[ci].warps : cls[ci].lanes / 32);
+      Curve &cv = warp ? cls[ci].warp : cls[ci].lane;
+      for (int lv = 0; lv < kLevels && st == LABS_OK; ++lv) {
+        const size_t want = lv == 0 ? resident_warps / 8 : (lv == 1 ? resident_warps / 2 : resident_warps);
+        size_t units = std::max<size_t>(1, want) * tables_per_warp;  // tables: lanes or warps
+        const size_t task_bytes = align_up(sizeof(BatchTask) * units);
+        const size_t fit = half_bytes > task_bytes ? (half_bytes - task_bytes) / (words * 8) : 0;
+        units = std::min(units, fit);
+        units = (units + per_block - 1) / per_block * per_block;
+        if (units > fit) units -= per_block;
+        const size_t n_tasks = units / tables_per_warp;
+        if (n_tasks == 0) {
+          if (warp) cls[ci].warp_offered = false;
+          break;
+        }
+        std::vector<BatchTask> tk(n_tasks);
+        for (size_t i = 0; i < n_tasks; ++i) tk[i] = BatchTask{0u, 1000000u, (uint32_t)i, tune_record};
+        BatchKernelParams k{};
+        k.probs = d_probs;
+        k.tasks = reinterpret_cast<const BatchTask *>(l.arena);
+        k.n_tasks = (uint32_t)n_tasks;
+        k.task_next = l.task_next;
+        k.pool = reinterpret_cast<uint64_t *>(l.arena + task_bytes);
+        k.pool_words = words;
+        k.rec = rec;
+        k.ps = ps;
+        k.mul_one = 1u;
+        k.mul_two = 2u;
+        k.mul_four = 4u;
+        k.mul_h31 = 0x80000000u;
+        k.mul_h30 = 0x40000000u;
+        k.err = d_err;
+        float ms = 0.f;
+        unsigned long long evals = 0;
+        if (cudaMemcpyAsync(l.arena, tk.data(), sizeof(BatchTask) * n_tasks, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
           st = LABS_ECUDA;
+        for (int rep = 0; rep < 2 && st == LABS_OK; ++rep) {  // the first run warms up
+          const cudaError_t e =
+              (cudaMemsetAsync(l.task_next, 0, sizeof(unsigned int), s) != cudaSuccess ||
+               cudaMemsetAsync(rec.left + tune_record, 0xFF, sizeof(uint32_t), s) != cudaSuccess ||
+               cudaMemsetAsync(rec.evals + tune_record, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+               cudaEventRecord(e0, s) != cudaSuccess)
+                  ? cudaErrorUnknown
+                  : (warp ? launch_batch_warp(W, cfg.block_threads, k, s, (int)(units / per_block))
+                          : launch_batch(W, cfg.block_threads, k, s, nullptr, (int)(units / per_block)));
+          if (e != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            st = LABS_ECUDA;
+        }
+        if (st == LABS_OK &&
+            cudaMemcpy(&evals, rec.evals + tune_record, sizeof(evals), cudaMemcpyDeviceToHost) != cudaSuccess)
+          st = LABS_ECUDA;
+        if (st != LABS_OK) break;
+        cv.warps[lv] = (double)n_tasks;
+        cv.evals_per_s[lv] = (double)evals / (std::max(ms, 1e-3f) / 1e3);
+        for (int j = lv + 1; j < kLevels; ++j) {  // until measured, flat
+          cv.warps[j] = cv.warps[lv];
+          cv.evals_per_s[j] = cv.evals_per_s[lv];
+        }
       }
-      if (st == LABS_OK &&
-          cudaMemcpy(&evals, rec.evals + tune_record, sizeof(evals), cudaMemcpyDeviceToHost) != cudaSuccess)
-        st = LABS_ECUDA;
-      if (st != LABS_OK) break;
-      const double warps_used = warp ? (double)units : (double)units / 32.0;
-      const double rate = (double)evals / (std::max(ms, 1e-3f) / 1e3) / warps_used;
-      if (warp) cls[ci].rate_warp = rate;
-      else cls[ci].rate_lane = rate;
     }
   }
   cudaEventDestroy(e0);
@@ -859,11 +890,7 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LABS_ECUDA);
   labs_status tst = sv->tune_modes();
   if (tst != LABS_OK) return fail(tst);
-  if (cfg.walk_mode == 2)  // every launch in warp mode
-    for (auto &ci : sv->cls) {
-      ci.rate_warp = 1.0;
-      ci.rate_lane = 0.0;
-    }
+  for (auto &ci : sv->cls) ci.forced = cfg.walk_mode;
   try {
     sv->th = std::thread([sv]() { sv->loop(); });
   } catch (...) {
