@@ -808,7 +808,7 @@ def main():
     ap.add_argument("--serve-walk-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: lane or warp per walk chosen per launch, 1: lane per walk, 2: warp per walk")
     ap.add_argument("--plain-requests", type=int, default=10)
-    ap.add_argument("--capacity-requests", type=int, default=96)
+    ap.add_argument("--capacity-requests", type=int, default=160)
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)
     ap.add_argument("--plain-instances", type=int, default=64)
