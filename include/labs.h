@@ -205,8 +205,9 @@ typedef struct labs_batch_opts {
                                 captured as a CUDA graph on the first run and replayed after */
   int32_t autotune;          /* 1: pick per class, by timing candidates on a sample of its first
                                 launch (cached per process): one walk per lane with 64, 128 or
-                                256 walks per CTA and 1.5 or 3 table slots per pivot, or one
-                                walk per warp (offered while every problem has <= 4096 walks) */
+                                256 walks per CTA, 1.5 or 3 table slots per pivot and the scan's
+                                flip loop unrolled once or twice, or one walk per warp (offered
+                                while every problem has <= 4096 walks) */
   int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
   int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 15 or autotuned */
   int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
@@ -233,10 +234,11 @@ labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t *best_seq, 
  * neighbourhood scans used, summed over the walk steps of its rounds. */
 labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, uint64_t *plane_steps);
 /* Launch shape chosen for class W (any output may be NULL): threads per CTA,
- * table factor x 10, walks resident at once, and 1 if the class runs one walk
- * per warp (the lanes split each walk's flips) or 0 for one walk per lane. */
+ * table factor x 10, walks resident at once, 1 if the class runs one walk per
+ * warp (the lanes split each walk's flips) or 0 for one walk per lane, and how
+ * many times the scan's flip loop is unrolled (1 or 2). */
 labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads, int32_t *table_factor_x10,
-                             int32_t *resident_walks, int32_t *warp_per_walk);
+                             int32_t *resident_walks, int32_t *warp_per_walk, int32_t *unroll);
 labs_status labs_batch_destroy(labs_batch *b);
 
 /* ---------------------------------------------------------------- serving

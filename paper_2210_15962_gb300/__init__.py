@@ -175,7 +175,7 @@ _EXPORTS = {
                                            ctypes.c_void_p, ctypes.c_void_p]),
     "labs_batch_plane_steps": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "labs_batch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                          ctypes.c_void_p, ctypes.c_void_p]),
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "labs_batch_destroy": (ctypes.c_int32, [ctypes.c_void_p]),
     "labs_serve_cfg_init": (None, [ctypes.POINTER(labs_serve_cfg)]),
     "labs_serve_create": (ctypes.c_int32, [ctypes.POINTER(labs_serve_cfg), ctypes.POINTER(ctypes.c_void_p)]),
@@ -486,11 +486,11 @@ class Batch:
         return [self.result(i) for i in range(len(self.problems))]
 
     def shape(self, W: int) -> dict:
-        v = np.zeros(4, dtype=np.int32)
-        _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3]), _ptr(v[3:4])),
-               "labs_batch_shape")
+        v = np.zeros(5, dtype=np.int32)
+        _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3]), _ptr(v[3:4]),
+                                       _ptr(v[4:5])), "labs_batch_shape")
         return {"block_threads": int(v[0]), "table_factor_x10": int(v[1]), "resident_walks": int(v[2]),
-                "warp_per_walk": bool(v[3])}
+                "warp_per_walk": bool(v[3]), "unroll": int(v[4])}
 
     def close(self):
         if getattr(self, "_h", None):

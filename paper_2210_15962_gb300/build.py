@@ -19,19 +19,20 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["walk_kernels.cu", "walk_class.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_api.cu",
-           "serve.cu", "model.cu"]
+SOURCES = ["walk_kernels.cu", "walk_class.cu", "labs_api.cu", "noalloc.cu", "batch_kernels.cu", "batch_class.cu",
+           "batch_api.cu", "serve.cu", "model.cu"]
+PER_CLASS = ("walk_class.cu", "batch_class.cu")  # compiled once per lag-word class W
 HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))  # every header of the sources
-LAG_WORD_CLASSES = range(1, 9)  # walk_class.cu is compiled once per class W (m <= 32 W lags)
+LAG_WORD_CLASSES = range(1, 9)  # the per-class sources are compiled once per class W (m <= 32 W lags)
 
 
 def _units():
     """(source, object, extra flags) of every translation unit."""
     units = []
     for src in SOURCES:
-        if src == "walk_class.cu":
+        if src in PER_CLASS:
             for w in LAG_WORD_CLASSES:
-                units.append((src, "walk_class_w%d.o" % w, ["-DPSAW_W=%d" % w]))
+                units.append((src, src.replace(".cu", "_w%d.o" % w), ["-DPSAW_W=%d" % w]))
         else:
             units.append((src, src.replace(".cu", ".o"), []))
     return units

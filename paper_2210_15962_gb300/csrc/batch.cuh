@@ -110,13 +110,18 @@ inline double batch_task_cost(int L, int walk_len) {
 
 // Reset the listed records for their new rounds (before any of their tasks run).
 cudaError_t launch_issue_records(const RecordInit *list, int n, const RoundRecords &rec, cudaStream_t s);
+// Kernel variants of a class: one walk per lane, the same with the scan's
+// flip loop unrolled twice, and one walk per warp.
+constexpr int kBatchLane = 0, kBatchWarp = 1, kBatchLaneUnroll2 = 2;
+
 // Launch the persistent kernel for lag-word class W with `block` threads per
 // block and as many blocks as fit on the device at once, at most max_blocks
-// when max_blocks > 0 (the pool must hold grid * block lanes).
+// when max_blocks > 0 (the pool must hold grid * block lanes); unroll 1 or 2
+// unrolls the scan's flip loop.
 cudaError_t launch_batch(int W, int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out,
-                         int max_blocks = 0);
+                         int max_blocks = 0, int unroll = 1);
 // Lanes the persistent kernel of class W keeps resident with `block` threads per block.
-int batch_resident_lanes(int W, int block);
+int batch_resident_lanes(int W, int block, int unroll = 1);
 // Warp mode (one walk per warp, tasks of one walk; the pool holds one table
 // per warp of the grid): the launch, and the warps it keeps resident.
 cudaError_t launch_batch_warp(int W, int block, const BatchKernelParams &p, cudaStream_t s, int max_blocks = 0);

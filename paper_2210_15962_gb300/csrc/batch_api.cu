@@ -43,6 +43,7 @@ cudaError_t dalloc(T **p, size_t n) {
 struct ClassPlan {
   int W = 0;
   bool warp = false;  // warp mode: one walk per warp, tasks of one walk
+  int unroll = 1;     // lane mode: the scan's flip loop unrolled 1 or 2 times
   int block = 128;
   int factor_x10 = kTableFactorX10;
   std::vector<int> probs;  // problem indices of this class
@@ -64,6 +65,7 @@ std::mutex g_tune_mu;
 struct Tuned {
   int block, factor_x10;
   bool warp;
+  int unroll;
 };
 std::map<TuneKey, Tuned> g_tuned;
 
@@ -213,7 +215,7 @@ labs_status build_pools(labs_batch *b) {
     }
     c.pool_words = (words + 1) / 2 * 2;
     // a table per lane, or per warp in warp mode
-    c.resident = c.warp ? batch_resident_warps(c.W, c.block) : batch_resident_lanes(c.W, c.block);
+    c.resident = c.warp ? batch_resident_warps(c.W, c.block) : batch_resident_lanes(c.W, c.block, c.unroll);
     if (c.resident <= 0) return LABS_ECUDA;
     BCU(dalloc(&c.pool, (size_t)c.resident * c.pool_words));
   }
@@ -311,7 +313,7 @@ labs_status enqueue_launch(labs_batch *b, std::vector<std::pair<cudaEvent_t, cud
     BCU(cudaStreamWaitEvent(x, b->fork, 0));
     if (c.n_tasks) {
       if (c.warp) BCU(launch_batch_warp(c.W, c.block, kernel_params(b, c, (int)ci), x));
-      else BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr));
+      else BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr, 0, c.unroll));
       ++*launches;
     }
     BCU(cudaEventRecord(b->cs_done[ci], x));
@@ -342,9 +344,9 @@ uint32_t first_launch_rounds(const labs_batch *b, const labs_problem &p) {
 }
 
 // Time candidate launch shapes of one class: lane mode (one walk per lane,
-// tasks of 32 walks) with walks per CTA in {64, 128, 256} and table capacity
-// in {1.5, 3} x pivots, and warp mode (one walk per warp) with 128 or 256
-// threads per CTA.  Each candidate runs the class's first launch as far as one
+// tasks of 32 walks) with walks per CTA in {64, 128, 256}, table capacity in
+// {1.5, 3} x pivots and the scan's flip loop unrolled once or twice, and warp
+// mode (one walk per warp) with 128 or 256 threads per CTA.  Each candidate runs the class's first launch as far as one
 // wave of its resident lanes (or warps) reaches, on rounds no solve uses, with
 // walks shortened to at most 256 steps; the one with the lowest time per
 // neighbour evaluation wins (cached per process).  The sample's tasks all
@@ -366,20 +368,22 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       c.block = it->second.block;
       c.factor_x10 = it->second.factor_x10;
       c.warp = it->second.warp;
+      c.unroll = it->second.unroll;
       return LABS_OK;
     }
   }
   struct Cand {
     bool warp;
-    int block, factor;
+    int block, factor, unroll;
   };
   std::vector<Cand> cands;
-  for (int fct : {15, 30})
-    for (int blk : {64, 128, 256}) cands.push_back({false, blk, fct});
+  for (int u : {1, 2})
+    for (int fct : {15, 30})
+      for (int blk : {64, 128, 256}) cands.push_back({false, blk, fct, u});
   if (b->warp_allowed)
-    for (int blk : {128, 256}) cands.push_back({true, blk, kTableFactorX10});
+    for (int blk : {128, 256}) cands.push_back({true, blk, kTableFactorX10, 1});
   double best_ns = 1e300;
-  Cand best = {c.warp, c.block, c.factor_x10};
+  Cand best = {c.warp, c.block, c.factor_x10, c.unroll};
   std::vector<labs_problem> saved = b->pr;
   for (int i : c.probs) b->pr[i].walk_len = std::min(b->pr[i].walk_len, 256);
   auto restore = [&](labs_status st) {
@@ -390,6 +394,7 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
     c.warp = cd.warp;
     c.block = cd.block;
     c.factor_x10 = cd.factor;
+    c.unroll = cd.unroll;
     labs_status st = build_pools(b);
     if (st != LABS_OK) return restore(st);
     // the first launch's tasks, as far as one wave reaches
@@ -422,7 +427,7 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       cudaMemsetAsync(b->rec.evals + b->tune_record, 0, sizeof(unsigned long long), b->s);
       cudaEventRecord(e0, b->s);
       if (cd.warp) launch_batch_warp(c.W, c.block, kernel_params(b, c, ci), b->s);
-      else launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr);
+      else launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr, 0, c.unroll);
       cudaEventRecord(e1, b->s);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&ms, e0, e1);
@@ -441,9 +446,10 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   c.warp = best.warp;
   c.block = best.block;
   c.factor_x10 = best.factor;
+  c.unroll = best.unroll;
   c.n_tasks = 0;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[key] = Tuned{best.block, best.factor, best.warp};
+  g_tuned[key] = Tuned{best.block, best.factor, best.warp, best.unroll};
   return LABS_OK;
 }
 
@@ -805,7 +811,7 @@ extern "C" labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, ui
 
 extern "C" labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads,
                                         int32_t *table_factor_x10, int32_t *resident_walks,
-                                        int32_t *warp_per_walk) {
+                                        int32_t *warp_per_walk, int32_t *unroll) {
   if (!b) return LABS_EINVAL;
   for (auto &c : b->cls) {
     if (c.W != W) continue;
@@ -813,6 +819,7 @@ extern "C" labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t 
     if (table_factor_x10) *table_factor_x10 = c.factor_x10;
     if (resident_walks) *resident_walks = c.resident;
     if (warp_per_walk) *warp_per_walk = c.warp ? 1 : 0;
+    if (unroll) *unroll = c.warp ? 1 : c.unroll;
     return LABS_OK;
   }
   return LABS_ENOTFOUND;

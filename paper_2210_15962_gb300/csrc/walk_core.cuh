@@ -568,7 +568,7 @@ LABS_HD uint32_t flip_key(const WalkState<W, T> &st, const Muls &mu, const uint3
 // pair lag c - a on one side of t throughout: t >= tpair for all of them or
 // for none): packed keys into top, skipping t == tprev; windows B, F and the
 // bit ba of position a advanced one lag per flip.
-template <int W, int T, int TP, int K, bool RESCAN, int NX, int NY>
+template <int W, int T, int TP, int K, bool RESCAN, int NX, int NY, int U = 1>
 LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
                         int t0, int t1, int tprev, int tpair, uint32_t floor, uint32_t (&B)[W], uint32_t (&F)[W],
                         uint32_t &ba, uint32_t (&top)[K]) {
@@ -582,6 +582,9 @@ LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls
   uint32_t kbase = key_base<TP>(2 * t0 + q, n, nxy0);
   uint32_t kdiff = key_diff<TP>(n, nxy0);
   const uint32_t *row = rows + (size_t)t0 * MT::kRowWords;
+  // U > 1 unrolls the flip loop, giving the scheduler U flips' independent
+  // popcount chains at once (a launch-shape knob of the batch autotuner)
+#pragma unroll(U)
   for (int t = t0; t < t1; ++t, row += MT::kRowWords) {
     uint32_t Vx[W], Vye[W];
     load_mask_row<W>(row, Vx, Vye);
@@ -617,20 +620,20 @@ constexpr int kPatternMinWords = 2;
 // lags.  The patterns compiled are nx = 0 .. ceil(W/2) (t <= 16 W) and
 // ny = max(1, W/2) .. W (the y side keeps at least half the class); any other
 // pattern decides per flip.
-template <int W, int T, int TP, int K, bool RESCAN, int NX = 0, int NY = (W / 2 > 1 ? W / 2 : 1)>
+template <int W, int T, int TP, int K, bool RESCAN, int NX = 0, int NY = (W / 2 > 1 ? W / 2 : 1), int U = 1>
 LABS_HD void scan_run(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *rows, int q,
                       int nx, int ny, int t0, int t1, int tprev, int tpair, uint32_t floor, uint32_t (&B)[W],
                       uint32_t (&F)[W], uint32_t &ba, uint32_t (&top)[K]) {
   if constexpr (NX > (W + 1) / 2) {
-    scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
+    scan_flips<W, T, TP, K, RESCAN, -1, -1, U>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
   } else if constexpr (NY > W) {
-    scan_run<W, T, TP, K, RESCAN, NX + 1, (W / 2 > 1 ? W / 2 : 1)>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair,
+    scan_run<W, T, TP, K, RESCAN, NX + 1, (W / 2 > 1 ? W / 2 : 1), U>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair,
                                                                    floor, B, F, ba, top);
   } else {
     if (nx == NX && ny == NY)
-      scan_flips<W, T, TP, K, RESCAN, NX, NY>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
+      scan_flips<W, T, TP, K, RESCAN, NX, NY, U>(st, g, mu, rows, q, t0, t1, tprev, tpair, floor, B, F, ba, top);
     else
-      scan_run<W, T, TP, K, RESCAN, NX, NY + 1>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair, floor, B, F, ba,
+      scan_run<W, T, TP, K, RESCAN, NX, NY + 1, U>(st, g, mu, rows, q, nx, ny, t0, t1, tprev, tpair, floor, B, F, ba,
                                                 top);
   }
 }
@@ -642,7 +645,7 @@ LABS_HD void scan_run(const WalkState<W, T> &st, const Geometry &g, const Muls &
 // masks come from the table mt (MaskTable<W>, filled for this geometry).  In
 // narrow classes the flips of a class split into runs where the number of
 // words with x lags, ceil(t/32), and with y lags, ceil((Nq-1-t)/32), is fixed.
-template <int W, int T, int TP, int K, bool RESCAN, int PMAX>
+template <int W, int T, int TP, int K, bool RESCAN, int PMAX, int U = 1>
 LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt,
                                 int jprev, uint32_t floor, uint32_t (&top)[K]) {
   using MT = MaskTable<W>;
@@ -680,13 +683,14 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
         if (ny > 0 && Nq - 1 - 32 * (ny - 1) < t1) t1 = Nq - 1 - 32 * (ny - 1);  // ... or of ny
         if (SteppedKey<W>::value && t < tpair && tpair < t1) t1 = tpair;  // ... or of the pair lag's side
         if (t1 > nloop) t1 = nloop;
-        scan_run<W, T, TP, K, RESCAN>(st, g, mu, rows, q, nx, ny, t, t1, tprev, tpair, floor, B, F, ba, top);
+        scan_run<W, T, TP, K, RESCAN, 0, (W / 2 > 1 ? W / 2 : 1), U>(st, g, mu, rows, q, nx, ny, t, t1, tprev, tpair,
+                                                                    floor, B, F, ba, top);
         t = t1;
       }
     } else {
       for (int t = 0; t < nloop;) {  // with SteppedKey two runs, split where the pair lag changes side
         const int t1 = (SteppedKey<W>::value && t < tpair && tpair < nloop) ? tpair : nloop;
-        scan_flips<W, T, TP, K, RESCAN, -1, -1>(st, g, mu, rows, q, t, t1, tprev, tpair, floor, B, F, ba, top);
+        scan_flips<W, T, TP, K, RESCAN, -1, -1, U>(st, g, mu, rows, q, t, t1, tprev, tpair, floor, B, F, ba, top);
         t = t1;
       }
     }
@@ -705,21 +709,21 @@ LABS_HD void eval_neighbours_tp(const WalkState<W, T> &st, const Geometry &g, co
 
 // Dispatch on the plane count (the caller may pass any tp >= planes_needed);
 // floor > 0 selects the rescan variant (candidates at or above floor only).
-template <int W, int T, int K, bool RESCAN, int PMAX>
+template <int W, int T, int K, bool RESCAN, int PMAX, int U = 1>
 LABS_HD void eval_neighbours_r(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
                                int jprev, uint32_t floor, uint32_t (&top)[K]) {
   constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
-  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
-  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
-  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
-  else eval_neighbours_tp<W, T, T3, K, RESCAN, PMAX>(st, g, mu, mt, jprev, floor, top);
+  if (tp >= T) eval_neighbours_tp<W, T, T, K, RESCAN, PMAX, U>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 1) eval_neighbours_tp<W, T, T - 1, K, RESCAN, PMAX, U>(st, g, mu, mt, jprev, floor, top);
+  else if (tp == T - 2) eval_neighbours_tp<W, T, T - 2, K, RESCAN, PMAX, U>(st, g, mu, mt, jprev, floor, top);
+  else eval_neighbours_tp<W, T, T3, K, RESCAN, PMAX, U>(st, g, mu, mt, jprev, floor, top);
 }
 
-template <int W, int T, int K, int PMAX>
+template <int W, int T, int K, int PMAX, int U = 1>
 LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const Muls &mu, const uint32_t *mt, int tp,
                              int jprev, uint32_t floor, uint32_t (&top)[K]) {
-  if (floor == 0) eval_neighbours_r<W, T, K, false, PMAX>(st, g, mu, mt, tp, jprev, 0u, top);
-  else eval_neighbours_r<W, T, K, true, PMAX>(st, g, mu, mt, tp, jprev, floor, top);
+  if (floor == 0) eval_neighbours_r<W, T, K, false, PMAX, U>(st, g, mu, mt, tp, jprev, 0u, top);
+  else eval_neighbours_r<W, T, K, true, PMAX, U>(st, g, mu, mt, tp, jprev, floor, top);
 }
 
 LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }

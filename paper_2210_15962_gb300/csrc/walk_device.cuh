@@ -54,8 +54,8 @@ __device__ __forceinline__ void clear_tables_warp(uint64_t *my_table, size_t wor
 // two lag words up, the best pivot's step and key, written only when E
 // improves, are parked in shared memory (word k at bst[k * stride]) so that
 // they hold no registers during the scan (one-word walks measured faster
-// keeping them in registers).
-template <int W, int T, int K, int PMAX>
+// keeping them in registers).  U unrolls the scan's flip loop.
+template <int W, int T, int K, int PMAX, int U = 1>
 __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, const uint32_t *mt, uint32_t *bst,
                                          int stride, uint64_t seed, uint32_t walk, uint32_t round, int walk_len,
                                          uint64_t *table, uint32_t cap, int kw64, int recheck_every, int32_t *trace,
@@ -92,7 +92,7 @@ __device__ __forceinline__ void run_walk(const Geometry &g, const Muls &mu, cons
     plane_sum += (uint32_t)tp;
     while (need) {
       uint32_t top[K];
-      eval_neighbours<W, T, K, PMAX>(st, g, mu, mt, tp, jprev, floor, top);
+      eval_neighbours<W, T, K, PMAX, U>(st, g, mu, mt, tp, jprev, floor, top);
 #pragma unroll
       for (int r = 0; r < K; ++r) {
         if (need) {
