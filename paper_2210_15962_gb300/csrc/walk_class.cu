@@ -186,11 +186,19 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_warp(const WalkP
   atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
 }
 
+// resident blocks the warp variant is compiled for: as the lane variant, except
+// the two-word class, whose warp step needs a few more registers than 7 blocks
+// per SM leave (it spilled)
+template <int W>
+struct MinBlocksWarp {
+  static constexpr int value = W == 2 ? 6 : MinBlocksFor<W>::value;
+};
+
 template <int W>
 static cudaError_t launch_w_warp(const WalkParams &p, cudaStream_t s) {
   constexpr int T = PlanesFor<W>::value;
   const unsigned blocks = (p.g_count + kWalkBlock / 32 - 1) / (kWalkBlock / 32);
-  walk_kernel_warp<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
+  walk_kernel_warp<W, T, kTopK, MinBlocksWarp<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
 

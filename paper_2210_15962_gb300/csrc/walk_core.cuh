@@ -729,26 +729,17 @@ LABS_HD void eval_neighbours(const WalkState<W, T> &st, const Geometry &g, const
 LABS_HD int key_flip(uint32_t k) { return (int)(k & 0xFFu); }
 LABS_HD int key_delta(uint32_t k) { return (int)(k >> 8) - kDeltaBias; }
 
-// Move to the neighbour of flip a (Algorithm 2, the move): C_{2i} -= 4 u_i
-// on the digit planes by a bit-sliced add, E += delta, and flip the bits.
+// The move's update of the digit planes (Algorithm 2, the move): C_{2i} -= 4
+// u_i for the flip a with position bit ba, its y window F (class bits t+1, t+2,
+// ...) and x window X (class bits t-1, t-2, ...; only the lags it holds are
+// read), as a bit-sliced add of 2 d, d = -u / 2 in {-2..2}; E += delta.
 template <int W, int T>
-LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta) {
-  constexpr int NS = W + 1;
+LABS_HD void move_planes(WalkState<W, T> &st, const Geometry &g, int a, int delta, uint32_t ba,
+                         const uint32_t (&F)[W], const uint32_t (&X)[W]) {
   const int q = a & 1, t = a >> 1;
   const int Nq = g.D - q;  // class size N_q without indexing g.N
   const bool centre = (a == g.c);
-  uint32_t cq[NS];  // the flip's parity class, selected without dynamic indexing
-  const uint32_t mq = sel_mask(q != 0);
-#pragma unroll
-  for (int w = 0; w < NS; ++w) cq[w] = (st.cls[1][w] & mq) | (st.cls[0][w] & ~mq);
-  const uint32_t ba = get_bit(cq, t);
   const uint32_t bm = 0u - ba;
-  // Y window: class bits t+1 .. ; X window: class bits t-1, t-2, .. via a full bit reversal
-  uint32_t F[W], R[NS], X[W];
-  shr_dyn(F, cq, t + 1);
-#pragma unroll
-  for (int w = 0; w < NS; ++w) R[w] = brev32(cq[NS - 1 - w]);
-  shr_dyn(X, R, 32 * NS - t);
   const int i0 = g.c - a;  // pair lag excluded from the y side
 #pragma unroll
   for (int w = 0; w < W; ++w) {
@@ -776,14 +767,47 @@ LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta
     }
   }
   st.E += delta;
+}
+
+// The move's bit flips: position a and its mirror (Eq. 2) in the parity
+// classes, bit a of the key.
+template <int W, int T>
+LABS_HD void move_bits(WalkState<W, T> &st, const Geometry &g, int a) {
+  constexpr int NS = W + 1;
+  const int q = a & 1, t = a >> 1;
+  const uint32_t mq = sel_mask(q != 0);
+  uint32_t cq[NS];  // the flip's parity class, selected without dynamic indexing
+#pragma unroll
+  for (int w = 0; w < NS; ++w) cq[w] = (st.cls[1][w] & mq) | (st.cls[0][w] & ~mq);
   xor_bit(cq, t, 1u);
-  if (!centre) xor_bit(cq, (g.L - 1 - a - q) >> 1, 1u);
+  if (a != g.c) xor_bit(cq, (g.L - 1 - a - q) >> 1, 1u);
 #pragma unroll
   for (int w = 0; w < NS; ++w) {
     st.cls[0][w] = (st.cls[0][w] & mq) | (cq[w] & ~mq);
     st.cls[1][w] = (cq[w] & mq) | (st.cls[1][w] & ~mq);
   }
   xor_bit(st.key, a, 1u);
+}
+
+// Move to the neighbour of flip a (Algorithm 2, the move): cut the flip's
+// windows from its parity class, update the planes and E, flip the bits.
+template <int W, int T>
+LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta) {
+  constexpr int NS = W + 1;
+  const int q = a & 1, t = a >> 1;
+  uint32_t cq[NS];  // the flip's parity class, selected without dynamic indexing
+  const uint32_t mq = sel_mask(q != 0);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) cq[w] = (st.cls[1][w] & mq) | (st.cls[0][w] & ~mq);
+  const uint32_t ba = get_bit(cq, t);
+  // Y window: class bits t+1 .. ; X window: class bits t-1, t-2, .. via a full bit reversal
+  uint32_t F[W], R[NS], X[W];
+  shr_dyn(F, cq, t + 1);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) R[w] = brev32(cq[NS - 1 - w]);
+  shr_dyn(X, R, 32 * NS - t);
+  move_planes(st, g, a, delta, ba, F, X);
+  move_bits(st, g, a);
 }
 
 // ------------------------------------------------------ visited hash table

@@ -45,6 +45,43 @@ __device__ __forceinline__ void warp_publish_classes(const WalkState<W, T> &st, 
   __syncwarp();
 }
 
+// The move of flip a on every lane's copy of the walk: its windows cut from
+// the shared mirrors (as the scan cuts them), the planes' update and the bit
+// flips in registers; then lane 0 flips the same bits in the mirrors (the
+// position, its Eq. 2 mirror, and their places in the reversal).
+template <int W, int T>
+__device__ __forceinline__ void warp_apply_move(WalkState<W, T> &st, const Geometry &g, uint32_t *sm, int lane,
+                                                int a, int delta) {
+  constexpr int NS = W + 1, CW = WarpWalkSmem<W>::kClsWords;
+  const int q = a & 1, t = a >> 1;
+  const uint32_t *C = sm + q * CW;
+  const uint32_t *R = sm + (2 + q) * CW;
+  uint32_t F[W], X[W];
+  const int of = (t + 1) >> 5, sf = (t + 1) & 31;
+#pragma unroll
+  for (int w = 0; w < W; ++w) F[w] = fshr(C[of + w], C[of + w + 1], (uint32_t)sf);
+  const int u = 32 * NS - t, ob = u >> 5, sb = u & 31;
+#pragma unroll
+  for (int w = 0; w < W; ++w) X[w] = w < x_words<W>() ? fshr(R[ob + w], R[ob + w + 1], (uint32_t)sb) : 0u;
+  const uint32_t ba = (C[t >> 5] >> (t & 31)) & 1u;
+  move_planes(st, g, a, delta, ba, F, X);
+  move_bits(st, g, a);
+  __syncwarp();  // every lane has read the mirrors before lane 0 changes them
+  if (lane == 0) {
+    uint32_t *Cw = sm + q * CW;
+    uint32_t *Rw = sm + (2 + q) * CW;
+    const int r = 32 * NS - 1 - t;
+    Cw[t >> 5] ^= 1u << (t & 31);
+    Rw[r >> 5] ^= 1u << (r & 31);
+    if (a != g.c) {
+      const int k = (g.L - 1 - a - q) >> 1, rk = 32 * NS - 1 - k;
+      Cw[k >> 5] ^= 1u << (k & 31);
+      Rw[rk >> 5] ^= 1u << (rk & 31);
+    }
+  }
+  __syncwarp();
+}
+
 // The K smallest keys of the flips this lane owns in class q (t = lane,
 // lane + 32, ...), as eval_neighbours_tp computes them for one flip each.
 template <int W, int T, int TP, int K, bool RESCAN>
@@ -216,12 +253,12 @@ __device__ void run_walk_warp(const Geometry &g, const Muls &mu, const uint32_t 
       stuck = 1;
       break;
     }
-    apply_move(st, g, chosen, cdelta);
+    warp_apply_move(st, g, sm, lane, chosen, cdelta);
     if (lane == 0) {
       table_store(table, cslot, kw64, st.key, g.D);
       if (trace) trace[step - 1] = chosen;
     }
-    warp_publish_classes(st, sm, lane);
+    __syncwarp();
     jprev = chosen;
     moves = step;
     if (st.E < bestE) {
