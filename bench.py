@@ -3,15 +3,25 @@ L=121 (D=61), 131072 concurrent walks of 8192 steps, a budget of 1e11
 neighbour evaluations (two whole rounds), Philox seed 1 (rank r uses seed 1+r).
 
 One "step" = one whole solve (every round until the budget) through the C ABI.
-  value  : evaluations/s with inputs resident in HBM (device buffers, workspace
-           preallocated), CUDA events on the launching stream, max over ranks;
-  e2e    : the same metric through labs_walks with HOST buffers (seed upload,
-           workspace allocation and result download inside the timed region);
-  roofline: the walk kernel's bit-sliced core against the int32 ALU-pipe peak;
+  value   : evaluations/s with inputs resident in HBM (device buffers, workspace
+            preallocated), CUDA events on the launching stream, max over ranks;
+  e2e     : the same metric through labs_walks with HOST buffers (seed upload,
+            workspace allocation and result download inside the timed region);
+  roofline: the walk kernel against the popcount (XU) pipe: the population
+            counts the bit-sliced evaluation needs per neighbour (popc_needed)
+            over the kernel's per-launch time, against 152 SMs x 16 x 2070 MHz;
+            the int32 ALU-pipe unit beside it;
+  batched : the 64-instance workload through the persistent batch path, against
+            one labs_walks per instance, with its own roofline;
+  serving : a Poisson request stream through the server (p50/p99 latency),
+            against one labs_walks per request, and the server's capacity with
+            the stream's first requests submitted at once;
   cpu_baseline: the CPU oracle on a bounded sample of the same walks.
 
 `--impl reference` times the CPU oracle (the reference arm of this project)
 on the same workload and prints the same JSON line with "impl": "reference".
+Other workloads (--workload batched, serving, large, table1, walklen,
+variants) print their own lines.
 
 Multi-GPU (torchrun): each rank solves its own independent problem (weak
 scaling, no data-path collective); the host barrier and a max-reduction of the
