@@ -170,7 +170,7 @@ int ilog2(uint64_t x) {
   return r;
 }
 
-constexpr int32_t kSampleSteps = 64;  // steps per walk of a variant-choice sample round
+constexpr int32_t kSampleSteps = 256;  // steps per walk of a variant-choice sample round
 
 }  // namespace
 }  // namespace psaw
