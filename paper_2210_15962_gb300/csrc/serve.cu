@@ -111,25 +111,40 @@ struct Curve {
   }
 };
 
-// What the scheduler knows of each lag-word class: the lanes (one walk per
-// lane) and warps (one walk per warp) its kernels keep resident, and the
-// throughput curve of each mode.
+// The kernel variants a launch can run a class with (batch.cuh): one walk per
+// lane, the same with the scan's flip loop unrolled twice, one walk per warp.
+constexpr int kModes = 3;
+constexpr int kModeVariant[kModes] = {kBatchLane, kBatchLaneUnroll2, kBatchWarp};
+inline bool mode_is_warp(int m) { return kModeVariant[m] == kBatchWarp; }
+
+// What the scheduler knows of each lag-word class: per mode, the tables (lanes,
+// or warps in warp mode) its kernel keeps resident, whether it is offered, and
+// its throughput curve.
 struct ClassInfo {
-  int lanes = 0, warps = 0;
-  Curve lane, warp;
-  bool warp_offered = false;
-  int forced = 0;  // 1: always lane mode, 2: always warp mode
+  int resident[kModes] = {0, 0, 0};
+  bool offered[kModes] = {false, false, false};
+  Curve curve[kModes];
+  int forced = 0;  // 1: always one walk per lane, 2: always one walk per warp
 };
 
-// Lane or warp mode for a class in one launch: the one whose curve is higher at
-// the warps the launch's tasks occupy (one walk per lane fills a warp per 32
+// The mode for a class in one launch: the one whose curve is highest at the
+// warps the launch's tasks occupy (one walk per lane fills a warp per 32
 // walks, one walk per warp a warp per walk).
-bool choose_warp(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) {
-  if (ci.forced) return ci.forced == 2;
-  if (!ci.warp_offered) return false;
-  const double lane = ci.lane.at((double)std::min<uint64_t>(chunk_tasks, (uint64_t)ci.lanes / 32));
-  const double warp = ci.warp.at((double)std::min<uint64_t>(walk_tasks, (uint64_t)ci.warps));
-  return warp > lane;
+int choose_mode(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) {
+  if (ci.forced == 2) return 2;
+  int best = 0;
+  double best_rate = -1.0;
+  for (int m = 0; m < kModes; ++m) {
+    if (!ci.offered[m] || (ci.forced == 1 && mode_is_warp(m))) continue;
+    const uint64_t warps = mode_is_warp(m) ? std::min<uint64_t>(walk_tasks, (uint64_t)ci.resident[m])
+                                           : std::min<uint64_t>(chunk_tasks, (uint64_t)ci.resident[m] / 32);
+    const double rate = ci.curve[m].at((double)warps);
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = m;
+    }
+  }
+  return best;
 }
 
 // Layout of one launch inside its half of the arena (byte offsets; sizes
@@ -145,7 +160,7 @@ struct Carve {
   std::vector<size_t> pool_words;  // per class, per lane
   std::vector<int> lanes;          // per class: lanes, or warps in warp mode, of the grid
   std::vector<uint32_t> n_tasks;   // per class
-  std::vector<uint8_t> warp;       // per class: warp mode
+  std::vector<uint8_t> mode;       // per class: the kernel variant (kModeVariant)
   uint32_t n_problems = 0, n_issue = 0;
   size_t total = 0;
 };
@@ -158,7 +173,7 @@ Carve carve_launch(const std::vector<Share> &sh, const std::vector<ClassInfo> &c
   c.pool_words.assign(nc, 0);
   c.lanes.assign(nc, 0);
   c.n_tasks.assign(nc, 0);
-  c.warp.assign(nc, 0);
+  c.mode.assign(nc, 0);
   c.n_problems = (uint32_t)sh.size();
   std::vector<uint64_t> chunk_tasks(nc, 0), walk_tasks(nc, 0);
   for (const Share &s : sh) {
@@ -168,8 +183,8 @@ Carve carve_launch(const std::vector<Share> &sh, const std::vector<ClassInfo> &c
     if (s.k) c.pool_words[s.W - 1] = std::max(c.pool_words[s.W - 1], s.table_words);
   }
   for (size_t w = 0; w < nc; ++w) {
-    c.warp[w] = choose_warp(cls[w], chunk_tasks[w], walk_tasks[w]) ? 1 : 0;
-    c.n_tasks[w] = (uint32_t)(c.warp[w] ? walk_tasks[w] : chunk_tasks[w]);
+    c.mode[w] = (uint8_t)choose_mode(cls[w], chunk_tasks[w], walk_tasks[w]);
+    c.n_tasks[w] = (uint32_t)(mode_is_warp(c.mode[w]) ? walk_tasks[w] : chunk_tasks[w]);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -185,10 +200,11 @@ Carve carve_launch(const std::vector<Share> &sh, const std::vector<ClassInfo> &c
   for (size_t w = 0; w < nc; ++w) {
     if (!c.n_tasks[w]) continue;
     // a table per lane (32 per task) or per warp (one per task), whole CTAs, at most the resident ones
-    const size_t per_block = c.warp[w] ? (size_t)block / 32 : (size_t)block;
-    const size_t units = c.warp[w] ? (size_t)c.n_tasks[w] : (size_t)c.n_tasks[w] * 32;
+    const bool warp = mode_is_warp(c.mode[w]);
+    const size_t per_block = warp ? (size_t)block / 32 : (size_t)block;
+    const size_t units = warp ? (size_t)c.n_tasks[w] : (size_t)c.n_tasks[w] * 32;
     const size_t want = (units + per_block - 1) / per_block * per_block;
-    c.lanes[w] = (int)std::min<size_t>(want, (size_t)(c.warp[w] ? cls[w].warps : cls[w].lanes));
+    c.lanes[w] = (int)std::min<size_t>(want, (size_t)cls[w].resident[c.mode[w]]);
     c.pool[w] = take(sizeof(uint64_t) * c.pool_words[w] * (size_t)c.lanes[w]);
   }
   c.total = off;
@@ -360,7 +376,7 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
     plist[i] = s.slot;
     const double cost = batch_task_cost(s.L, s.walk_len);
     const bool layered = target[s.slot] >= 0;
-    const bool warp = cv.warp[s.W - 1] != 0;
+    const bool warp = mode_is_warp(cv.mode[s.W - 1]);
     const uint32_t units = warp ? (uint32_t)s.walks : s.chunks;  // tasks per round: walks, or chunks of 32
     for (uint32_t j = 0; j < s.k; ++j) {
       const uint32_t round = first_round[s.slot] + j;
@@ -425,11 +441,12 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
     k.mul_h30 = 0x40000000u;
     k.err = d_err;
     // the pool holds cv.lanes[ci] tables: never more blocks than that
+    const int variant = kModeVariant[cv.mode[ci]];
     const cudaError_t e =
-        cv.warp[ci] ? launch_batch_warp((int)ci + 1, cfg.block_threads, k, l.cs[ci],
-                                        cv.lanes[ci] / (cfg.block_threads / 32))
-                    : launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr,
-                                   cv.lanes[ci] / cfg.block_threads);
+        variant == kBatchWarp
+            ? launch_batch_warp((int)ci + 1, cfg.block_threads, k, l.cs[ci], cv.lanes[ci] / (cfg.block_threads / 32))
+            : launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr, cv.lanes[ci] / cfg.block_threads,
+                           variant == kBatchLaneUnroll2 ? 2 : 1);
     if (e != cudaSuccess) return LABS_ECUDA;
     if (cudaEventRecord(l.cs_done[ci], l.cs[ci]) != cudaSuccess ||
         cudaStreamWaitEvent(s, l.cs_done[ci], 0) != cudaSuccess)
@@ -517,8 +534,9 @@ labs_status labs_server::harvest(Launch &l) {
   return LABS_OK;
 }
 
-// Measure, for every class, the throughput curve of lane mode and of warp
-// mode: evaluations per second with 1/8, 1/2 and all of the warps each mode
+// Measure, for every class, the throughput curve of each kernel mode (one
+// walk per lane, the same unrolled, one walk per warp): evaluations per
+// second with 1/8, 1/2 and all of the warps each mode
 // keeps resident busy (as far as half the arena holds their tables), on a
 // sample problem (the class's largest L up to max_L, walks of 128 steps, a
 // round no request uses).  Slot 0 holds the sample problem meanwhile; the
@@ -537,7 +555,7 @@ labs_status labs_server::tune_modes() {
     pr.L = L;
     pr.W = W;
     pr.walk_len = std::min(8 * D, 128);
-    pr.walks = std::max(cls[ci].lanes, cls[ci].warps);
+    pr.walks = std::max({cls[ci].resident[0], cls[ci].resident[1], cls[ci].resident[2]});
     pr.cap = visited_table_cap(pr.walk_len);
     pr.kw64 = key_words64(D);
     pr.seed = 0x5EEDu;
@@ -548,13 +566,14 @@ labs_status labs_server::tune_modes() {
       st = LABS_ECUDA;
       break;
     }
-    cls[ci].warp_offered = warp_allowed;
-    for (int mode = 0; mode < (warp_allowed ? 2 : 1) && st == LABS_OK; ++mode) {
-      const bool warp = mode == 1;
+    for (int mode = 0; mode < kModes && st == LABS_OK; ++mode) {
+      const bool warp = mode_is_warp(mode);
+      cls[ci].offered[mode] = !warp || warp_allowed;
+      if (!cls[ci].offered[mode]) continue;
       const int per_block = warp ? cfg.block_threads / 32 : cfg.block_threads;
       const int tables_per_warp = warp ? 1 : 32;
-      const size_t resident_warps = (size_t)(warp ? cls[ci].warps : cls[ci].lanes / 32);
-      Curve &cv = warp ? cls[ci].warp : cls[ci].lane;
+      const size_t resident_warps = (size_t)cls[ci].resident[mode] / tables_per_warp;
+      Curve &cv = cls[ci].curve[mode];
       for (int lv = 0; lv < kLevels && st == LABS_OK; ++lv) {
         const size_t want = lv == 0 ? resident_warps / 8 : (lv == 1 ? resident_warps / 2 : resident_warps);
         size_t units = std::max<size_t>(1, want) * tables_per_warp;  // tables: lanes or warps
@@ -565,7 +584,7 @@ labs_status labs_server::tune_modes() {
         if (units > fit) units -= per_block;
         const size_t n_tasks = units / tables_per_warp;
         if (n_tasks == 0) {
-          if (warp) cls[ci].warp_offered = false;
+          if (lv == 0) cls[ci].offered[mode] = false;
           break;
         }
         std::vector<BatchTask> tk(n_tasks);
@@ -598,7 +617,8 @@ labs_status labs_server::tune_modes() {
                cudaEventRecord(e0, s) != cudaSuccess)
                   ? cudaErrorUnknown
                   : (warp ? launch_batch_warp(W, cfg.block_threads, k, s, (int)(units / per_block))
-                          : launch_batch(W, cfg.block_threads, k, s, nullptr, (int)(units / per_block)));
+                          : launch_batch(W, cfg.block_threads, k, s, nullptr, (int)(units / per_block),
+                                         kModeVariant[mode] == kBatchLaneUnroll2 ? 2 : 1));
           if (e != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
               cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
             st = LABS_ECUDA;
@@ -758,11 +778,12 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   size_t tune_slots = 1;
   for (int W = 1; W <= Wmax; ++W) {
     ClassInfo ci;
-    ci.lanes = batch_resident_lanes(W, cfg.block_threads);
-    ci.warps = batch_resident_warps(W, cfg.block_threads);
-    if (ci.lanes <= 0 || ci.warps <= 0) return fail(LABS_ECUDA);
+    ci.resident[0] = batch_resident_lanes(W, cfg.block_threads, 1);
+    ci.resident[1] = batch_resident_lanes(W, cfg.block_threads, 2);
+    ci.resident[2] = batch_resident_warps(W, cfg.block_threads);
+    if (ci.resident[0] <= 0 || ci.resident[1] <= 0 || ci.resident[2] <= 0) return fail(LABS_ECUDA);
     sv->cls.push_back(ci);
-    tune_slots = std::max<size_t>(tune_slots, std::max(ci.lanes / 32, ci.warps));
+    tune_slots = std::max<size_t>(tune_slots, std::max({ci.resident[0] / 32, ci.resident[1] / 32, ci.resident[2]}));
   }
   sv->ring = ring;
   sv->slot_ticket.assign(n, 0);

@@ -582,10 +582,7 @@ LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls
   uint32_t kbase = key_base<TP>(2 * t0 + q, n, nxy0);
   uint32_t kdiff = key_diff<TP>(n, nxy0);
   const uint32_t *row = rows + (size_t)t0 * MT::kRowWords;
-  // U > 1 unrolls the flip loop, giving the scheduler U flips' independent
-  // popcount chains at once (a launch-shape knob of the batch autotuner)
-#pragma unroll(U)
-  for (int t = t0; t < t1; ++t, row += MT::kRowWords) {
+  auto one_flip = [&](int t) {
     uint32_t Vx[W], Vye[W];
     load_mask_row<W>(row, Vx, Vye);
     if constexpr (!SteppedKey<W>::value) {
@@ -607,6 +604,14 @@ LABS_HD void scan_flips(const WalkState<W, T> &st, const Geometry &g, const Muls
 #pragma unroll
     for (int w = 0; w < W; ++w) F[w] = imadhi(F[w], mu.h31, (w + 1 < W) ? imad(F[w + 1], mu.h31, 0u) : 0u);
     ba = ba_next;
+  };
+  if constexpr (U == 1) {
+    for (int t = t0; t < t1; ++t, row += MT::kRowWords) one_flip(t);
+  } else {
+    // U > 1 unrolls the flip loop, giving the scheduler U flips' independent
+    // popcount chains at once (a launch-shape knob of the batch autotuner)
+#pragma unroll(U)
+    for (int t = t0; t < t1; ++t, row += MT::kRowWords) one_flip(t);
   }
 }
 
@@ -807,7 +812,15 @@ LABS_HD void apply_move(WalkState<W, T> &st, const Geometry &g, int a, int delta
   for (int w = 0; w < NS; ++w) R[w] = brev32(cq[NS - 1 - w]);
   shr_dyn(X, R, 32 * NS - t);
   move_planes(st, g, a, delta, ba, F, X);
-  move_bits(st, g, a);
+  // the bit flips on the class already selected (move_bits without its selection)
+  xor_bit(cq, t, 1u);
+  if (a != g.c) xor_bit(cq, (g.L - 1 - a - q) >> 1, 1u);
+#pragma unroll
+  for (int w = 0; w < NS; ++w) {
+    st.cls[0][w] = (st.cls[0][w] & mq) | (cq[w] & ~mq);
+    st.cls[1][w] = (cq[w] & mq) | (st.cls[1][w] & ~mq);
+  }
+  xor_bit(st.key, a, 1u);
 }
 
 // ------------------------------------------------------ visited hash table
