@@ -54,10 +54,10 @@ SM_MAX_MHZ = 2070.0
 
 
 # DRAM traffic of one walk-kernel launch of the default workload, from an ncu
-# capture of the walk kernel on 107008 walks x 1024 steps (18.68 GB, scaled by
+# capture of the walk kernel on 107008 walks x 1024 steps (18.73 GB, scaled by
 # walk-steps to 131072 x 8192), valid only for the kernel sources it was
 # captured from.
-TRAFFIC = {"sources_sha256_prefix": "6dd5a5d1b544e5e9", "bytes_per_launch": 18.69e9 * (131072 * 8192) / (107008 * 1024)}
+TRAFFIC = {"sources_sha256_prefix": "bc6ce0618c877d45", "bytes_per_launch": 18.726e9 * (131072 * 8192) / (107008 * 1024)}
 WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_incr.cuh", "walk_class.cu", "walk_kernels.cuh"]
 
 
@@ -472,6 +472,8 @@ def measure_serving(args, warmup):
         "evals_run": st["evals_run"] - st0["evals_run"],
         "useful_frac": (st["evals"] - st0["evals"]) / max(1, st["evals_run"] - st0["evals_run"]),
         "mem_peak_bytes": st["mem_peak"],
+        "class_kernels": {"lane": stc["lane_launches"], "lane_unrolled": stc["lane_unrolled_launches"],
+                          "warp": stc["warp_launches"]},
         "roofline": popc_roofline(needed, busy_s, kernel="batch_kernel<W> (all classes, two launches in flight)",
                                   popc_per_eval=needed / max(1, evals),
                                   note="useful evaluations only (rounds past a request's stop not counted), "

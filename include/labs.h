@@ -304,6 +304,9 @@ typedef struct labs_serve_stats {
                                 rounds up to each stop) */
   uint64_t mem_peak;         /* largest share of the arena one launch used (<= mem_bytes / 2) */
   uint64_t fixed_bytes;      /* device bytes of the per-slot state, outside the arena */
+  uint64_t lane_launches;          /* class kernels launched with one walk per lane, */
+  uint64_t lane_unrolled_launches; /* the same with the scan's flip loop unrolled twice, */
+  uint64_t warp_launches;          /* and with one walk per warp */
 } labs_serve_stats;
 
 typedef struct labs_server labs_server; /* opaque */

@@ -144,6 +144,9 @@ class labs_serve_stats(ctypes.Structure):
         ("evals_run", ctypes.c_uint64),
         ("mem_peak", ctypes.c_uint64),
         ("fixed_bytes", ctypes.c_uint64),
+        ("lane_launches", ctypes.c_uint64),
+        ("lane_unrolled_launches", ctypes.c_uint64),
+        ("warp_launches", ctypes.c_uint64),
     ]
 
 

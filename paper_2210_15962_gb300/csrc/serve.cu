@@ -129,7 +129,11 @@ struct ClassInfo {
 
 // The mode for a class in one launch: the one whose curve is highest at the
 // warps the launch's tasks occupy (one walk per lane fills a warp per 32
-// walks, one walk per warp a warp per walk).
+// walks, one walk per warp a warp per walk).  Another mode replaces the plain
+// lane mode only when its curve is kModeMargin higher: the curves come from
+// short samples, and a choice within their noise would trade away a sure
+// result for a guess.
+constexpr double kModeMargin = 1.05;
 int choose_mode(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) {
   if (ci.forced == 2) return 2;
   int best = 0;
@@ -138,7 +142,7 @@ int choose_mode(const ClassInfo &ci, uint64_t chunk_tasks, uint64_t walk_tasks) 
     if (!ci.offered[m] || (ci.forced == 1 && mode_is_warp(m))) continue;
     const uint64_t warps = mode_is_warp(m) ? std::min<uint64_t>(walk_tasks, (uint64_t)ci.resident[m])
                                            : std::min<uint64_t>(chunk_tasks, (uint64_t)ci.resident[m] / 32);
-    const double rate = ci.curve[m].at((double)warps);
+    const double rate = ci.curve[m].at((double)warps) * (m == 0 ? kModeMargin : 1.0);
     if (rate > best_rate) {
       best_rate = rate;
       best = m;
@@ -255,6 +259,7 @@ struct labs_server {
   // counters
   uint64_t n_submitted = 0, n_completed = 0, evals_done = 0, evals_run = 0;
   uint64_t launches = 0, walk_launches = 0;
+  uint64_t mode_launches[kModes] = {0, 0, 0};  // class kernels launched in each mode
   double busy_ms = 0.0, busy_end_ms = 0.0;
   // device state
   void *fixed = nullptr;
@@ -448,6 +453,7 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
             : launch_batch((int)ci + 1, cfg.block_threads, k, l.cs[ci], nullptr, cv.lanes[ci] / cfg.block_threads,
                            variant == kBatchLaneUnroll2 ? 2 : 1);
     if (e != cudaSuccess) return LABS_ECUDA;
+    ++mode_launches[cv.mode[ci]];
     if (cudaEventRecord(l.cs_done[ci], l.cs[ci]) != cudaSuccess ||
         cudaStreamWaitEvent(s, l.cs_done[ci], 0) != cudaSuccess)
       return LABS_ECUDA;
@@ -1021,6 +1027,9 @@ extern "C" labs_status labs_serve_get_stats(labs_server *sv, labs_serve_stats *o
   out->busy_ms = sv->busy_ms;
   out->mem_used = sv->mem_used;
   out->mem_peak = sv->mem_peak;
+  out->lane_launches = sv->mode_launches[0];
+  out->lane_unrolled_launches = sv->mode_launches[1];
+  out->warp_launches = sv->mode_launches[2];
   out->fixed_bytes = sv->fixed_bytes;
   out->status = sv->failed;
   return LABS_OK;
