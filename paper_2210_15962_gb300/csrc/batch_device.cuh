@@ -13,9 +13,10 @@ constexpr int kBatchMaxThreads = 256;
 
 // Widest lag-word class whose scan runs through pattern-specialised loops: the
 // classes' persistent kernels run side by side, so their code shares the SMs'
-// instruction caches and is kept smaller than in the per-round kernel (with
-// classes up to 4 words specialised the batched workload measured 13% slower).
-constexpr int kBatchPatternMaxWords = 2;
+// instruction caches and is kept smaller than in the per-round kernel
+// (measured on the serving mix, one class at a time: specialised loops gain
+// 12% at three words and lose 20% at four).
+constexpr int kBatchPatternMaxWords = 3;
 
 // register budget per thread of each class: the smallest that does not spill
 // (the task loop keeps more state live than the per-round kernel).  Tighter

@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel(const WalkParams
   if (p.trace_flips && gw - p.trace_begin < p.trace_count)
     trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
   WalkOut<NS> o;
-  run_walk<W, T, K, kWalkPatternMaxWords>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock, p.seeds[prob], walk,
-                                          p.round, p.walk_len, table, p.cap, p.kw64, p.recheck_every, trace, p.err, o);
+  run_walk<W, T, K, kWalkPatternMaxWords, ScanUnroll<W>::value>(g, mu, mask_rows, best_park + threadIdx.x, kWalkBlock,
+                                                                p.seeds[prob], walk, p.round, p.walk_len, table, p.cap,
+                                                                p.kw64, p.recheck_every, trace, p.err, o);
   p.w_bestE[gw] = o.bestE;
   p.w_moves[gw] = o.moves;
   p.w_stuck[gw] = o.stuck;
@@ -186,12 +187,11 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_warp(const WalkP
   atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
 }
 
-// resident blocks the warp variant is compiled for: as the lane variant, except
-// the two-word class, whose warp step needs a few more registers than 7 blocks
-// per SM leave (it spilled)
+// resident blocks the warp variant is compiled for: 6 at two words (7 spilled),
+// otherwise as the full-space kernel
 template <int W>
 struct MinBlocksWarp {
-  static constexpr int value = W == 2 ? 6 : MinBlocksFor<W>::value;
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 6 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
 };
 
 template <int W>
@@ -242,7 +242,7 @@ template <int W>
 static cudaError_t launch_full(const WalkParams &p, cudaStream_t s) {
   constexpr int T = FullPlanesFor<W>::value;
   const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
-  full_walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
+  full_walk_kernel<W, T, kTopK, MinBlocksFull<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -15,11 +15,31 @@ struct PlanesFor {
   static constexpr int value = W == 1 ? 6 : (W == 2 ? 7 : (W <= 4 ? 8 : 9));
 };
 
-// resident blocks of kWalkBlock walks per SM each class is compiled for
-// (the register budget per thread is 65536 / (128 * MINB))
+// resident blocks of kWalkBlock walks per SM each class of the one-walk-per-
+// lane kernel is compiled for (the register budget per thread is
+// 65536 / (128 * MINB)); seven and eight words measured 8% and 4% faster with
+// 3 blocks (168 registers) than with 2, while 5 blocks at three words and 4 at
+// five lost 7% and 4%
 template <int W>
 struct MinBlocksFor {
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : 3));
+};
+
+// The same for the full-space kernel (full_core.cuh), whose scan keeps more
+// state per word.
+template <int W>
+struct MinBlocksFull {
   static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
+};
+
+// Flips of the scan's loop unrolled per iteration in the one-walk-per-lane
+// kernel: two at five to seven words (independent popcount chains for the
+// few resident warps: +4%, +3% and +2% at L=301, 383, 449), one elsewhere
+// (two lost 1.5% at two words, 27-30% at three and four, where the
+// registers do not hold a second flip's window, and 1% at eight)
+template <int W>
+struct ScanUnroll {
+  static constexpr int value = (W >= 5 && W <= 7) ? 2 : 1;
 };
 
 template <int NS>
