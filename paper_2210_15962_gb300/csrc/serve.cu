@@ -49,7 +49,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr int kSeqStride = 512;  // bytes per slot of the expanded best sequences (>= LABS_L_MAX)
 constexpr int kDepth = 2;        // launches in flight
-constexpr int kRingFactor = 3;   // round records per slot = kRingFactor x rounds_per_launch
+constexpr int kRingFactor = 6;   // round records per slot = kRingFactor x rounds_per_launch
 // Warp mode keeps a key slot per walk in every round record: it is offered
 // while max_walks is at most this.
 constexpr int kWarpModeMaxWalks = 4096;
@@ -313,16 +313,46 @@ size_t labs_server::admitted_carve(const Request *extra) {
 }
 
 // Rounds the next launch gives a request: what its budget still needs beyond
-// the rounds in flight, at most rounds_per_launch, and never so far ahead of
-// the finalized rounds that the ring would reuse a record still in use.
-static uint32_t rounds_to_issue(const Request &r, int rounds_per_launch, uint32_t ring) {
+// the rounds in flight, at most `most`, and never so far ahead of the
+// finalized rounds that the ring would reuse a record still in use.
+static uint32_t rounds_to_issue(const Request &r, int64_t most, uint32_t ring) {
   const uint64_t fr = (uint64_t)r.p.walks * (uint64_t)r.p.walk_len * (uint64_t)((r.p.L + 1) / 2);
   const uint64_t rem = r.p.step_budget > r.evals ? r.p.step_budget - r.evals : 0;
   const int64_t need = (int64_t)std::max<uint64_t>(1, (rem + fr - 1) / fr);
   const int64_t in_flight = (int64_t)r.issued - (int64_t)r.rounds;
   const int64_t room = (int64_t)r.rounds + (int64_t)ring - (int64_t)r.issued;
-  const int64_t k = std::min<int64_t>({need - in_flight, room, (int64_t)rounds_per_launch});
+  const int64_t k = std::min<int64_t>({need - in_flight, room, most});
   return k > 0 ? (uint32_t)k : 0u;
+}
+
+// Rounds per request of one launch.  Each gets rounds_per_launch (or what it
+// still needs); when those leave SMs idle (few requests, or the last ones of
+// a burst), requests get further rounds, one at a time in turn, until the
+// launch's warps reach what the device keeps resident of its widest-fitting
+// class or no request can take more.  The further rounds run on lanes that
+// would otherwise idle: a request that stops before them wastes nothing that
+// another could have used, and one that needs them finishes in fewer
+// launches.  Targets still stop every request at the same round.
+static std::vector<uint32_t> plan_rounds(const std::vector<const Request *> &rs, int rounds_per_launch,
+                                         uint32_t ring, const std::vector<ClassInfo> &cls) {
+  std::vector<uint32_t> k(rs.size());
+  uint64_t warps = 0, fill = 0;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    k[i] = rounds_to_issue(*rs[i], rounds_per_launch, ring);
+    const uint64_t chunks = (uint64_t)((rs[i]->p.walks + 31) / 32);
+    warps += k[i] * chunks;
+    fill = std::max<uint64_t>(fill, (uint64_t)cls[rs[i]->W - 1].resident[0] / 32);
+  }
+  for (bool grew = true; grew && warps < fill;) {
+    grew = false;
+    for (size_t i = 0; i < rs.size() && warps < fill; ++i) {
+      if (k[i] == 0 || rounds_to_issue(*rs[i], (int64_t)k[i] + 1, ring) <= k[i]) continue;
+      ++k[i];
+      warps += (uint64_t)((rs[i]->p.walks + 31) / 32);
+      grew = true;
+    }
+  }
+  return k;
 }
 
 // Plan and queue one launch on l's streams: the new requests' slot state, the
@@ -353,10 +383,21 @@ labs_status labs_server::enqueue(Launch &l, const std::vector<int> &admitted) {
       adm_target.push_back(r.p.target_E);
     }
     l.slots.clear();
+    std::vector<const Request *> listed;
+    for (int sl = 0; sl < cfg.max_active; ++sl)
+      if (slot_ticket[sl] && !slot_draining[sl]) listed.push_back(reqs[slot_ticket[sl]].get());
+    std::vector<uint32_t> ks = plan_rounds(listed, rpl, ring, cls);
+    {  // the further rounds only while the launch stays inside its half of the arena
+      std::vector<Share> trial;
+      for (size_t i = 0; i < listed.size(); ++i) trial.push_back(share_of(listed[i]->slot, listed[i]->p, ks[i]));
+      if (carve_launch(trial, cls, cfg.block_threads).total > half_bytes)
+        for (size_t i = 0; i < listed.size(); ++i) ks[i] = rounds_to_issue(*listed[i], rpl, ring);
+    }
+    size_t li = 0;
     for (int sl = 0; sl < cfg.max_active; ++sl) {
       if (!slot_ticket[sl] || slot_draining[sl]) continue;
       Request &r = *reqs[slot_ticket[sl]];
-      const uint32_t k = rounds_to_issue(r, rpl, ring);
+      const uint32_t k = ks[li++];
       sh.push_back(share_of(sl, r.p, k));
       target[sl] = r.p.target_E;
       first_round[sl] = r.issued;

@@ -12,14 +12,13 @@
 
 namespace psaw {
 
-// Longest L of the four-word class that runs with 3 resident blocks per SM.
-constexpr int kW4FewerBlocksMaxL = 233;
-
 // Widest lag-word class whose scan runs through loops specialised for the
-// pattern of active word sides.  Wider classes measured 1.3-2.4x slower with
-// specialised runs (by both sides' word counts, or by the non-empty words
-// only) than with one loop that keeps every word two-sided.
-constexpr int kWalkPatternMaxWords = 4;
+// pattern of active word sides.  Wider classes measured slower with
+// specialised runs than with one loop that keeps every word two-sided: four
+// words 9% at L=223 and 40% at L=255 (with the flip loop unrolled twice and 4
+// blocks per SM, 24% and 68% faster than the specialised runs with 3 blocks),
+// five to eight words 1.3-2.4x.
+constexpr int kWalkPatternMaxWords = 3;
 
 // One thread = one walk (Algorithm 2 with one lane in place of one block).
 // The warp zeroes the visited tables of its live lanes, then every lane runs
@@ -129,15 +128,6 @@ template <int W>
 static cudaError_t launch_w(const WalkParams &p, cudaStream_t s) {
   constexpr int T = PlanesFor<W>::value;
   const unsigned blocks = (p.g_count + kWalkBlock - 1) / kWalkBlock;
-  if constexpr (W == 4) {
-    // four-word classes: the shorter lengths run faster with 3 blocks per SM
-    // (170 registers), the longer with 4 (measured over two full waves each:
-    // L=199 +7%, 223 +5% with 3; L=245 +2%, 257 +14% with 4)
-    if (p.L <= kW4FewerBlocksMaxL) {
-      walk_kernel<W, T, kTopK, 3><<<blocks, kWalkBlock, 0, s>>>(p);
-      return cudaGetLastError();
-    }
-  }
   walk_kernel<W, T, kTopK, MinBlocksFor<W>::value><<<blocks, kWalkBlock, 0, s>>>(p);
   return cudaGetLastError();
 }

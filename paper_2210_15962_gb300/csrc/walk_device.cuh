@@ -33,13 +33,13 @@ struct MinBlocksFull {
 };
 
 // Flips of the scan's loop unrolled per iteration in the one-walk-per-lane
-// kernel: two at five to seven words (independent popcount chains for the
-// few resident warps: +4%, +3% and +2% at L=301, 383, 449), one elsewhere
-// (two lost 1.5% at two words, 27-30% at three and four, where the
+// kernel: two at four to seven words (independent popcount chains for the
+// few resident warps: +3% at L=223, +4%, +3% and +2% at L=301, 383, 449),
+// one elsewhere (two lost 1.5% at two words, 30% at three, where the
 // registers do not hold a second flip's window, and 1% at eight)
 template <int W>
 struct ScanUnroll {
-  static constexpr int value = (W >= 5 && W <= 7) ? 2 : 1;
+  static constexpr int value = (W >= 4 && W <= 7) ? 2 : 1;
 };
 
 template <int NS>
