@@ -814,8 +814,8 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--serve-budget", type=int, default=10 ** 10)
     ap.add_argument("--target-budget", type=int, default=2 * 10 ** 9)
-    ap.add_argument("--max-active", type=int, default=128)
-    ap.add_argument("--mem-gib", type=int, default=16)
+    ap.add_argument("--max-active", type=int, default=256)
+    ap.add_argument("--mem-gib", type=int, default=64)
     ap.add_argument("--rounds-per-launch", type=int, default=4)
     ap.add_argument("--serve-walk-mode", type=int, default=0, choices=[0, 1, 2],
                     help="0: lane or warp per walk chosen per launch, 1: lane per walk, 2: warp per walk")

@@ -209,7 +209,7 @@ typedef struct labs_batch_opts {
                                 flip loop unrolled once or twice, or one walk per warp (offered
                                 while every problem has <= 4096 walks) */
   int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
-  int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 15 or autotuned */
+  int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 30 or autotuned */
   int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
   int32_t walk_mode;         /* 0: one walk per lane, or what autotune picks; 1: one walk per lane;
                                 2: one walk per warp in every class (every problem <= 4096 walks,
@@ -365,7 +365,7 @@ labs_status labs_serve_destroy(labs_server *s);
  * serialised by the caller.
  * Returns LABS_OK, LABS_EINVAL (bad L, sizes or NULL outputs), LABS_ENOMEM
  * if the round's scratch (about n_walks * (slots * 8 * ceil((D+1)/64) + 52)
- * bytes, slots = the power of two >= 1.5 * (walk_len + 1), at least 64)
+ * bytes, slots = the power of two >= 3 * (walk_len + 1), at least 64)
  * exceeds LABS_NOALLOC_SCRATCH_BYTES, or LABS_ECUDA. */
 labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t round, int32_t n_walks, int32_t walk_len,
                                    int64_t *walk_best_E, int8_t *walk_best_seq, int32_t *walk_moves,

@@ -84,6 +84,10 @@ inline __device__ bool finalize_round(const RoundRecords &rec, const ProblemStat
 // update and the finalizer's unlock are each followed by a full fence before
 // each reads the other's word).  A record is the next round's only if it holds
 // that round (records are reused round after round), read before its count.
+// `done` is read again under the lock: a thread that saw the problem running
+// may take the lock right after the round that stopped it was finalized (the
+// stopping finalizer writes `done` before it unlocks), and must not add the
+// next round.
 inline __device__ void try_finalize(const RoundRecords &rec, const ProblemState &ps, int p) {
   for (;;) {
     if (load_volatile(ps.done + p)) return;
@@ -97,6 +101,10 @@ inline __device__ void try_finalize(const RoundRecords &rec, const ProblemState 
     if (load_volatile(rec.left + j) != 0u) return;  // round r not complete yet
     if (atomicCAS(ps.fin + p, st, st | 1u) != st) continue;
     __threadfence();
+    if (load_volatile(ps.done + p)) {  // stopped by the round before r
+      atomicExch(ps.fin + p, st);
+      return;
+    }
     const bool stop = finalize_round(rec, ps, p, r);
     __threadfence();
     atomicExch(ps.fin + p, (r + 1u) << 1);

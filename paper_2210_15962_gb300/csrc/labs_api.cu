@@ -30,7 +30,7 @@ bool valid_space_L(int32_t space, int32_t L) { return space == kSpaceFull ? vali
 int key_bits(int32_t space, int32_t L) { return space == kSpaceFull ? L : (L + 1) / 2; }
 int space_lag_words(int32_t space, int32_t L) { return space == kSpaceFull ? full_lag_words(L) : lag_words(L); }
 
-// visited-table slots: a power of two >= 1.5 x the pivots of a walk
+// visited-table slots: a power of two >= 3 x the pivots of a walk
 uint32_t table_cap(int32_t walk_len) { return visited_table_cap(walk_len); }
 
 // A bump allocator over one device block.

@@ -199,3 +199,23 @@ def test_batch_autotune_offers_warp_mode(m):
         for W in (5, 7):
             sh = b.shape(W)
             assert sh["block_threads"] in (64, 128, 256) and sh["resident_walks"] > 0
+
+
+def test_batch_rounds_after_a_stop_are_never_counted(m):
+    # every problem reaches its target in its first round while 16 of its
+    # rounds are issued in the launch: whatever order the chunks finish in
+    # around the stopping round's finalization, the later rounds add neither
+    # evaluations nor rounds (Algorithm 1), in lane and in warp mode
+    probs = []
+    for i in range(48):
+        L = (61, 121, 161)[i % 3]
+        walks, wl, seed = 64, 120, 800 + i
+        probs.append((L, walks, wl, seed, 10 ** 12, target_after_rounds(L, walks, wl, seed, 1)))
+    for mode in (1, 2):
+        with m.Batch(probs, rounds_per_launch=16, walk_mode=mode) as b:
+            b.run()
+            res = b.results()
+        for p, r in zip(probs, res):
+            L, walks, wl = p[:3]
+            assert r["rounds"] == 1 and r["evals"] == walks * wl * ((L + 1) // 2), (mode, p, r["rounds"], r["evals"])
+            assert r["best_E"] == p[5]

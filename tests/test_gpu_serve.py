@@ -86,10 +86,10 @@ def test_requests_arriving_while_others_run(m):
 
 def launch_bytes(walks, walk_len, L, rounds):
     """Arena bytes of one launch over one request that runs `rounds` rounds: a visited
-    table (power-of-two slots >= 1.5 x pivots, 64-bit words of D + 1 bits) for each
+    table (power-of-two slots >= 3 x pivots, 64-bit words of D + 1 bits) for each
     walk of each round in flight, plus its lists (under 64 KiB here)."""
     slots = 64
-    while slots < (walk_len + 1) * 15 // 10 + 1:
+    while slots < (walk_len + 1) * 3 + 1:
         slots *= 2
     words = slots * (((L + 1) // 2 + 1 + 63) // 64)
     words += words % 2
@@ -224,3 +224,28 @@ def test_served_results_match_oracle_every_class(m, walk_mode):
         assert r["evals"] == int(w["evals"][0]) and r["rounds"] == int(w["rounds"][0]), p
         if tgt >= 0:
             assert r["reached_target"] == 1 and r["rounds"] <= 2
+
+
+def test_rounds_after_a_stop_are_never_counted(m):
+    # every request reaches its target in its first round while up to 8 (and,
+    # on an idle device, more) of its rounds run at once: the rounds issued
+    # past the stop must add neither evaluations nor rounds (Algorithm 1 stops
+    # at the first round whose best reaches the target), however their chunks
+    # finish around the stopping round's finalization
+    import oracle
+    reqs = []
+    for i in range(48):
+        L = (61, 121)[i % 2]
+        walks, wl, seed = 64, 120, 700 + i
+        D = (L + 1) // 2
+        o = oracle.solve(L, [seed], walks, wl, walks * wl * D, threads=8)
+        reqs.append((L, walks, wl, seed, 10 ** 12, int(o["best_E"][0]), o))
+    with m.Server(max_walks=64, rounds_per_launch=8) as sv:
+        tickets = [sv.submit(*p[:6]) for p in reqs]
+        results = [sv.wait(t) for t in tickets]
+    for p, r in zip(reqs, results):
+        L, walks, wl, seed, _, tgt, o = p
+        assert r["status"] == m.LABS_OK
+        assert r["rounds"] == 1 and r["evals"] == walks * wl * ((L + 1) // 2), (p[:6], r["rounds"], r["evals"])
+        assert r["best_E"] == tgt and r["reached_target"] == 1
+        assert np.array_equal(r["best_seq"], o["best_seq"][0]), p[:6]
