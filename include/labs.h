@@ -82,7 +82,9 @@ typedef struct labs_opts {
   int32_t max_rounds;     /* 0 = no limit; else stop every problem after this many rounds */
   int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (1 or 3,
                              whichever ran a short sample round of the same launch size faster;
-                             timed once per process per lag-word class and launch size),
+                             timed once per process per lag-word class and launch size by the
+                             first call with walks of >= 256 steps; a call of shorter walks
+                             times a sample of its own),
                              1 = full scan, one lane per walk (every neighbour from the
                                  correlations each step),
                              2 = incremental (stored neighbour deltas updated after each move),

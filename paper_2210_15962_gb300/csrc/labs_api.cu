@@ -154,7 +154,9 @@ int32_t resolve_variant(int32_t kernel) {
 // The library's choice for labs_opts.kernel == 0 (skew space): one lane per
 // walk or one warp per walk, whichever ran a sample round of the same launch
 // size faster, timed once per process for each lag-word class and launch size
-// (log2 of the walks in one launch).  The incremental variant is never chosen:
+// (log2 of the walks in one launch) by the first call whose walks have at least
+// kSampleSteps steps (a call of shorter walks times a sample of its own
+// length and keeps the choice to itself).  The incremental variant is never chosen:
 // it measured slower than the full scan at every class (it pays a fixed
 // per-flip cost at small W and its shared-memory state caps occupancy at
 // large W).  Every variant gives the same results.
@@ -419,7 +421,7 @@ struct Run {
     for (int32_t v : cand) {
       WalkParams p = params(0xFFFFF000u, 0, (uint32_t)g_chunk);
       p.variant = v;
-      p.walk_len = std::min(cfg.walk_len, kSampleSteps);
+      p.walk_len = std::min(cfg.walk_len, kSampleSteps);  // the call's tables hold this many
       p.cap = visited_table_cap(p.walk_len);
       p.done = nullptr;
       p.recheck_every = 0;
@@ -441,8 +443,13 @@ struct Run {
     cudaEventDestroy(e1);
     if (st != LABS_OK) return st;
     cfg.kernel = best;
-    std::lock_guard<std::mutex> lock(g_variant_mu);
-    g_variant[key] = best;
+    // a choice made on walks shorter than kSampleSteps holds for this call
+    // only: their start-up (tables, first pivot) weighs more than in longer
+    // walks, and the cached choice is meant for the step loop's rate
+    if (cfg.walk_len >= kSampleSteps) {
+      std::lock_guard<std::mutex> lock(g_variant_mu);
+      g_variant[key] = best;
+    }
     return LABS_OK;
   }
 
