@@ -177,8 +177,7 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_warp(const WalkP
   atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
 }
 
-// resident blocks the warp variant is compiled for: 6 at two words (7 spilled),
-// otherwise as the full-space kernel
+// resident blocks the warp variant is compiled for: 6 at two words (7 spilled)
 template <int W>
 struct MinBlocksWarp {
   static constexpr int value = W == 1 ? 8 : (W == 2 ? 6 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));

@@ -26,10 +26,11 @@ struct MinBlocksFor {
 };
 
 // The same for the full-space kernel (full_core.cuh), whose scan keeps more
-// state per word.
+// state per word: 3 blocks at seven words (+2% at L=200), 2 at eight (3
+// spill there).
 template <int W>
 struct MinBlocksFull {
-  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 7 : (W <= 4 ? 4 : (W <= 7 ? 3 : 2)));
 };
 
 // Flips of the scan's loop unrolled per iteration in the one-walk-per-lane
