@@ -177,10 +177,13 @@ __global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_warp(const WalkP
   atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
 }
 
-// resident blocks the warp variant is compiled for: 6 at two words (7 spilled)
+// resident blocks the warp variant is compiled for: 6 at two words (7
+// spilled); one more than the full-space kernel at three and five to eight
+// words (8192 walks of 2048 steps: +3% at L=161, +4% at L=301, +7% at 383,
+// +14% at 449, +10% at 511); four words spill with 5
 template <int W>
 struct MinBlocksWarp {
-  static constexpr int value = W == 1 ? 8 : (W == 2 ? 6 : (W <= 4 ? 4 : (W <= 6 ? 3 : 2)));
+  static constexpr int value = W == 1 ? 8 : (W == 2 ? 6 : (W == 3 ? 5 : (W <= 6 ? 4 : 3)));
 };
 
 template <int W>
