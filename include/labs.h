@@ -267,8 +267,10 @@ typedef struct labs_serve_cfg {
   int32_t max_L;             /* largest L accepted (sizes the table pools), default 301 */
   int32_t max_walks;         /* largest walks per round accepted, default 2048 */
   int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
-  int32_t rounds_per_launch; /* rounds each admitted request gets per launch at most, default 4
-                                (two launches are in flight: the next is queued while one runs) */
+  int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 4 (two
+                                launches are in flight: the next is queued while one runs); a
+                                launch that would leave SMs idle gives requests further rounds,
+                                up to 6 x rounds_per_launch in flight per request */
   int32_t block_threads;     /* threads per CTA of the batch kernels, default 128 */
   int32_t walk_mode;         /* 0: per launch and class, one walk per lane or per warp, whichever
                                 keeps the GPU faster busy with the launch's tasks (rates measured

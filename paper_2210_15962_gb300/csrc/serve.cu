@@ -329,9 +329,9 @@ static uint32_t rounds_to_issue(const Request &r, int64_t most, uint32_t ring) {
 // still needs); when those leave SMs idle (few requests, or the last ones of
 // a burst), requests get further rounds, one at a time in turn, until the
 // launch's warps reach what the device keeps resident of its widest-fitting
-// class or no request can take more.  The further rounds run on lanes that
-// would otherwise idle: a request that stops before them wastes nothing that
-// another could have used, and one that needs them finishes in fewer
+// class or no request can take more.  The further rounds mostly run on lanes
+// that would otherwise idle (the saturated throughput measured the same with
+// and without them), and a request that needs them finishes in fewer
 // launches.  Targets still stop every request at the same round.
 static std::vector<uint32_t> plan_rounds(const std::vector<const Request *> &rs, int rounds_per_launch,
                                          uint32_t ring, const std::vector<ClassInfo> &cls) {
