@@ -19,14 +19,15 @@ constexpr int kBatchMaxThreads = 256;
 constexpr int kBatchPatternMaxWords = 3;
 
 // register budget per thread of each class (the task loop keeps more state
-// live than the per-round kernel).  Measured one class at a time (57 or 38
-// problems of 2048 walks, autotuned shapes): five words run 4% faster at 168
-// than at 208; six to eight words, which also fit 168 without spilling, run
-// 1-15% slower there than unbounded.  Tighter budgets that spill measured
-// slower.
+// live than the per-round kernel).  Measured one class at a time (38 to 76
+// problems of 2048 walks, autotuned shapes): two words run 6-10% faster at 96
+// than at 112 (80: 4-9%), five words 4% faster at 168 than at 208; three
+// words lose 5-9% at 102, and six to eight words, which also fit 168 without
+// spilling, run 1-15% slower there than unbounded.  Tighter budgets that
+// spill measured slower.
 template <int W>
 struct MaxRegsFor {
-  static constexpr int value = W == 1 ? 104 : (W == 2 ? 112 : (W <= 4 ? 128 : (W == 5 ? 168 : 255)));
+  static constexpr int value = W == 1 ? 104 : (W == 2 ? 96 : (W <= 4 ? 128 : (W == 5 ? 168 : 255)));
 };
 
 // shared memory words of one warp: mask table, then (W + 2) parked words per lane
