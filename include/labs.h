@@ -80,15 +80,18 @@ typedef struct labs_opts {
   int64_t target_E;       /* stop a problem after the first round whose best E <= target_E;
                              < 0 = no target.  Set to -1 by labs_opts_init. */
   int32_t max_rounds;     /* 0 = no limit; else stop every problem after this many rounds */
-  int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (1 or 3,
-                             whichever ran a short sample round of the same launch size faster;
-                             timed once per process per lag-word class and launch size by the
-                             first call with walks of >= 256 steps; a call of shorter walks
-                             times a sample of its own),
+  int32_t kernel;         /* neighbourhood evaluation: 0 = the library's choice (1, 3 or, for
+                             launches of at most 16 walks per SM, 4: whichever ran a short
+                             sample round of the same launch size faster; timed once per
+                             process per lag-word class and launch size by the first call
+                             with walks of >= 256 steps; a call of shorter walks times a
+                             sample of its own),
                              1 = full scan, one lane per walk (every neighbour from the
                                  correlations each step),
                              2 = incremental (stored neighbour deltas updated after each move),
-                             3 = full scan, one warp per walk (the lanes split the D flips);
+                             3 = full scan, one warp per walk (the lanes split the D flips),
+                             4 = full scan, one CTA of 128 threads per walk (its threads split
+                                 the D flips; the paper's block per walk, Algorithm 2);
                              all give the same results; other values: LABS_EINVAL (the full
                              search space takes 0 and 1 only) */
   void *workspace;        /* optional device scratch of workspace_bytes bytes (e.g. from

@@ -34,6 +34,7 @@ KERNEL_AUTO = 0
 KERNEL_FULL_SCAN = 1
 KERNEL_INCREMENTAL = 2
 KERNEL_WARP = 3
+KERNEL_CTA = 4
 
 
 class LabsError(RuntimeError):

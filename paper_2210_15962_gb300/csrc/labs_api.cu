@@ -147,13 +147,15 @@ struct RunConfig {
 // The neighbourhood evaluation of labs_opts.kernel (0 is resolved by
 // Run::pick_variant before any round runs; the full scan stands in for it).
 int32_t resolve_variant(int32_t kernel) {
-  if (kernel == kVariantFullScan || kernel == kVariantIncremental || kernel == kVariantWarp) return kernel;
+  if (kernel == kVariantFullScan || kernel == kVariantIncremental || kernel == kVariantWarp ||
+      kernel == kVariantCta)
+    return kernel;
   return kVariantFullScan;
 }
 
 // The library's choice for labs_opts.kernel == 0 (skew space): one lane per
-// walk or one warp per walk, whichever ran a sample round of the same launch
-// size faster, timed once per process for each lag-word class and launch size
+// walk, one warp per walk or (for launches of few walks) one CTA per walk,
+// whichever ran a sample round of the same launch size faster, timed once per process for each lag-word class and launch size
 // (log2 of the walks in one launch) by the first call whose walks have at least
 // kSampleSteps steps (a call of shorter walks times a sample of its own
 // length and keeps the choice to itself).  The incremental variant is never chosen:
@@ -173,6 +175,7 @@ int ilog2(uint64_t x) {
 }
 
 constexpr int32_t kSampleSteps = 256;  // steps per walk of a variant-choice sample round
+constexpr int kCtaMaxWalksPerSm = 16;  // largest launch (walks per SM) for which one CTA per walk is timed
 
 }  // namespace
 }  // namespace psaw
@@ -412,13 +415,22 @@ struct Run {
         return LABS_OK;
       }
     }
-    const int32_t cand[2] = {kVariantFullScan, kVariantWarp};
+    // one CTA per walk is timed only for launches of at most kCtaMaxWalksPerSm
+    // walks per SM: with more, one warp per walk already keeps the SMs busy and
+    // the CTA's extra per-step work (every warp applies the move) only costs
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return LABS_ECUDA;
+    const bool offer_cta = g_chunk <= (size_t)kCtaMaxWalksPerSm * (size_t)sms;
+    const int32_t cand[3] = {kVariantFullScan, kVariantWarp, kVariantCta};
     float best_ms = 1e30f;
     int32_t best = kVariantFullScan;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LABS_ECUDA;
     labs_status st = LABS_OK;
     for (int32_t v : cand) {
+      if (v == kVariantCta && !offer_cta) continue;
       WalkParams p = params(0xFFFFF000u, 0, (uint32_t)g_chunk);
       p.variant = v;
       p.walk_len = std::min(cfg.walk_len, kSampleSteps);  // the call's tables hold this many
@@ -533,7 +545,7 @@ static labs_status walks_impl(int32_t space, int32_t L, const uint64_t *seeds, i
   if (opts_in) opts = *opts_in;
   else labs_opts_init(&opts);
   // the full search space has the full-scan kernel only
-  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantWarp;
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantCta;
   if (!valid_space_L(space, L) || !seeds || !best_seq || !best_E || n_seeds < 1 || walks_per_seed < 1 ||
       walk_len < 1 || walk_len > (1 << 26) || step_budget < 1 || opts.recheck_every < 0 || opts.max_rounds < 0 ||
       opts.kernel < 0 || opts.kernel > max_kernel)
@@ -629,7 +641,7 @@ static labs_status saw_round_impl(int32_t space, int32_t L, uint64_t seed, uint3
                                   int32_t *walk_best_step, int32_t *trace_flips, int32_t trace_begin,
                                   int32_t trace_count, int32_t visited_walk, uint64_t *visited_keys,
                                   int32_t visited_cap, int32_t *visited_count, int32_t kernel) {
-  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantWarp;
+  const int32_t max_kernel = space == kSpaceFull ? kVariantFullScan : kVariantCta;
   if (!valid_space_L(space, L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 ||
       kernel < 0 || kernel > max_kernel)
     return LABS_EINVAL;

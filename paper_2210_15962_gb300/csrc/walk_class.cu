@@ -3,6 +3,7 @@
 // of the full search space (all length-L sequences).  This file is
 // compiled once per class with -DPSAW_W=W (1..8), so that the classes' large,
 // pattern-specialised kernels build in parallel.
+#include "walk_cta.cuh"
 #include "walk_device.cuh"
 #include "walk_warp.cuh"
 
@@ -194,6 +195,53 @@ static cudaError_t launch_w_warp(const WalkParams &p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// One CTA = one walk (walk_cta.cuh): same contract as walk_kernel; block b
+// runs walk lid = b, its kWalkBlock threads splitting the walk's flips.
+template <int W, int T, int K, int MINB>
+__global__ void __launch_bounds__(kWalkBlock, MINB) walk_kernel_cta(const WalkParams p) {
+  constexpr int NS = W + 1;
+  const uint32_t lid = blockIdx.x;
+  const size_t table_words = (size_t)p.cap * (size_t)p.kw64;
+  const uint32_t gw = p.g_begin + lid;
+  const uint32_t prob = gw / (uint32_t)p.walks_per_problem;
+  const uint32_t walk = gw - prob * (uint32_t)p.walks_per_problem;
+  const bool live = lid < p.g_count && !(p.done && p.done[prob]);  // the same on every thread of the block
+  uint64_t *table = p.tables + (size_t)lid * table_words;
+  const Geometry g = make_geometry(p.L, T);
+  __shared__ __align__(16) uint32_t mask_rows[MaskTable<W>::kWords];
+  __shared__ uint32_t cta_sm[CtaWalkSmem<W>::kWords];
+  fill_mask_rows<W>(g, mask_rows, threadIdx.x, blockDim.x);
+  if (!live) return;
+  // the walk's table, zeroed by the block with 16-byte stores (table_words is even)
+  uint4 *t4 = reinterpret_cast<uint4 *>(table);
+  for (size_t i = threadIdx.x; i < table_words / 2; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();  // the mask table and the zeroed table are visible to the block
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  int32_t *trace = nullptr;
+  if (p.trace_flips && gw - p.trace_begin < p.trace_count)
+    trace = p.trace_flips + (size_t)(gw - p.trace_begin) * (size_t)p.walk_len;
+  WalkOut<NS> o;
+  run_walk_cta<W, T, K>(g, mu, mask_rows, cta_sm, p.seeds[prob], walk, p.round, p.walk_len, table, p.cap, p.kw64,
+                        p.recheck_every, trace, p.err, o);
+  if (threadIdx.x != 0) return;
+  p.w_bestE[gw] = o.bestE;
+  p.w_moves[gw] = o.moves;
+  p.w_stuck[gw] = o.stuck;
+  p.w_best_step[gw] = o.best_step;
+#pragma unroll
+  for (int w = 0; w < kKeyWords; ++w) p.w_key[(size_t)gw * kKeyWords + w] = w < NS ? o.best_key[w] : 0u;
+  atomicAdd(&p.p_evals[prob], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
+  if (p.plane_steps) atomicAdd(p.plane_steps, (unsigned long long)o.planes);
+  atomicMin(&p.p_round_best[prob], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
+}
+
+template <int W>
+static cudaError_t launch_w_cta(const WalkParams &p, cudaStream_t s) {
+  constexpr int T = PlanesFor<W>::value;
+  walk_kernel_cta<W, T, kTopK, MinBlocksWarp<W>::value><<<p.g_count, kWalkBlock, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 // The full search space (full_core.cuh): same contract as walk_kernel with L
 // flips per step and the whole sequence as key (kKeyWords >= W + 1 words).
 template <int W, int T, int K, int MINB>
@@ -243,6 +291,7 @@ cudaError_t launch_walk_class(const WalkParams &p, cudaStream_t s) {
   if (p.space == kSpaceFull) return launch_full<W>(p, s);
   if (p.variant == kVariantIncremental) return launch_w_incr<W>(p, s);
   if (p.variant == kVariantWarp) return launch_w_warp<W>(p, s);
+  if (p.variant == kVariantCta) return launch_w_cta<W>(p, s);
   return launch_w<W>(p, s);
 }
 

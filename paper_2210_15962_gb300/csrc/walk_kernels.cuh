@@ -16,6 +16,7 @@ constexpr int kTopK = 4;          // candidates kept per pass of the neighbourho
 constexpr int32_t kVariantFullScan = 1;     // every Delta_j from the digit planes each step
 constexpr int32_t kVariantIncremental = 2;  // stored Delta_j updated after each move
 constexpr int32_t kVariantWarp = 3;         // the full scan with one warp per walk (lanes split the flips)
+constexpr int32_t kVariantCta = 4;          // the full scan with one CTA per walk (its threads split the flips)
 
 enum ErrorBits : int32_t {
   kErrRecheck = 1,   // incremental state disagreed with the XOR+popc recheck

@@ -82,12 +82,14 @@ __device__ __forceinline__ void warp_apply_move(WalkState<W, T> &st, const Geome
   __syncwarp();
 }
 
-// The K smallest keys of the flips this lane owns in class q (t = lane,
-// lane + 32, ...), as eval_neighbours_tp computes them for one flip each.
+// The K smallest keys of the flips this thread owns in class q (t = first,
+// first + stride, ...: a lane of a warp that owns the walk takes every 32nd
+// flip, a thread of a CTA that owns it every blockDim-th), as
+// eval_neighbours_tp computes them for one flip each.
 template <int W, int T, int TP, int K, bool RESCAN>
 __device__ __forceinline__ void warp_scan_class(const WalkState<W, T> &st, const Geometry &g, const Muls &mu,
-                                                const uint32_t *mt, const uint32_t *sm, int q, int lane, int jprev,
-                                                uint32_t floor, uint32_t (&top)[K]) {
+                                                const uint32_t *mt, const uint32_t *sm, int q, int first,
+                                                int stride, int jprev, uint32_t floor, uint32_t (&top)[K]) {
   using MT = MaskTable<W>;
   constexpr int NS = W + 1, CW = WarpWalkSmem<W>::kClsWords;
   const int Nq = g.D - q;
@@ -100,7 +102,7 @@ __device__ __forceinline__ void warp_scan_class(const WalkState<W, T> &st, const
   const uint32_t *R = sm + (2 + q) * CW;
   const uint32_t *rows = mt + (size_t)q * MT::kRows * MT::kRowWords;
   const int tend = nloop + (has_centre ? 1 : 0);
-  for (int t = lane; t < tend; t += 32) {
+  for (int t = first; t < tend; t += stride) {
     // y window: class bits t+1, t+2, ...; x window: bits t-1, t-2, ...
     // (the reversal R holds class bit 32 NS - 1 - k at bit k)
     uint32_t F[W], B[W];
@@ -131,12 +133,12 @@ __device__ __forceinline__ void warp_scan_class(const WalkState<W, T> &st, const
 
 template <int W, int T, int TP, int K, bool RESCAN>
 __device__ __forceinline__ void warp_scan_tp(const WalkState<W, T> &st, const Geometry &g, const Muls &mu,
-                                             const uint32_t *mt, const uint32_t *sm, int lane, int jprev,
-                                             uint32_t floor, uint32_t (&top)[K]) {
+                                             const uint32_t *mt, const uint32_t *sm, int first, int stride,
+                                             int jprev, uint32_t floor, uint32_t (&top)[K]) {
 #pragma unroll
   for (int r = 0; r < K; ++r) top[r] = kNone;
-  warp_scan_class<W, T, TP, K, RESCAN>(st, g, mu, mt, sm, 0, lane, jprev, floor, top);
-  warp_scan_class<W, T, TP, K, RESCAN>(st, g, mu, mt, sm, 1, lane, jprev, floor, top);
+  warp_scan_class<W, T, TP, K, RESCAN>(st, g, mu, mt, sm, 0, first, stride, jprev, floor, top);
+  warp_scan_class<W, T, TP, K, RESCAN>(st, g, mu, mt, sm, 1, first, stride, jprev, floor, top);
 }
 
 // The warp's K smallest keys in order (warp-uniform), from each lane's K smallest.
@@ -154,22 +156,24 @@ __device__ __forceinline__ void warp_merge_top(uint32_t (&top)[K], uint32_t (&wt
   }
 }
 
+// The warp's K smallest keys of the flips its threads own (first, stride as
+// in warp_scan_class), in order and warp-uniform.
 template <int W, int T, int K>
 __device__ __forceinline__ void warp_scan(const WalkState<W, T> &st, const Geometry &g, const Muls &mu,
-                                          const uint32_t *mt, const uint32_t *sm, int lane, int tp, int jprev,
-                                          uint32_t floor, uint32_t (&wtop)[K]) {
+                                          const uint32_t *mt, const uint32_t *sm, int first, int stride, int tp,
+                                          int jprev, uint32_t floor, uint32_t (&wtop)[K]) {
   constexpr int T3 = T - 3 >= 2 ? T - 3 : 2;
   uint32_t top[K];
   if (floor == 0) {
-    if (tp >= T) warp_scan_tp<W, T, T, K, false>(st, g, mu, mt, sm, lane, jprev, 0u, top);
-    else if (tp == T - 1) warp_scan_tp<W, T, T - 1, K, false>(st, g, mu, mt, sm, lane, jprev, 0u, top);
-    else if (tp == T - 2) warp_scan_tp<W, T, T - 2, K, false>(st, g, mu, mt, sm, lane, jprev, 0u, top);
-    else warp_scan_tp<W, T, T3, K, false>(st, g, mu, mt, sm, lane, jprev, 0u, top);
+    if (tp >= T) warp_scan_tp<W, T, T, K, false>(st, g, mu, mt, sm, first, stride, jprev, 0u, top);
+    else if (tp == T - 1) warp_scan_tp<W, T, T - 1, K, false>(st, g, mu, mt, sm, first, stride, jprev, 0u, top);
+    else if (tp == T - 2) warp_scan_tp<W, T, T - 2, K, false>(st, g, mu, mt, sm, first, stride, jprev, 0u, top);
+    else warp_scan_tp<W, T, T3, K, false>(st, g, mu, mt, sm, first, stride, jprev, 0u, top);
   } else {
-    if (tp >= T) warp_scan_tp<W, T, T, K, true>(st, g, mu, mt, sm, lane, jprev, floor, top);
-    else if (tp == T - 1) warp_scan_tp<W, T, T - 1, K, true>(st, g, mu, mt, sm, lane, jprev, floor, top);
-    else if (tp == T - 2) warp_scan_tp<W, T, T - 2, K, true>(st, g, mu, mt, sm, lane, jprev, floor, top);
-    else warp_scan_tp<W, T, T3, K, true>(st, g, mu, mt, sm, lane, jprev, floor, top);
+    if (tp >= T) warp_scan_tp<W, T, T, K, true>(st, g, mu, mt, sm, first, stride, jprev, floor, top);
+    else if (tp == T - 1) warp_scan_tp<W, T, T - 1, K, true>(st, g, mu, mt, sm, first, stride, jprev, floor, top);
+    else if (tp == T - 2) warp_scan_tp<W, T, T - 2, K, true>(st, g, mu, mt, sm, first, stride, jprev, floor, top);
+    else warp_scan_tp<W, T, T3, K, true>(st, g, mu, mt, sm, first, stride, jprev, floor, top);
   }
   warp_merge_top<K>(top, wtop);
 }
@@ -211,7 +215,7 @@ __device__ void run_walk_warp(const Geometry &g, const Muls &mu, const uint32_t 
     bool decided = false;
     while (!decided) {
       uint32_t wtop[K];
-      warp_scan<W, T, K>(st, g, mu, mt, sm, lane, tp, jprev, floor, wtop);
+      warp_scan<W, T, K>(st, g, mu, mt, sm, lane, 32, tp, jprev, floor, wtop);
       // lane r < K probes candidate r; the first candidate in key order that is
       // absent (no more neighbours: stuck) or unvisited decides the step
       uint32_t cand = kNone;

@@ -112,7 +112,7 @@ def test_walks_rejects_bad_sizes(lib):
     lib.labs_opts_init(ctypes.byref(o))
     o.recheck_every = -1
     assert lib.labs_walks(27, p(seeds), 1, 4, 8, 100, p(seq), p(E), ctypes.byref(o), None) == m.LABS_EINVAL
-    for bad_kernel in (-1, 4):
+    for bad_kernel in (-1, 5):
         lib.labs_opts_init(ctypes.byref(o))
         o.kernel = bad_kernel
         assert lib.labs_walks(27, p(seeds), 1, 4, 8, 100, p(seq), p(E), ctypes.byref(o), None) == m.LABS_EINVAL
@@ -134,7 +134,7 @@ def test_saw_round_rejects_bad_args(lib):
     assert lib.labs_saw_round(27, 1, 0, 4, 8, 0, None, None, None, None, None, m._ptr(t), 2, 4, -1, None, 0,
                               None, 0) == m.LABS_EINVAL
     assert lib.labs_saw_round(27, 1, 0, 4, 8, 0, None, None, None, None, None, None, 0, 0, -1, None, 0,
-                              None, 4) == m.LABS_EINVAL
+                              None, 5) == m.LABS_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

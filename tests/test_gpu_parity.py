@@ -71,7 +71,9 @@ def test_energy_batch_and_bad_values(m, orc):
 
 
 # ------------------------------------------------------- one round, per walk
-KERNELS = [1, 2, 3]  # full scan (lane per walk), incremental, full scan (warp per walk): all give the oracle's results
+# full scan (lane per walk), incremental, full scan (warp per walk), full scan (CTA per walk): all give the
+# oracle's results
+KERNELS = [1, 2, 3, 4]
 
 
 def compare_round(m, orc, L, seed, rnd, n_walks, walk_len, check_walks, trace_walks=(), recheck=0, kernel=1):
@@ -215,7 +217,7 @@ def test_variants_agree_on_whole_solves(m, L):
     D = (L + 1) // 2
     wl = 8 * D
     # every variant, and the library's timed choice (kernel 0), solve alike
-    res = [m.labs_walks(L, [3, 4], 256, wl, 256 * wl * D * 2, kernel=k) for k in (1, 2, 3, 0)]
+    res = [m.labs_walks(L, [3, 4], 256, wl, 256 * wl * D * 2, kernel=k) for k in (1, 2, 3, 4, 0)]
     for r in res[1:]:
         for key in ("best_E", "best_seq", "evals", "rounds"):
             assert np.array_equal(res[0][key], r[key]), key
