@@ -737,8 +737,8 @@ def run_walklen(args, world, rank, local):
 
 
 def run_variants(args, world, rank, local):
-    """One lane per walk against one warp per walk (labs_opts.kernel 1 and 3)
-    and the library's timed choice (kernel 0): one round of --walk-len-variants
+    """One lane per walk against one warp and one CTA per walk (labs_opts.kernel
+    1, 3 and 4) and the library's timed choice (kernel 0): one round of --walk-len-variants
     steps at each L of --variants-L and each walk count of --variants-walks,
     evaluations per second of each (CUDA events around the call's kernels)."""
     import torch
@@ -755,7 +755,7 @@ def run_variants(args, world, rank, local):
         for walks in [int(x) for x in args.variants_walks.split(",")]:
             row = {"L": L, "walks": walks, "walk_len": wl}
             ref = None
-            for name, k in (("lane_per_walk", 1), ("warp_per_walk", 3), ("library_choice", 0)):
+            for name, k in (("lane_per_walk", 1), ("warp_per_walk", 3), ("cta_per_walk", 4), ("library_choice", 0)):
                 pkg.labs_walks(L, [7], walks, min(wl, 64), walks * min(wl, 64) * D, kernel=k, stream=stream)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -795,7 +795,7 @@ def main():
     ap.add_argument("--workload", default="plain",
                     choices=["plain", "batched", "serving", "large", "table1", "walklen", "variants"])
     ap.add_argument("--variants-L", default="121,301,449,511")
-    ap.add_argument("--variants-walks", default="1024,8192,65536")
+    ap.add_argument("--variants-walks", default="256,1024,8192,65536")
     ap.add_argument("--walk-len-variants", type=int, default=2048)
     ap.add_argument("--walklen-cal-budget", type=int, default=10 ** 12)
     ap.add_argument("--walklen-seeds", type=int, default=4)
