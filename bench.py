@@ -57,7 +57,7 @@ SM_MAX_MHZ = 2070.0
 # capture of the walk kernel on 107008 walks x 1024 steps (18.73 GB, scaled by
 # walk-steps to 131072 x 8192), valid only for the kernel sources it was
 # captured from.
-TRAFFIC = {"sources_sha256_prefix": "18ee803c8b3c3f91", "bytes_per_launch": 20.865e9 * (131072 * 8192) / (107008 * 1024)}
+TRAFFIC = {"sources_sha256_prefix": "01e717a4a5da2314", "bytes_per_launch": 20.868e9 * (131072 * 8192) / (107008 * 1024)}
 WALK_SOURCES = ["walk_core.cuh", "walk_device.cuh", "walk_incr.cuh", "walk_class.cu", "walk_kernels.cuh"]
 
 
