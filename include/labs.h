@@ -211,13 +211,15 @@ typedef struct labs_batch_opts {
   int32_t autotune;          /* 1: pick per class, by timing candidates on a sample of its first
                                 launch (cached per process): one walk per lane with 64, 128 or
                                 256 walks per CTA, 1.5 or 3 table slots per pivot and the scan's
-                                flip loop unrolled once or twice, or one walk per warp (offered
-                                while every problem has <= 4096 walks) */
+                                flip loop unrolled once or twice, or one walk per warp or per
+                                CTA of 128 threads (both offered while every problem has <= 4096
+                                walks) */
   int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
   int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 30 or autotuned */
   int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
   int32_t walk_mode;         /* 0: one walk per lane, or what autotune picks; 1: one walk per lane;
-                                2: one walk per warp in every class (every problem <= 4096 walks,
+                                2: one walk per warp in every class; 3: one walk per CTA of 128
+                                threads in every class (2 and 3: every problem <= 4096 walks,
                                 else LABS_EINVAL); all give the same results */
 } labs_batch_opts;
 
@@ -239,9 +241,10 @@ labs_status labs_batch_result(const labs_batch *b, int32_t i, int8_t *best_seq, 
  * neighbourhood scans used, summed over the walk steps of its rounds. */
 labs_status labs_batch_plane_steps(const labs_batch *b, int32_t i, uint64_t *plane_steps);
 /* Launch shape chosen for class W (any output may be NULL): threads per CTA,
- * table factor x 10, walks resident at once, 1 if the class runs one walk per
- * warp (the lanes split each walk's flips) or 0 for one walk per lane, and how
- * many times the scan's flip loop is unrolled (1 or 2). */
+ * table factor x 10, walks resident at once, the walk's unit (0: one walk per
+ * lane, 1: one walk per warp, the lanes splitting each walk's flips, 2: one
+ * walk per CTA of 128 threads, its threads splitting them), and how many times
+ * the scan's flip loop is unrolled (1 or 2). */
 labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t *block_threads, int32_t *table_factor_x10,
                              int32_t *resident_walks, int32_t *warp_per_walk, int32_t *unroll);
 labs_status labs_batch_destroy(labs_batch *b);

@@ -28,6 +28,7 @@ LABS_ESHUTDOWN = -8
 WALK_MODE_AUTO = 0
 WALK_MODE_LANE = 1
 WALK_MODE_WARP = 2
+WALK_MODE_CTA = 3  # batches only: one walk per CTA of 128 threads
 LABS_L_MIN = 5
 LABS_L_MAX = 511
 KERNEL_AUTO = 0
@@ -494,7 +495,8 @@ class Batch:
         _check(load().labs_batch_shape(self._h, W, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3]), _ptr(v[3:4]),
                                        _ptr(v[4:5])), "labs_batch_shape")
         return {"block_threads": int(v[0]), "table_factor_x10": int(v[1]), "resident_walks": int(v[2]),
-                "warp_per_walk": bool(v[3]), "unroll": int(v[4])}
+                "warp_per_walk": int(v[3]) == 1, "cta_per_walk": int(v[3]) == 2,
+                "walk_unit": ("lane", "warp", "cta")[int(v[3])], "unroll": int(v[4])}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -111,8 +111,8 @@ inline double batch_task_cost(int L, int walk_len) {
 // Reset the listed records for their new rounds (before any of their tasks run).
 cudaError_t launch_issue_records(const RecordInit *list, int n, const RoundRecords &rec, cudaStream_t s);
 // Kernel variants of a class: one walk per lane, the same with the scan's
-// flip loop unrolled twice, and one walk per warp.
-constexpr int kBatchLane = 0, kBatchWarp = 1, kBatchLaneUnroll2 = 2;
+// flip loop unrolled twice, one walk per warp, and one walk per CTA.
+constexpr int kBatchLane = 0, kBatchWarp = 1, kBatchLaneUnroll2 = 2, kBatchCta = 3;
 
 // Launch the persistent kernel for lag-word class W with `block` threads per
 // block and as many blocks as fit on the device at once, at most max_blocks
@@ -126,6 +126,10 @@ int batch_resident_lanes(int W, int block, int unroll = 1);
 // per warp of the grid): the launch, and the warps it keeps resident.
 cudaError_t launch_batch_warp(int W, int block, const BatchKernelParams &p, cudaStream_t s, int max_blocks = 0);
 int batch_resident_warps(int W, int block);
+// CTA mode (one walk per CTA of 128 threads, tasks of one walk; the pool holds
+// one table per CTA of the grid): the launch, and the CTAs it keeps resident.
+cudaError_t launch_batch_cta(int W, const BatchKernelParams &p, cudaStream_t s, int max_blocks = 0);
+int batch_resident_ctas(int W);
 // Finalize, in round order, the complete rounds of the listed problems (those
 // the in-kernel finalization left, normally none).
 cudaError_t launch_batch_finalize(const int32_t *problems, int n, const RoundRecords &rec, const ProblemState &ps,

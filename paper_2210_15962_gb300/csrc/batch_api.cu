@@ -43,6 +43,8 @@ cudaError_t dalloc(T **p, size_t n) {
 struct ClassPlan {
   int W = 0;
   bool warp = false;  // warp mode: one walk per warp, tasks of one walk
+  bool cta = false;   // CTA mode: one walk per CTA of 128 threads, tasks of one walk
+  bool per_walk() const { return warp || cta; }
   int unroll = 1;     // lane mode: the scan's flip loop unrolled 1 or 2 times
   int block = 128;
   int factor_x10 = kTableFactorX10;
@@ -64,7 +66,7 @@ struct TuneKey {
 std::mutex g_tune_mu;
 struct Tuned {
   int block, factor_x10;
-  bool warp;
+  bool warp, cta;
   int unroll;
 };
 std::map<TuneKey, Tuned> g_tuned;
@@ -215,7 +217,9 @@ labs_status build_pools(labs_batch *b) {
     }
     c.pool_words = (words + 1) / 2 * 2;
     // a table per lane, or per warp in warp mode
-    c.resident = c.warp ? batch_resident_warps(c.W, c.block) : batch_resident_lanes(c.W, c.block, c.unroll);
+    c.resident = c.cta    ? batch_resident_ctas(c.W)
+                 : c.warp ? batch_resident_warps(c.W, c.block)
+                          : batch_resident_lanes(c.W, c.block, c.unroll);
     if (c.resident <= 0) return LABS_ECUDA;
     BCU(dalloc(&c.pool, (size_t)c.resident * c.pool_words));
   }
@@ -254,13 +258,13 @@ labs_status plan_launch(labs_batch *b, const std::vector<int32_t> &next_round, c
       const labs_problem &p = b->pr[i];
       uint64_t r = std::min<uint64_t>(rounds_needed(p, evals[i]), b->ring[i]);
       if (p.target_E >= 0) r = std::min<uint64_t>(r, (uint64_t)b->rounds_per_launch);
-      const bool warp = b->cls[ci].warp;
-      const uint32_t chunks = warp ? (uint32_t)p.walks : (uint32_t)((p.walks + 31) / 32);
+      const bool per_walk = b->cls[ci].per_walk();
+      const uint32_t chunks = per_walk ? (uint32_t)p.walks : (uint32_t)((p.walks + 31) / 32);
       const double cost = task_cost(p);
       for (uint32_t k = 0; k < (uint32_t)r; ++k) {
         const uint32_t round = (uint32_t)next_round[i] + k;
         const uint32_t rec = b->rec_base[i] + round % b->ring[i];
-        issue.push_back(RecordInit{rec, round, chunks, warp ? 0u : 5u});
+        issue.push_back(RecordInit{rec, round, chunks, per_walk ? 0u : 5u});
         for (uint32_t ch = 0; ch < chunks; ++ch)
           tk[ci].push_back({p.target_E >= 0 ? k : 0u, cost, BatchTask{(uint32_t)i, round, ch, rec}});
       }
@@ -312,7 +316,8 @@ labs_status enqueue_launch(labs_batch *b, std::vector<std::pair<cudaEvent_t, cud
     cudaStream_t x = b->cs[ci];
     BCU(cudaStreamWaitEvent(x, b->fork, 0));
     if (c.n_tasks) {
-      if (c.warp) BCU(launch_batch_warp(c.W, c.block, kernel_params(b, c, (int)ci), x));
+      if (c.cta) BCU(launch_batch_cta(c.W, kernel_params(b, c, (int)ci), x));
+      else if (c.warp) BCU(launch_batch_warp(c.W, c.block, kernel_params(b, c, (int)ci), x));
       else BCU(launch_batch(c.W, c.block, kernel_params(b, c, (int)ci), x, nullptr, 0, c.unroll));
       ++*launches;
     }
@@ -345,8 +350,9 @@ uint32_t first_launch_rounds(const labs_batch *b, const labs_problem &p) {
 
 // Time candidate launch shapes of one class: lane mode (one walk per lane,
 // tasks of 32 walks) with walks per CTA in {64, 128, 256}, table capacity in
-// {1.5, 3} x pivots and the scan's flip loop unrolled once or twice, and warp
-// mode (one walk per warp) with 128 or 256 threads per CTA.  Each candidate runs the class's first launch as far as one
+// {1.5, 3} x pivots and the scan's flip loop unrolled once or twice, warp
+// mode (one walk per warp) with 128 or 256 threads per CTA, and CTA mode (one
+// walk per CTA of 128 threads).  Each candidate runs the class's first launch as far as one
 // wave of its resident lanes (or warps) reaches, on rounds no solve uses, with
 // walks shortened to at most 256 steps; the one with the lowest time per
 // neighbour evaluation wins (cached per process).  The sample's tasks all
@@ -368,22 +374,25 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       c.block = it->second.block;
       c.factor_x10 = it->second.factor_x10;
       c.warp = it->second.warp;
+      c.cta = it->second.cta;
       c.unroll = it->second.unroll;
       return LABS_OK;
     }
   }
   struct Cand {
-    bool warp;
+    bool warp, cta;
     int block, factor, unroll;
   };
   std::vector<Cand> cands;
   for (int u : {1, 2})
     for (int fct : {15, 30})
-      for (int blk : {64, 128, 256}) cands.push_back({false, blk, fct, u});
-  if (b->warp_allowed)
-    for (int blk : {128, 256}) cands.push_back({true, blk, kTableFactorX10, 1});
+      for (int blk : {64, 128, 256}) cands.push_back({false, false, blk, fct, u});
+  if (b->warp_allowed) {
+    for (int blk : {128, 256}) cands.push_back({true, false, blk, kTableFactorX10, 1});
+    cands.push_back({false, true, kWalkBlock, kTableFactorX10, 1});
+  }
   double best_ns = 1e300;
-  Cand best = {c.warp, c.block, c.factor_x10, c.unroll};
+  Cand best = {c.warp, c.cta, c.block, c.factor_x10, c.unroll};
   std::vector<labs_problem> saved = b->pr;
   for (int i : c.probs) b->pr[i].walk_len = std::min(b->pr[i].walk_len, 256);
   auto restore = [&](labs_status st) {
@@ -392,18 +401,20 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   };
   for (const Cand &cd : cands) {
     c.warp = cd.warp;
+    c.cta = cd.cta;
     c.block = cd.block;
     c.factor_x10 = cd.factor;
     c.unroll = cd.unroll;
     labs_status st = build_pools(b);
     if (st != LABS_OK) return restore(st);
     // the first launch's tasks, as far as one wave reaches
-    const uint64_t wave = cd.warp ? (uint64_t)c.resident : (uint64_t)c.resident / 32;
-    const uint64_t want = std::max<uint64_t>(1, std::min(cd.warp ? walk_tasks : lane_tasks, wave));
+    const bool per_walk = cd.warp || cd.cta;
+    const uint64_t wave = per_walk ? (uint64_t)c.resident : (uint64_t)c.resident / 32;
+    const uint64_t want = std::max<uint64_t>(1, std::min(per_walk ? walk_tasks : lane_tasks, wave));
     std::vector<BatchTask> tk;
     for (uint64_t k = 0; tk.size() < want; ++k) {
       const int i = c.probs[k % c.probs.size()];
-      const uint32_t units = cd.warp ? (uint32_t)b->pr[i].walks : (uint32_t)((b->pr[i].walks + 31) / 32);
+      const uint32_t units = per_walk ? (uint32_t)b->pr[i].walks : (uint32_t)((b->pr[i].walks + 31) / 32);
       const uint64_t pass = k / c.probs.size();
       tk.push_back(BatchTask{(uint32_t)i, 1000u + (uint32_t)(pass / units), (uint32_t)(pass % units),
                              b->tune_record});
@@ -426,7 +437,8 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
       cudaMemsetAsync(b->rec.left + b->tune_record, 0xFF, sizeof(uint32_t), b->s);
       cudaMemsetAsync(b->rec.evals + b->tune_record, 0, sizeof(unsigned long long), b->s);
       cudaEventRecord(e0, b->s);
-      if (cd.warp) launch_batch_warp(c.W, c.block, kernel_params(b, c, ci), b->s);
+      if (cd.cta) launch_batch_cta(c.W, kernel_params(b, c, ci), b->s);
+      else if (cd.warp) launch_batch_warp(c.W, c.block, kernel_params(b, c, ci), b->s);
       else launch_batch(c.W, c.block, kernel_params(b, c, ci), b->s, nullptr, 0, c.unroll);
       cudaEventRecord(e1, b->s);
       cudaEventSynchronize(e1);
@@ -444,12 +456,13 @@ labs_status autotune_class(labs_batch *b, ClassPlan &c, int ci) {
   }
   b->pr = saved;
   c.warp = best.warp;
+  c.cta = best.cta;
   c.block = best.block;
   c.factor_x10 = best.factor;
   c.unroll = best.unroll;
   c.n_tasks = 0;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[key] = Tuned{best.block, best.factor, best.warp, best.unroll};
+  g_tuned[key] = Tuned{best.block, best.factor, best.warp, best.cta, best.unroll};
   return LABS_OK;
 }
 
@@ -554,17 +567,17 @@ labs_status alloc_state(labs_batch *b) {
 }
 
 // Key slots of every record for the classes' chosen modes: a slot per chunk of
-// 32 walks in lane mode, per walk in warp mode; the autotuner's slots first.
+// 32 walks in lane mode, per walk in warp and CTA mode; the autotuner's slots first.
 labs_status alloc_keys(labs_batch *b) {
   std::vector<unsigned long long> base(b->n_records + 1);
   unsigned long long next = kTuneKeySlots;
   base[b->tune_record] = 0;
   for (size_t i = 0; i < b->pr.size(); ++i) {
-    bool warp = false;
+    bool per_walk = false;
     for (auto &c : b->cls)
-      if (c.W == b->W[i]) warp = c.warp;
-    const unsigned long long slots = warp ? (unsigned long long)b->pr[i].walks
-                                          : (unsigned long long)((b->pr[i].walks + 31) / 32);
+      if (c.W == b->W[i]) per_walk = c.per_walk();
+    const unsigned long long slots = per_walk ? (unsigned long long)b->pr[i].walks
+                                              : (unsigned long long)((b->pr[i].walks + 31) / 32);
     for (uint32_t k = 0; k < b->ring[i]; ++k) {
       base[b->rec_base[i] + k] = next;
       next += slots;
@@ -605,7 +618,7 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (opts.block_threads < 0 || opts.block_threads > 256 || (opts.block_threads % 32) != 0 ||
       opts.table_factor_x10 < 0 || (opts.table_factor_x10 > 0 && opts.table_factor_x10 < 12) ||
       opts.rounds_per_launch < 0 || opts.rounds_per_launch > (int32_t)kMaxRingRounds || opts.walk_mode < 0 ||
-      opts.walk_mode > 2)
+      opts.walk_mode > 3)
     return LABS_EINVAL;
   for (int i = 0; i < n; ++i)
     if (!valid_problem(problems[i])) return LABS_EINVAL;
@@ -653,8 +666,11 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
     b->n_records += (uint32_t)r;
   }
   b->warp_allowed = max_walks <= (uint32_t)kWarpModeMaxWalks && opts.walk_mode != 1;
-  if (opts.walk_mode == 2 && !b->warp_allowed) return fail(LABS_EINVAL);
-  for (auto &c : b->cls) c.warp = opts.walk_mode == 2;
+  if (opts.walk_mode >= 2 && !b->warp_allowed) return fail(LABS_EINVAL);
+  for (auto &c : b->cls) {
+    c.warp = opts.walk_mode == 2;
+    c.cta = opts.walk_mode == 3;
+  }
   std::sort(b->cls.begin(), b->cls.end(), [](const ClassPlan &x, const ClassPlan &y) { return x.W > y.W; });
   if ((st = alloc_state(b)) != LABS_OK) return fail(st);
   for (size_t ci = 0; ci < b->cls.size(); ++ci) {
@@ -670,7 +686,7 @@ extern "C" labs_status labs_batch_create(const labs_problem *problems, int32_t n
   if (opts.autotune) {
     for (size_t ci = 0; ci < b->cls.size(); ++ci) {
       ClassPlan &c = b->cls[ci];
-      const bool fixed = (opts.block_threads && opts.table_factor_x10) || opts.walk_mode == 2;
+      const bool fixed = (opts.block_threads && opts.table_factor_x10) || opts.walk_mode >= 2;
       if (!fixed && (st = autotune_class(b, c, (int)ci)) != LABS_OK) return fail(st);
       if (opts.block_threads) c.block = opts.block_threads;
       if (opts.table_factor_x10) c.factor_x10 = opts.table_factor_x10;
@@ -818,8 +834,8 @@ extern "C" labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t 
     if (block_threads) *block_threads = c.block;
     if (table_factor_x10) *table_factor_x10 = c.factor_x10;
     if (resident_walks) *resident_walks = c.resident;
-    if (warp_per_walk) *warp_per_walk = c.warp ? 1 : 0;
-    if (unroll) *unroll = c.warp ? 1 : c.unroll;
+    if (warp_per_walk) *warp_per_walk = c.cta ? 2 : (c.warp ? 1 : 0);
+    if (unroll) *unroll = c.per_walk() ? 1 : c.unroll;
     return LABS_OK;
   }
   return LABS_ENOTFOUND;

@@ -1,4 +1,4 @@
-// The persistent batch kernels of one lag-word class W (lane mode and warp
+// The persistent batch kernels of one lag-word class W (lane, warp and CTA
 // mode) and their launch helpers.  Compiled once per class with -DPSAW_W=W
 // (1..8) so that the classes build in parallel.
 #include "batch_device.cuh"
@@ -56,6 +56,34 @@ static int resident_warps_w(int block) {
   return per_sm * sms * (block / 32);
 }
 
+// CTA mode: blocks of kWalkBlock threads, one walk (and one visited table) each
+template <int W>
+static size_t batch_cta_smem_bytes() {
+  return (size_t)kBatchWalkCtaWords<W> * sizeof(uint32_t);
+}
+
+template <int W>
+static int resident_ctas_w() {
+  const size_t smem = batch_cta_smem_bytes<W>();
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaFuncSetAttribute(batch_kernel_cta<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_cta<W>, kWalkBlock, smem) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+template <int W>
+static cudaError_t launch_batch_cta_w(const BatchKernelParams &p, cudaStream_t s, int max_blocks) {
+  int grid = resident_ctas_w<W>();
+  if (max_blocks > 0 && max_blocks < grid) grid = max_blocks;
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  batch_kernel_cta<W><<<grid, kWalkBlock, batch_cta_smem_bytes<W>(), s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int W, int U>
 static cudaError_t launch_batch_w(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out,
                                   int max_blocks) {
@@ -88,10 +116,12 @@ static int resident_w(int block) {
 }
 
 // variant: kBatchLane (one walk per lane), kBatchLaneUnroll2 (the same with the
-// scan's flip loop unrolled twice) or kBatchWarp (one walk per warp)
+// scan's flip loop unrolled twice), kBatchWarp (one walk per warp) or kBatchCta
+// (one walk per CTA of kWalkBlock threads; `block` is ignored)
 template <int W>
 cudaError_t launch_batch_class(int block, const BatchKernelParams &p, cudaStream_t s, int *grid_out, int max_blocks,
                                int variant) {
+  if (variant == kBatchCta) return launch_batch_cta_w<W>(p, s, max_blocks);
   if (variant == kBatchWarp) return launch_batch_warp_w<W>(block, p, s, max_blocks);
   if (variant == kBatchLaneUnroll2) return launch_batch_w<W, 2>(block, p, s, grid_out, max_blocks);
   return launch_batch_w<W, 1>(block, p, s, grid_out, max_blocks);
@@ -99,6 +129,7 @@ cudaError_t launch_batch_class(int block, const BatchKernelParams &p, cudaStream
 
 template <int W>
 int batch_resident_class(int block, int variant) {
+  if (variant == kBatchCta) return resident_ctas_w<W>();
   if (variant == kBatchWarp) return resident_warps_w<W>(block);
   if (variant == kBatchLaneUnroll2) return resident_w<W, 2>(block);
   return resident_w<W, 1>(block);

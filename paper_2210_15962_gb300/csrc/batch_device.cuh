@@ -4,6 +4,7 @@
 // the in-kernel round finalization they share with the post-launch pass.
 #pragma once
 #include "batch.cuh"
+#include "walk_cta.cuh"
 #include "walk_device.cuh"
 #include "walk_warp.cuh"
 
@@ -37,6 +38,11 @@ constexpr int kBatchWarpWords = MaskTable<W>::kWords + (W + 2) * 32;
 // rounded to 16 bytes so that every warp's mask table stays 16-byte aligned
 template <int W>
 constexpr int kBatchWalkWarpWords = (MaskTable<W>::kWords + WarpWalkSmem<W>::kWords + 3) / 4 * 4;
+// in CTA mode (one walk per CTA of kWalkBlock threads): the mask table, the
+// walk's CtaWalkSmem words, then the task index and its problem's stop flag as
+// thread 0 read them
+template <int W>
+constexpr int kBatchWalkCtaWords = MaskTable<W>::kWords + CtaWalkSmem<W>::kWords + 2;
 
 __device__ __forceinline__ uint32_t load_volatile(const uint32_t *x) { return *(const volatile uint32_t *)x; }
 __device__ __forceinline__ int32_t load_volatile(const int32_t *x) { return *(const volatile int32_t *)x; }
@@ -244,6 +250,68 @@ __global__ void __launch_bounds__(kBatchMaxThreads) __maxnreg__(MaxRegsFor<W>::v
       }
     }
     __syncwarp();
+  }
+}
+
+// CTA mode: every CTA of kWalkBlock threads takes tasks of one walk
+// (task.chunk = the walk's index) and runs the walk with its threads splitting
+// the flips (run_walk_cta); one visited table per CTA.  Thread 0 takes the
+// task and reads its problem's stop flag for the whole block, so every thread
+// takes the same branches; the walk publishes its best key in its own key slot
+// of the round's record, as in warp mode.
+template <int W>
+__global__ void __launch_bounds__(kWalkBlock) __maxnreg__(MaxRegsFor<W>::value)
+    batch_kernel_cta(const BatchKernelParams p) {
+  constexpr int T = PlanesFor<W>::value;
+  constexpr int NS = W + 1;
+  const int tid = threadIdx.x;
+  uint64_t *table = p.pool + (size_t)blockIdx.x * p.pool_words;
+  const Muls mu{p.mul_one, p.mul_two, p.mul_four, p.mul_h31, p.mul_h30};
+  extern __shared__ __align__(16) uint32_t batch_smem[];
+  uint32_t *mask_rows = batch_smem;
+  uint32_t *csm = mask_rows + MaskTable<W>::kWords;
+  uint32_t *task_word = csm + CtaWalkSmem<W>::kWords;  // [0] task index, [1] its problem's stop flag
+  int rows_L = 0;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(p.task_next, 1u);
+      task_word[0] = t;
+      task_word[1] = t < p.n_tasks ? (uint32_t)load_volatile(p.ps.done + p.tasks[t].problem) : 0u;
+    }
+    __syncthreads();
+    const uint32_t t = task_word[0];
+    const bool skip = task_word[1] != 0u;
+    __syncthreads();  // every thread has read the task before thread 0 takes the next
+    if (t >= p.n_tasks) break;
+    if (skip) continue;  // a problem stopped by an earlier round needs none of its later rounds
+    const BatchTask task = p.tasks[t];
+    const BatchProblem pr = p.probs[task.problem];
+    const uint32_t walk = task.chunk;
+    const size_t words = (size_t)pr.cap * (size_t)pr.kw64;  // even: cap >= 64
+    uint4 *t4 = reinterpret_cast<uint4 *>(table);
+    for (size_t i = (size_t)tid; i < words / 2; i += kWalkBlock) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    const Geometry g = make_geometry(pr.L, T);
+    if (pr.L != rows_L) {  // block-uniform: every thread read the same task
+      fill_mask_rows<W>(g, mask_rows, tid, kWalkBlock);
+      rows_L = pr.L;
+    }
+    __syncthreads();  // the zeroed table and the mask table are visible to the block
+    WalkOut<NS> o;
+    run_walk_cta<W, T, kTopK>(g, mu, mask_rows, csm, pr.seed, walk, task.round, pr.walk_len, table, pr.cap,
+                              pr.kw64, 0, nullptr, p.err, o);
+    if (tid == 0) {
+      uint32_t *k = p.rec.keys + (p.rec.key_base[task.rec] + walk) * kKeyWords;
+#pragma unroll
+      for (int w = 0; w < kKeyWords; ++w) k[w] = w < NS ? o.best_key[w] : 0u;
+      atomicMin(&p.rec.best[task.rec], ((unsigned long long)(uint32_t)o.bestE << 32) | walk);
+      atomicAdd(&p.rec.evals[task.rec], (unsigned long long)g.D * (unsigned long long)(o.moves + o.stuck));
+      atomicAdd(&p.rec.planes[task.rec], (unsigned long long)o.planes);
+      __threadfence();
+      if (atomicSub(&p.rec.left[task.rec], 1u) == 1u) {
+        __threadfence();
+        try_finalize(p.rec, p.ps, (int)task.problem);
+      }
+    }
   }
 }
 

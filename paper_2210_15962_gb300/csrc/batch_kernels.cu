@@ -71,6 +71,11 @@ int batch_resident_lanes(int W, int block, int unroll) {
 }
 int batch_resident_warps(int W, int block) { return dispatch_resident(W, block, kBatchWarp); }
 
+cudaError_t launch_batch_cta(int W, const BatchKernelParams &p, cudaStream_t s, int max_blocks) {
+  return dispatch_launch(W, kWalkBlock, p, s, nullptr, max_blocks, kBatchCta);
+}
+int batch_resident_ctas(int W) { return dispatch_resident(W, kWalkBlock, kBatchCta); }
+
 // After a launch: finalize what the in-kernel finalization left (normally
 // nothing), one thread per listed problem.
 __global__ void batch_finalize_kernel(const int32_t *problems, int n, const RoundRecords rec, const ProblemState ps) {

@@ -201,7 +201,7 @@ def test_batch_rejects_bad_problems(lib, bad):
 
 def test_batch_rejects_bad_options(lib):
     import paper_2210_15962_gb300 as m
-    for kw in [dict(block_threads=48), dict(block_threads=512), dict(table_factor_x10=5), dict(walk_mode=3)]:
+    for kw in [dict(block_threads=48), dict(block_threads=512), dict(table_factor_x10=5), dict(walk_mode=4)]:
         with pytest.raises(m.LabsError) as ei:
             m.Batch([(27, 64, 100, 1, 1000)], **kw)
         assert ei.value.status == m.LABS_EINVAL

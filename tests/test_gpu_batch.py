@@ -189,8 +189,23 @@ def test_batch_warp_mode_vs_oracle_every_class(m):
             assert b.shape(W)["warp_per_walk"]
 
 
+def test_batch_cta_mode_vs_oracle_every_class(m):
+    # one walk per CTA of 128 threads (its warps split each walk's flips and
+    # merge their candidates in shared memory) in every class, budget and
+    # target problems, against the oracle
+    probs = list(CLASS_PROBS)
+    tgt = target_after_rounds(161, 40, 120, 401, 2)
+    probs.append((161, 40, 120, 401, 10 ** 12, tgt))
+    with m.Batch(probs, walk_mode=3, rounds_per_launch=2) as b:
+        b.run()
+        check_oracle(probs, b.results())
+        for W in {((p[0] - 1) // 2 + 31) // 32 for p in probs}:
+            sh = b.shape(W)
+            assert sh["cta_per_walk"] and sh["walk_unit"] == "cta"
+
+
 def test_batch_autotune_offers_warp_mode(m):
-    # few walks per class: the autotuner times lane and warp mode on the
+    # few walks per class: the autotuner times lane, warp and CTA mode on the
     # first launch's tasks; whatever it picks, the results are the oracle's
     probs = [(301, 64, 300, 501, 64 * 300 * 151), (449, 48, 200, 502, 48 * 200 * 225 * 2)]
     with m.Batch(probs, autotune=True) as b:
@@ -205,13 +220,13 @@ def test_batch_rounds_after_a_stop_are_never_counted(m):
     # every problem reaches its target in its first round while 16 of its
     # rounds are issued in the launch: whatever order the chunks finish in
     # around the stopping round's finalization, the later rounds add neither
-    # evaluations nor rounds (Algorithm 1), in lane and in warp mode
+    # evaluations nor rounds (Algorithm 1), in lane, warp and CTA mode
     probs = []
     for i in range(48):
         L = (61, 121, 161)[i % 3]
         walks, wl, seed = 64, 120, 800 + i
         probs.append((L, walks, wl, seed, 10 ** 12, target_after_rounds(L, walks, wl, seed, 1)))
-    for mode in (1, 2):
+    for mode in (1, 2, 3):
         with m.Batch(probs, rounds_per_launch=16, walk_mode=mode) as b:
             b.run()
             res = b.results()
