@@ -214,7 +214,8 @@ typedef struct labs_batch_opts {
                                 flip loop unrolled once or twice, or one walk per warp or per
                                 CTA of 128 threads (both offered while every problem has <= 4096
                                 walks) */
-  int32_t block_threads;     /* walks per CTA (32..256, multiple of 32); 0 = 128 or autotuned */
+  int32_t block_threads;     /* walks per CTA (32..256, multiple of 32) in lane mode, threads per
+                                CTA in warp mode (CTA mode: always 128); 0 = 128 or autotuned */
   int32_t table_factor_x10;  /* visited-table slots per pivot x 10 (>= 12); 0 = 30 or autotuned */
   int32_t rounds_per_launch; /* rounds a problem with a target gets per launch; 0 = 4 */
   int32_t walk_mode;         /* 0: one walk per lane, or what autotune picks; 1: one walk per lane;

@@ -831,7 +831,7 @@ extern "C" labs_status labs_batch_shape(const labs_batch *b, int32_t W, int32_t 
   if (!b) return LABS_EINVAL;
   for (auto &c : b->cls) {
     if (c.W != W) continue;
-    if (block_threads) *block_threads = c.block;
+    if (block_threads) *block_threads = c.cta ? kWalkBlock : c.block;  // a CTA-mode block is one walk's
     if (table_factor_x10) *table_factor_x10 = c.factor_x10;
     if (resident_walks) *resident_walks = c.resident;
     if (warp_per_walk) *warp_per_walk = c.cta ? 2 : (c.warp ? 1 : 0);
