@@ -13,7 +13,8 @@
 // step; its scan, move, plane-count, start and table functions are the
 // kernels' own.  force_tp = 1 scans with all T digit planes instead of the
 // fewest that hold every C; pmax is the widest lag-word class that scans in
-// pattern runs (4 in the per-round kernel, 2 in the persistent batch kernel).
+// pattern runs (3 in the per-round and the persistent batch kernels; 2 and 4
+// exercise the same templates one class narrower and wider).
 #include <cstdint>
 #include <cstdio>
 #include <iostream>
@@ -272,7 +273,7 @@ int main() {
   while (std::getline(std::cin, line)) {
     std::istringstream in(line);
     std::string space;
-    int L = 0, walk_len = 0, force_tp = 0, pmax = 4;
+    int L = 0, walk_len = 0, force_tp = 0, pmax = 3;
     unsigned long long seed = 0;
     unsigned round = 0, walk = 0;
     if (!(in >> space >> L >> seed >> round >> walk >> walk_len)) continue;
@@ -281,8 +282,9 @@ int main() {
     if (space == "skew") {
       in >> pmax;
       if (L < kLMin || L > kLMax || (L % 2) == 0) return 2;
-      r = pmax == 2 ? skew_by_class<2>(L, seed, round, walk, walk_len, force_tp != 0)
-                    : skew_by_class<4>(L, seed, round, walk, walk_len, force_tp != 0);
+      r = pmax == 2   ? skew_by_class<2>(L, seed, round, walk, walk_len, force_tp != 0)
+          : pmax == 3 ? skew_by_class<3>(L, seed, round, walk, walk_len, force_tp != 0)
+                      : skew_by_class<4>(L, seed, round, walk, walk_len, force_tp != 0);
     } else if (space == "incr") {
       if (L < kLMin || L > kLMax || (L % 2) == 0) return 2;
       r = incr_by_class(L, seed, round, walk, walk_len);

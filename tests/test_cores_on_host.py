@@ -72,8 +72,8 @@ def test_skew_cores_match_the_oracle(cores, oracle_mod):
         W = ((L - 1) // 2 + 31) // 32
         for walk in range(2):
             for force_tp in (0, 1):
-                # the per-round kernel's pattern runs (pmax 4) and the batch kernel's (pmax 2)
-                for pmax in ((4, 2) if 2 <= W <= 4 else (4,)):
+                # the kernels' pattern runs (pmax 3) and the same templates one class narrower and wider
+                for pmax in ((3, 4, 2) if 2 <= W <= 4 else (3,)):
                     cases.append(("skew", L, 11, 2, walk, walk_len_for(L), force_tp, pmax))
     for case, got in zip(cases, run_cases(cores, cases)):
         compare(oracle_mod, case, got, full=False)
