@@ -164,7 +164,8 @@ labs_status labs_walks(int32_t L, const uint64_t *seeds, int32_t n_seeds, int32_
 
 /* Device bytes labs_walks needs to run all walks of a round at once (a
  * smaller opts->workspace makes it run each round in several launches; the
- * minimum is what one warp of walks needs). */
+ * minimum is what one warp of walks needs).  0 for arguments labs_walks
+ * rejects; SIZE_MAX if the size does not fit in a size_t. */
 size_t labs_walks_workspace_size(int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len);
 
 /* One round (Eq. 4) of walks 0..n_walks-1 of the problem `seed`, with
@@ -273,7 +274,7 @@ typedef struct labs_serve_cfg {
   int32_t max_active;        /* requests admitted at once (slots), default 64 */
   int32_t max_L;             /* largest L accepted (sizes the table pools), default 301 */
   int32_t max_walks;         /* largest walks per round accepted, default 2048 */
-  int32_t max_walk_len;      /* largest walk length accepted, 0 = 8 * (max_L + 1) / 2 */
+  int32_t max_walk_len;      /* largest walk length accepted (<= 2^26), 0 = 8 * (max_L + 1) / 2 */
   int32_t rounds_per_launch; /* rounds each admitted request gets per launch, default 4 (two
                                 launches are in flight: the next is queued while one runs); a
                                 launch that would leave SMs idle gives requests further rounds,

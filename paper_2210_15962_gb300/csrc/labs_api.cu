@@ -305,10 +305,15 @@ extern "C" labs_status labs_to_hex(const int8_t *seq, int32_t L, char *out, size
 }
 
 static size_t workspace_size(int32_t space, int32_t L, int32_t n_seeds, int32_t walks_per_seed, int32_t walk_len) {
-  if (!valid_space_L(space, L) || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1) return 0;
+  // the argument rules of labs_walks
+  if (!valid_space_L(space, L) || n_seeds < 1 || walks_per_seed < 1 || walk_len < 1 || walk_len > (1 << 26) ||
+      (uint64_t)n_seeds * (uint64_t)walks_per_seed > (1ull << 31))
+    return 0;
   const size_t n_walks = (size_t)n_seeds * (size_t)walks_per_seed;
   const size_t tb = (size_t)table_cap(walk_len) * key_words64(key_bits(space, L)) * 8;
   Buffers b;
+  const size_t fixed = carve(b, nullptr, L, n_seeds, n_walks, 0, tb);
+  if (tb > (SIZE_MAX - fixed) / n_walks) return SIZE_MAX;  // not representable: more than any device holds
   return carve(b, nullptr, L, n_seeds, n_walks, n_walks, tb);
 }
 
@@ -645,7 +650,8 @@ static labs_status saw_round_impl(int32_t space, int32_t L, uint64_t seed, uint3
   if (!valid_space_L(space, L) || n_walks < 1 || walk_len < 1 || walk_len > (1 << 26) || recheck_every < 0 ||
       kernel < 0 || kernel > max_kernel)
     return LABS_EINVAL;
-  if (trace_flips && (trace_begin < 0 || trace_count < 0 || trace_begin + trace_count > n_walks)) return LABS_EINVAL;
+  if (trace_flips && (trace_begin < 0 || trace_count < 0 || (int64_t)trace_begin + trace_count > n_walks))
+    return LABS_EINVAL;
   if (visited_keys && (visited_walk < 0 || visited_walk >= n_walks || visited_cap < 0 || !visited_count))
     return LABS_EINVAL;
   const int D = key_bits(space, L);

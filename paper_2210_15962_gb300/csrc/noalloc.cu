@@ -86,7 +86,8 @@ extern "C" labs_status labs_saw_round_noalloc(int32_t L, uint64_t seed, uint32_t
   const size_t o_seed = take(sizeof(uint64_t));
   const size_t o_err = take(sizeof(int32_t));
   const size_t o_tables = take(0);
-  if (o_tables + table_bytes * (size_t)n_walks > kScratchBytes) return LABS_ENOMEM;  // does not fit
+  // does not fit (compared by division: the product can exceed 64 bits)
+  if (o_tables > kScratchBytes || table_bytes > (kScratchBytes - o_tables) / (size_t)n_walks) return LABS_ENOMEM;
 
   cudaStream_t s = (cudaStream_t)stream;
   void *base = nullptr;

@@ -801,6 +801,7 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
   if (cfg.max_L == 0) cfg.max_L = 301;
   if (cfg.max_active <= 0 || cfg.max_active > 4096 || cfg.max_L < LABS_L_MIN || cfg.max_L > LABS_L_MAX ||
       !(cfg.max_L & 1) || cfg.max_walks <= 0 || cfg.max_walks > (1 << 20) || cfg.max_walk_len < 0 ||
+      cfg.max_walk_len > (1 << 26) ||
       cfg.rounds_per_launch <= 0 || cfg.rounds_per_launch > 64 || cfg.block_threads < 32 ||
       cfg.block_threads > 256 || cfg.block_threads % 32 || cfg.mem_bytes < 2 * kAlign || cfg.walk_mode < 0 ||
       cfg.walk_mode > 2 || (cfg.walk_mode == 2 && cfg.max_walks > kWarpModeMaxWalks))
@@ -971,7 +972,8 @@ extern "C" labs_status labs_serve_create(const labs_serve_cfg *cfg_in, labs_serv
 extern "C" labs_status labs_serve_submit(labs_server *sv, const labs_problem *req, uint64_t *ticket) {
   if (!sv || !req || !ticket) return LABS_EINVAL;
   const labs_problem &p = *req;
-  if (p.L < LABS_L_MIN || p.L > LABS_L_MAX || !(p.L & 1) || p.walks < 1 || p.walk_len < 1 || p.step_budget < 1)
+  if (p.L < LABS_L_MIN || p.L > LABS_L_MAX || !(p.L & 1) || p.walks < 1 || p.walk_len < 1 ||
+      p.walk_len > (1 << 26) || p.step_budget < 1)
     return LABS_EINVAL;
   // requests that can never be admitted: above the server's limits, or a
   // launch over this request alone does not fit half the arena

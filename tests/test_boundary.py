@@ -118,6 +118,26 @@ def test_walks_rejects_bad_sizes(lib):
         assert lib.labs_walks(27, p(seeds), 1, 4, 8, 100, p(seq), p(E), ctypes.byref(o), None) == m.LABS_EINVAL
 
 
+def test_size_arithmetic_does_not_wrap(lib):
+    # sizes whose byte counts exceed 64 bits are refused, never wrapped to a
+    # small number (argument checks only: no CUDA call is reached)
+    import paper_2210_15962_gb300 as m
+    big_walks, big_len = (1 << 31) - 1, 1 << 26
+    assert lib.labs_walks_workspace_size(511, 1, big_walks, big_len) == 2 ** 64 - 1
+    assert lib.labs_walks_workspace_size(121, 1, 4, big_len + 1) == 0    # labs_walks rejects it
+    assert lib.labs_walks_workspace_size(121, 65536, 65536, 8) == 0      # more than 2^31 walks
+    assert lib.labs_walks_workspace_size(121, 1, 4, 8) > 0
+    fake = ctypes.c_void_p(16)  # never dereferenced: the call returns before touching its buffers
+    assert lib.labs_saw_round_noalloc(511, 1, 0, big_walks, big_len, fake, fake, None, None, None) == m.LABS_ENOMEM
+    assert lib.labs_saw_round_noalloc(27, 1, 0, 4, big_len + 1, fake, fake, None, None, None) == m.LABS_EINVAL
+    t = np.zeros(64, dtype=np.int32)
+    assert lib.labs_saw_round(27, 1, 0, 4, 8, 0, None, None, None, None, None, m._ptr(t), (1 << 31) - 1, 2, -1,
+                              None, 0, None, 0) == m.LABS_EINVAL
+    with pytest.raises(m.LabsError) as ei:
+        m.Server(max_walk_len=(1 << 26) + 1)
+    assert ei.value.status == m.LABS_EINVAL
+
+
 def test_energy_rejects_bad_args(lib):
     import paper_2210_15962_gb300 as m
     assert lib.labs_energy(None, 5) == m.LABS_EINVAL
