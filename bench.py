@@ -294,7 +294,9 @@ def measure_batched(args, rank, steps, warmup):
     import paper_2210_15962_gb300 as pkg
     from paper_2210_15962_gb300 import workloads
     wl = workloads.batched_instances(n=args.instances, walks=args.batch_walks)
-    probs = [(p.L, p.walks, p.walk_len, p.seed + 1000 * rank, p.step_budget) for p in wl.problems]
+    # --batch-walk-len > 0 replaces the 8*D walk length (a smaller device footprint for profiler captures)
+    probs = [(p.L, p.walks, args.batch_walk_len or p.walk_len, p.seed + 1000 * rank, p.step_budget)
+             for p in wl.problems]
     stream = torch.cuda.Stream()
     b = pkg.Batch(probs, use_graph=True, autotune=True, stream=stream)
     for _ in range(warmup):
@@ -339,7 +341,7 @@ def measure_batched(args, rank, steps, warmup):
         "value": ev / dev_s, "unit": "neighbour_evals/s", "steps": steps, "ms_per_step": dev_s * 1e3 / steps,
         "evals": ev, "seconds": dev_s, "launches": launches, "walk_launches": wlaunch,
         "config": {"workload": wl.name, "instances": len(probs), "walks": args.batch_walks,
-                   "L_range": [min(Ls), max(Ls)], "walk_len": "8*D",
+                   "L_range": [min(Ls), max(Ls)], "walk_len": args.batch_walk_len or "8*D",
                    "budget_range": [min(p[4] for p in probs), max(p[4] for p in probs)],
                    "path": "batched persistent kernel, CUDA graph replay, autotuned shapes",
                    "shapes": {str(k): v for k, v in shapes.items()}},
@@ -828,6 +830,7 @@ def main():
     ap.add_argument("--capacity-requests", type=int, default=0, help="0: all of the stream's requests")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)
+    ap.add_argument("--batch-walk-len", type=int, default=0, help="batched workload walk length, 0: 8*D")
     ap.add_argument("--plain-instances", type=int, default=64)
     args = ap.parse_args()
     world, rank, local = dist_setup()
