@@ -303,6 +303,32 @@ def test_batch_and_solve_round_logic(oracle_mod):
     assert int(r2["rounds"][0]) == 1
 
 
+def test_round_boundaries_and_ties(oracle_mod):
+    # Algorithm 1 with the budget and the target read at round boundaries: a
+    # problem stops once its evaluations reach the budget (not only once they
+    # pass it) or once its best is at or below the target; among equal
+    # energies the earliest (round, walk) wins
+    L, walks, wl = 19, 16, 8
+    b0 = oracle_mod.walk_batch(L, 4, 0, 0, walks, wl)
+    b1 = oracle_mod.walk_batch(L, 4, 1, 0, walks, wl)
+    per_round = int(b0["evals"].sum())
+    r = oracle_mod.solve(L, [4], walks, wl, per_round)
+    assert int(r["rounds"][0]) == 1 and int(r["evals"][0]) == per_round
+    best0 = int(b0["best_E"].min())
+    r = oracle_mod.solve(L, [4], walks, wl, 3 * per_round, target_E=best0)
+    assert int(r["rounds"][0]) == 1
+    # ties: several walks share the best energy with different sequences (checked
+    # here so that the pin keeps its meaning), and the first of them wins
+    allE = list(b0["best_E"]) + list(b1["best_E"])
+    best = min(allE)
+    tied = [i for i, e in enumerate(allE) if e == best]
+    seqs = [(b0 if i < walks else b1)["best_seq"][i % walks] for i in tied]
+    assert len(tied) >= 2 and any(not np.array_equal(seqs[0], q) for q in seqs[1:])
+    r = oracle_mod.solve(L, [4], walks, wl, per_round + 1)
+    assert int(r["rounds"][0]) == 2 and int(r["best_E"][0]) == best
+    assert np.array_equal(r["best_seq"][0], seqs[0])
+
+
 # ------------------------------------------- predictive model (Section 4.1, Eq. 6-7)
 # lambda(L) is the paper's printed fit; the pins check Eq. 6 and Eq. 7 against
 # each other, against properties of the exponential distribution, and the fit
