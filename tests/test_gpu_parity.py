@@ -185,6 +185,29 @@ def test_solve_multi_seed_multi_round_and_target(m, orc):
     assert list(g3["rounds"]) == [2, 2, 2]
 
 
+def test_round_boundaries_and_ties_match_oracle(m, orc):
+    # a budget of exactly one round's evaluations, a target equal to the first
+    # round's best, and several walks tied at the best energy with different
+    # sequences (the first wins): the round loop's readings, as in the oracle
+    for L, walks, wl, seed in [(19, 16, 8, 4), (121, 64, 100, 6)]:
+        b0 = orc.walk_batch(L, seed, 0, 0, walks, wl, threads=8)
+        per_round = int(b0["evals"].sum())
+        best0 = int(b0["best_E"].min())
+        for budget, target in [(per_round, -1), (3 * per_round, best0), (per_round + 1, -1)]:
+            g = m.labs_walks(L, [seed], walks, wl, budget, target_E=target)
+            o = orc.solve(L, [seed], walks, wl, budget, target_E=target, threads=8)
+            assert list(g["rounds"]) == list(o["rounds"]), (L, budget, target)
+            assert np.array_equal(g["evals"].astype(np.int64), o["evals"].astype(np.int64))
+            assert np.array_equal(g["best_E"], o["best_E"]) and np.array_equal(g["best_seq"], o["best_seq"])
+        if L == 19:
+            assert list(m.labs_walks(L, [seed], walks, wl, per_round)["rounds"]) == [1]
+            tied = [w for w in range(walks) if int(b0["best_E"][w]) == best0]
+            assert len(tied) >= 2 and any(not np.array_equal(b0["best_seq"][tied[0]], b0["best_seq"][w])
+                                          for w in tied[1:])
+            g = m.labs_walks(L, [seed], walks, wl, per_round)
+            assert np.array_equal(g["best_seq"][0], b0["best_seq"][tied[0]])
+
+
 def test_chunked_workspace_and_device_buffers_match(m):
     import torch
     L, walks, wl = 61, 200, 400
