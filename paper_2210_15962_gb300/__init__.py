@@ -271,6 +271,27 @@ def labs_model_budget(L: int, P: float) -> int:
     return int(load().labs_model_budget(L, P))
 
 
+def _cuda_arg(t, dtypes, numel, what, name, optional=False):
+    """Device pointer of a caller-owned tensor after checking that the library
+    can use it: a contiguous CUDA tensor on the current device, of one of
+    `dtypes` (None: any), with at least `numel` elements.  Anything else raises
+    LabsError(LABS_EINVAL) before the library is called, since the library
+    cannot check a raw device pointer and would write past a short buffer."""
+    import torch
+    if t is None:
+        if optional:
+            return None
+        raise LabsError(LABS_EINVAL, "%s (%s is required)" % (what, name))
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.is_contiguous()
+          and (dtypes is None or t.dtype in dtypes) and t.numel() >= numel)
+    if not ok:
+        kind = "/".join(str(d) for d in dtypes) if dtypes else "any-type"
+        raise LabsError(LABS_EINVAL, "%s (%s must be a contiguous %s CUDA tensor on the current device with at "
+                                     "least %d elements)" % (what, name, kind, numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def labs_energy(seq) -> int:
     """Eq. 1 energy of one +-1 sequence (host array), computed on the GPU."""
     s = np.ascontiguousarray(seq, dtype=np.int8)
@@ -283,8 +304,9 @@ def labs_energy(seq) -> int:
 def labs_energy_batch(seqs, stream=None, check: bool = True):
     """Eq. 1 energies of a (n, L) int8 CUDA tensor, returned as an int64 CUDA tensor."""
     import torch
-    if not (isinstance(seqs, torch.Tensor) and seqs.is_cuda and seqs.dtype == torch.int8 and seqs.dim() == 2):
-        raise ValueError("seqs must be a 2-D int8 CUDA tensor")
+    if not (isinstance(seqs, torch.Tensor) and seqs.is_cuda and seqs.dtype == torch.int8 and seqs.dim() == 2
+            and seqs.device.index == torch.cuda.current_device()):
+        raise ValueError("seqs must be a 2-D int8 CUDA tensor on the current device")
     seqs = seqs.contiguous()
     out = torch.empty(seqs.shape[0], dtype=torch.int64, device=seqs.device)
     st = stream if stream is not None else torch.cuda.current_stream(seqs.device)
@@ -306,7 +328,7 @@ def make_opts(stream=None, device_buffers=False, recheck_every=0, target_E=-1, m
     o.max_rounds = int(max_rounds)
     o.kernel = int(kernel)
     if workspace is not None:
-        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.workspace = _cuda_arg(workspace, None, 1, "labs_walks", "workspace")
         o.workspace_bytes = workspace.numel() * workspace.element_size()
     if evals_per_seed is not None:
         o.evals_per_seed = ctypes.c_void_p(evals_per_seed.data_ptr() if hasattr(evals_per_seed, "data_ptr")
@@ -362,15 +384,24 @@ def labs_walks_device(L: int, seeds, walks_per_seed: int, walk_len: int, step_bu
                       space: str = "skew") -> dict:
     """labs_walks on device-resident buffers (torch CUDA tensors): seeds int64/uint64 (n,),
     best_seq int8 (n, L), best_E int64 (n,).  Stream-ordered; returns the call's stats."""
+    import torch
     full = _space(space)
+    what = "labs_walks_full" if full else "labs_walks"
+    n = seeds.numel() if isinstance(seeds, torch.Tensor) else 0
+    if n < 1 or L < 1:
+        raise LabsError(LABS_EINVAL, what)
+    i64 = (torch.int64, torch.uint64) if hasattr(torch, "uint64") else (torch.int64,)
+    sd = _cuda_arg(seeds, i64, n, what, "seeds")
+    bs = _cuda_arg(best_seq, (torch.int8,), n * L, what, "best_seq")
+    be = _cuda_arg(best_E, (torch.int64,), n, what, "best_E")
+    _cuda_arg(evals_per_seed, i64, n, what, "evals_per_seed", optional=True)
+    _cuda_arg(rounds_per_seed, (torch.int32,), n, what, "rounds_per_seed", optional=True)
     o = make_opts(stream=stream, device_buffers=True, recheck_every=recheck_every, target_E=target_E,
                   max_rounds=max_rounds, workspace=workspace, evals_per_seed=evals_per_seed,
                   rounds_per_seed=rounds_per_seed, kernel=kernel)
     stats = labs_stats()
     fn = load().labs_walks_full if full else load().labs_walks
-    _check(fn(L, ctypes.c_void_p(seeds.data_ptr()), seeds.numel(), walks_per_seed, walk_len, step_budget,
-              ctypes.c_void_p(best_seq.data_ptr()), ctypes.c_void_p(best_E.data_ptr()), ctypes.byref(o),
-              ctypes.byref(stats)), "labs_walks_full" if full else "labs_walks")
+    _check(fn(L, sd, n, walks_per_seed, walk_len, step_budget, bs, be, ctypes.byref(o), ctypes.byref(stats)), what)
     return stats.as_dict()
 
 
@@ -419,25 +450,13 @@ def labs_saw_round_noalloc(L: int, seed: int, round_: int, n_walks: int, walk_le
     walk_stuck: int32 (n_walks,) or None; all contiguous CUDA tensors on the current device.  Anything
     else raises LabsError(LABS_EINVAL) before the library is called."""
     import torch
-    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
-
-    def p(t, dtype, numel, name, optional=False):
-        if t is None:
-            if optional:
-                return None
-            raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc (%s is required)" % name)
-        ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == dtype
-              and t.is_contiguous() and t.numel() >= numel)
-        if not ok:
-            raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc (%s must be a contiguous %s CUDA tensor on the "
-                                         "current device with at least %d elements)" % (name, dtype, numel))
-        return ctypes.c_void_p(t.data_ptr())
+    what = "labs_saw_round_noalloc"
     if n_walks < 1 or L < 1:
-        raise LabsError(LABS_EINVAL, "labs_saw_round_noalloc")
-    args = (p(walk_best_E, torch.int64, n_walks, "walk_best_E"),
-            p(walk_best_seq, torch.int8, n_walks * L, "walk_best_seq"),
-            p(walk_moves, torch.int32, n_walks, "walk_moves", True),
-            p(walk_stuck, torch.int32, n_walks, "walk_stuck", True))
+        raise LabsError(LABS_EINVAL, what)
+    args = (_cuda_arg(walk_best_E, (torch.int64,), n_walks, what, "walk_best_E"),
+            _cuda_arg(walk_best_seq, (torch.int8,), n_walks * L, what, "walk_best_seq"),
+            _cuda_arg(walk_moves, (torch.int32,), n_walks, what, "walk_moves", optional=True),
+            _cuda_arg(walk_stuck, (torch.int32,), n_walks, what, "walk_stuck", optional=True))
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
     _check(load().labs_saw_round_noalloc(L, seed, round_, n_walks, walk_len, *args, st), "labs_saw_round_noalloc")
 

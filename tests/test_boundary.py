@@ -138,6 +138,22 @@ def test_size_arithmetic_does_not_wrap(lib):
     assert ei.value.status == m.LABS_EINVAL
 
 
+def test_device_entry_points_refuse_host_tensors(lib):
+    # the device-buffer bindings check their tensors before the library sees a pointer
+    import torch
+    import paper_2210_15962_gb300 as m
+    sd = torch.tensor([1], dtype=torch.int64)
+    with pytest.raises(m.LabsError) as ei:
+        m.labs_walks_device(27, sd, 4, 8, 100, torch.zeros((1, 27), dtype=torch.int8), torch.zeros(1, dtype=torch.int64))
+    assert ei.value.status == m.LABS_EINVAL
+    with pytest.raises(m.LabsError) as ei:
+        m.labs_saw_round_noalloc(27, 1, 0, 4, 8, torch.zeros(4, dtype=torch.int64), torch.zeros(4 * 27, dtype=torch.int8))
+    assert ei.value.status == m.LABS_EINVAL
+    with pytest.raises(m.LabsError) as ei:
+        m.make_opts(workspace=torch.zeros(64, dtype=torch.uint8))
+    assert ei.value.status == m.LABS_EINVAL
+
+
 def test_energy_rejects_bad_args(lib):
     import paper_2210_15962_gb300 as m
     assert lib.labs_energy(None, 5) == m.LABS_EINVAL

@@ -185,6 +185,32 @@ def test_solve_multi_seed_multi_round_and_target(m, orc):
     assert list(g3["rounds"]) == [2, 2, 2]
 
 
+def test_device_buffer_binding_rejects_bad_buffers(m):
+    # the binding refuses device buffers the library would write out of bounds
+    import torch
+    n, L = 2, 61
+    sd = torch.tensor([1, 2], dtype=torch.int64, device="cuda")
+    bs = torch.zeros((n, L), dtype=torch.int8, device="cuda")
+    be = torch.zeros(n, dtype=torch.int64, device="cuda")
+    bad = [
+        (sd, bs, torch.zeros(n, dtype=torch.int32, device="cuda")),        # wrong dtype
+        (sd, torch.zeros((n, L - 1), dtype=torch.int8, device="cuda"), be),  # too short
+        (sd, bs, torch.zeros(n, dtype=torch.int64)),                        # host tensor
+        (sd, torch.zeros((L, n), dtype=torch.int8, device="cuda").t(), be),  # not contiguous
+        (sd.to(torch.int32), bs, be),                                       # seeds of the wrong width
+    ]
+    for s_, q_, e_ in bad:
+        with pytest.raises(m.LabsError) as ei:
+            m.labs_walks_device(L, s_, 32, 50, 10 ** 6, q_, e_)
+        assert ei.value.status == m.LABS_EINVAL
+    with pytest.raises(m.LabsError):
+        m.labs_walks_device(L, sd, 32, 50, 10 ** 6, bs, be, workspace=torch.zeros(1024, dtype=torch.uint8))
+    m.labs_walks_device(L, sd, 32, 50, 10 ** 6, bs, be)
+    torch.cuda.synchronize()
+    ref = m.labs_walks(L, [1, 2], 32, 50, 10 ** 6)
+    assert np.array_equal(be.cpu().numpy(), ref["best_E"]) and np.array_equal(bs.cpu().numpy(), ref["best_seq"])
+
+
 def test_round_boundaries_and_ties_match_oracle(m, orc):
     # a budget of exactly one round's evaluations, a target equal to the first
     # round's best, and several walks tied at the best energy with different
