@@ -298,7 +298,7 @@ def measure_batched(args, rank, steps, warmup):
     probs = [(p.L, p.walks, args.batch_walk_len or p.walk_len, p.seed + 1000 * rank, p.step_budget)
              for p in wl.problems]
     stream = torch.cuda.Stream()
-    b = pkg.Batch(probs, use_graph=True, autotune=True, stream=stream)
+    b = pkg.Batch(probs, use_graph=True, autotune=True, walk_mode=args.batch_walk_mode, stream=stream)
     for _ in range(warmup):
         b.run()
     torch.cuda.synchronize()
@@ -344,6 +344,7 @@ def measure_batched(args, rank, steps, warmup):
                    "L_range": [min(Ls), max(Ls)], "walk_len": args.batch_walk_len or "8*D",
                    "budget_range": [min(p[4] for p in probs), max(p[4] for p in probs)],
                    "path": "batched persistent kernel, CUDA graph replay, autotuned shapes",
+                   "walk_mode": ["autotuned", "lane", "warp", "CTA"][args.batch_walk_mode],
                    "shapes": {str(k): v for k, v in shapes.items()}},
         "roofline": popc_roofline(needed * steps, kms / 1e3, kernel="batch_kernel<W> (all classes, concurrent)",
                                   kernel_ms_per_run=kms / steps,
@@ -831,6 +832,8 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--batch-walks", type=int, default=2048)
     ap.add_argument("--batch-walk-len", type=int, default=0, help="batched workload walk length, 0: 8*D")
+    ap.add_argument("--batch-walk-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="batched workload: 0 autotuned, 1 lane, 2 warp, 3 CTA per walk")
     ap.add_argument("--plain-instances", type=int, default=64)
     args = ap.parse_args()
     world, rank, local = dist_setup()
