@@ -298,7 +298,9 @@ def measure_batched(args, rank, steps, warmup):
     probs = [(p.L, p.walks, args.batch_walk_len or p.walk_len, p.seed + 1000 * rank, p.step_budget)
              for p in wl.problems]
     stream = torch.cuda.Stream()
-    b = pkg.Batch(probs, use_graph=True, autotune=True, walk_mode=args.batch_walk_mode, stream=stream)
+    # a fixed block size and table factor (both given) replace the autotuner's choice
+    b = pkg.Batch(probs, use_graph=True, autotune=True, walk_mode=args.batch_walk_mode,
+                  block_threads=args.batch_block, table_factor_x10=args.batch_table_factor, stream=stream)
     for _ in range(warmup):
         b.run()
     torch.cuda.synchronize()
@@ -834,6 +836,9 @@ def main():
     ap.add_argument("--batch-walk-len", type=int, default=0, help="batched workload walk length, 0: 8*D")
     ap.add_argument("--batch-walk-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="batched workload: 0 autotuned, 1 lane, 2 warp, 3 CTA per walk")
+    ap.add_argument("--batch-block", type=int, default=0, help="batched workload: threads per CTA, 0 autotuned")
+    ap.add_argument("--batch-table-factor", type=int, default=0,
+                    help="batched workload: visited-table slots per pivot x10, 0 autotuned")
     ap.add_argument("--plain-instances", type=int, default=64)
     args = ap.parse_args()
     world, rank, local = dist_setup()
