@@ -36,8 +36,10 @@ struct MinBlocksFull {
 // Flips of the scan's loop unrolled per iteration in the one-walk-per-lane
 // kernel: two at four to seven words (independent popcount chains for the
 // few resident warps: +3% at L=223, +4%, +3% and +2% at L=301, 383, 449),
-// one elsewhere (two lost 1.5% at two words, 30% at three, where the
-// registers do not hold a second flip's window, and 1% at eight)
+// one elsewhere (two lost 1.5% at two words, 30% at three, and 1% at
+// eight; at three words, the widest class with pattern-specialised scan
+// loops, the unrolled code no longer fits the instruction caches: the same
+// instructions and registers, four times the instruction-fetch stalls)
 template <int W>
 struct ScanUnroll {
   static constexpr int value = (W >= 4 && W <= 7) ? 2 : 1;
