@@ -105,6 +105,33 @@ def test_many_instances_config3_shape(m):
         check_same(m, probs, b.results())
 
 
+def test_full_size_batched_workload_vs_oracle_sampled(m):
+    # the batched workload at its full size and in the bench's launch
+    # configuration (64 instances of odd L in [101, 223], 2048 walks of 8*D
+    # steps, log-uniform budgets, CUDA graph, autotuned shapes); the instance
+    # the oracle solves fastest (L=117, two rounds of 2048 walks) is compared
+    # with it directly, the next seven with one labs_walks each
+    import os
+    import oracle
+    from paper_2210_15962_gb300 import workloads
+    wl = workloads.batched_instances(n=64, walks=2048)
+    probs = [(p.L, p.walks, p.walk_len, p.seed, p.step_budget) for p in wl.problems]
+    with m.Batch(probs, use_graph=True, autotune=True) as b:
+        b.run()
+        res = b.results()
+    cost = sorted(range(len(probs)), key=lambda i: -(-probs[i][4] // (probs[i][1] * probs[i][2] * ((probs[i][0] + 1) // 2)))
+                  * probs[i][1] * probs[i][2] * probs[i][0] ** 2)
+    for i in cost[:1]:
+        L, walks, wlen, seed, budget = probs[i]
+        o = oracle.solve(L, [seed], walks, wlen, budget, threads=os.cpu_count() or 8)
+        g = res[i]
+        assert g["best_E"] == int(o["best_E"][0]) and np.array_equal(g["best_seq"], o["best_seq"][0]), probs[i]
+        assert g["evals"] == int(o["evals"][0]) and g["rounds"] == int(o["rounds"][0]), probs[i]
+    for i in cost[1:8]:
+        a = alone(m, probs[i])
+        assert res[i]["best_E"] == a["best_E"] and res[i]["evals"] == a["evals"], probs[i]
+
+
 def oracle_result(p, threads=8):
     import oracle
     L, walks, wl, seed, budget = p[:5]

@@ -178,6 +178,36 @@ def test_tickets_timeouts_and_shutdown(m):
     assert time.time() - t0 < 120
 
 
+def test_full_size_requests_vs_oracle(m):
+    # requests of the serving stream's shape (2048 walks of 8*D steps) in a
+    # server configured like the bench's, mixed with other full-size
+    # requests; the two the oracle solves fastest (one round at L=121 and
+    # L=123, one of them with a target it reaches in that round) are compared
+    # with the oracle's Algorithm 1 + Algorithm 2 directly
+    import os
+    import oracle
+    from paper_2210_15962_gb300 import workloads
+    cores = os.cpu_count() or 8
+    wl121, wl123 = workloads.paper_walk_len(121), workloads.paper_walk_len(123)
+    o121 = oracle.solve(121, [5001], 2048, wl121, 2048 * wl121 * 61, threads=cores)
+    o123 = oracle.solve(123, [5002], 2048, wl123, 2048 * wl123 * 62, threads=cores)
+    checked = [
+        ((121, 2048, wl121, 5001, 10 ** 10, int(o121["best_E"][0])), o121),   # target reached in round 1
+        ((123, 2048, wl123, 5002, 2048 * wl123 * 62), o123),                   # budget of one round
+    ]
+    others = [(L, 2048, workloads.paper_walk_len(L), 5100 + L, 2 * 2048 * workloads.paper_walk_len(L) * ((L + 1) // 2))
+              for L in (161, 223, 301)]
+    with m.Server(max_L=301, max_walks=2048, max_active=64, mem_bytes=16 << 30, rounds_per_launch=4) as sv:
+        tickets = [sv.submit(*p) for p, _ in checked] + [sv.submit(*p) for p in others]
+        results = [sv.wait(t, timeout_s=600) for t in tickets]
+    for (p, o), r in zip(checked, results):
+        assert r["status"] == m.LABS_OK
+        assert r["best_E"] == int(o["best_E"][0]) and np.array_equal(r["best_seq"], o["best_seq"][0]), p
+        assert r["evals"] == int(o["evals"][0]) and r["rounds"] == int(o["rounds"][0]) == 1, p
+    for p, r in zip(others, results[len(checked):]):
+        check(m, p, r)
+
+
 def test_probability_target_sets_the_budget(m):
     # the stopping rule of the predictive model: run until Eq. 7 reaches P
     import oracle
