@@ -453,9 +453,12 @@ def measure_serving(args, warmup):
     # the plain path on the first requests, one labs_walks per request
     tp0 = time.perf_counter()
     plain_ev = 0
+    plain_t = []  # each request's time to its target (or budget) alone, with no queue
     same = True
     for p, r in list(zip(reqs, results))[:args.plain_requests]:
+        tq = time.perf_counter()
         g = pkg.labs_walks(p.L, [p.seed], p.walks, p.walk_len, p.step_budget, target_E=targets[p.L])
+        plain_t.append(time.perf_counter() - tq)
         plain_ev += int(g["evals"][0])
         same = same and int(g["best_E"][0]) == r["best_E"] and int(g["evals"][0]) == r["evals"] \
             and bool((g["best_seq"][0] == r["best_seq"]).all())
@@ -485,9 +488,15 @@ def measure_serving(args, warmup):
                                   popc_per_eval=needed / max(1, evals),
                                   note="useful evaluations only (rounds past a request's stop not counted), "
                                        "over the device's busy time"),
+        # the plain path one request at a time: its time per request with no queue, and the
+        # stream's load over what it sustains (above 1 its queue, and so its latency, grows
+        # without bound at the stream's rate)
         "plain": {"value": plain_ev / (tp1 - tp0), "unit": "neighbour_evals/s",
                   "requests": min(args.plain_requests, len(reqs)), "path": "labs_walks per request, one at a time",
-                  "same_results": bool(same)},
+                  "same_results": bool(same),
+                  "seconds_per_request_alone": ({"p50": float(np.percentile(plain_t, 50)), "max": float(max(plain_t))}
+                                                if plain_t else None),
+                  "stream_load": (evals / (t1 - t0)) / max(1e-9, plain_ev / (tp1 - tp0)) if plain_t else None},
         "gpu_launches": st["launches"] - st0["launches"],
         "capacity": {
             "value": cap_evals / (tc1 - tc0), "unit": "neighbour_evals/s", "requests": len(cap_reqs),
